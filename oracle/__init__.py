@@ -1,0 +1,227 @@
+"""ctypes front end of the FP64 oracle (``fse_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may use this package; the product path
+(``paper_1203_0571_gb300``) never imports it.  It shares no code with the CUDA
+library.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fse_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "libfse_oracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP, -O2, no -march flags: same code on x86 and Arm)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11",
+                           "-D_GNU_SOURCE", "-Wall", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("tol_pos", ctypes.c_double), ("tol_g", ctypes.c_double),
+                ("tol_sig", ctypes.c_double), ("tol_fit", ctypes.c_double),
+                ("max_iter_mom", ctypes.c_int), ("max_iter_fit", ctypes.c_int),
+                ("k_gain", ctypes.c_double), ("sigw_mode", ctypes.c_int),
+                ("n_min", ctypes.c_double), ("n_max", ctypes.c_double),
+                ("re_min", ctypes.c_double), ("re_max_frac", ctypes.c_double),
+                ("lm_lambda0", ctypes.c_double)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("x0", "y0", "e1", "e2", "sigma_w", "r50", "I0", "re", "n", "flux", "chi2")] + \
+               [("npix", ctypes.c_int32), ("it_mom", ctypes.c_int32), ("it_fit", ctypes.c_int32),
+                ("status", ctypes.c_uint32)]
+
+
+RESULT_DTYPE = np.dtype([(k, "f8") for k in
+                         ("x0", "y0", "e1", "e2", "sigma_w", "r50", "I0", "re", "n", "flux", "chi2")] +
+                        [("npix", "i4"), ("it_mom", "i4"), ("it_fit", "i4"), ("status", "u4")])
+assert RESULT_DTYPE.itemsize == ctypes.sizeof(Result)
+
+# status bits
+MOM_CONVERGED, FIT_CONVERGED, MOM_MAXITER, FIT_MAXITER = 1, 2, 4, 8
+NONFINITE, BAD_SIZE, MOM_FAILED, FIT_BOUND = 16, 32, 64, 128
+FIT_SINGULAR, NONPOS_FLUX, SIGW_CLAMPED, INIT_FALLBACK = 256, 512, 1024, 2048
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class Oracle:
+    """The oracle's entry points, bound to one compiled copy of fse_oracle.c."""
+
+    def __init__(self, path: str):
+        L = ctypes.CDLL(path)
+        L.orc_default_opts.argtypes = [ctypes.POINTER(Opts)]
+        for f in ("orc_sersic_b", "orc_sersic_db"):
+            getattr(L, f).argtypes = [ctypes.c_double]
+            getattr(L, f).restype = ctypes.c_double
+        L.orc_gamma_p.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.orc_gamma_p.restype = ctypes.c_double
+        L.orc_sersic_flux.argtypes = [ctypes.c_double] * 4
+        L.orc_sersic_flux.restype = ctypes.c_double
+        for f in ("orc_centroid", "orc_ellipticity"):
+            getattr(L, f).argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Opts),
+                                      ctypes.POINTER(Result)]
+        for f in ("orc_sersic_fit", "orc_measure"):
+            getattr(L, f).argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Opts),
+                                      ctypes.POINTER(Result)]
+        L.orc_moment_step.argtypes = [_dp, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 6 + \
+                                     [ctypes.c_int, _dp]
+        L.orc_fit_eval.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + \
+                                  [_dp, _dp]
+        L.orc_batch.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(Opts), ctypes.c_int,
+                                ctypes.c_void_p, ctypes.c_int]
+        L.orc_batch.restype = ctypes.c_int
+        self.L = L
+        self.path = path
+
+    def default_opts(self, **kw) -> Opts:
+        o = Opts()
+        self.L.orc_default_opts(ctypes.byref(o))
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+
+    def sersic_b(self, n: float) -> float:
+        return self.L.orc_sersic_b(float(n))
+
+    def sersic_db(self, n: float) -> float:
+        return self.L.orc_sersic_db(float(n))
+
+    def gamma_p(self, a: float, x: float) -> float:
+        return self.L.orc_gamma_p(float(a), float(x))
+
+    def sersic_flux(self, I0, re, n, gabs) -> float:
+        return self.L.orc_sersic_flux(float(I0), float(re), float(n), float(gabs))
+
+    def measure(self, I, ivar=None, opts: Opts | None = None) -> dict:
+        """Whole chain on one stamp (float64 array (h, w))."""
+        I = _img(I)
+        iv = None if ivar is None else _img(ivar)
+        r = Result()
+        self.L.orc_measure(_as_dp(I), None if iv is None else _as_dp(iv), I.shape[0], I.shape[1],
+                           ctypes.byref(opts or self.default_opts()), ctypes.byref(r))
+        return _res_dict(r)
+
+    def centroid(self, I, opts: Opts | None = None) -> dict:
+        I = _img(I)
+        r = Result()
+        self.L.orc_centroid(_as_dp(I), I.shape[0], I.shape[1],
+                            ctypes.byref(opts or self.default_opts()), ctypes.byref(r))
+        return _res_dict(r)
+
+    def ellipticity(self, I, x0, y0, sigma_w, opts: Opts | None = None) -> dict:
+        I = _img(I)
+        r = Result()
+        r.x0, r.y0, r.sigma_w = x0, y0, sigma_w
+        self.L.orc_ellipticity(_as_dp(I), I.shape[0], I.shape[1],
+                               ctypes.byref(opts or self.default_opts()), ctypes.byref(r))
+        return _res_dict(r)
+
+    def sersic_fit(self, I, x0, y0, e1, e2, sigma_w, ivar=None, opts: Opts | None = None) -> dict:
+        I = _img(I)
+        iv = None if ivar is None else _img(ivar)
+        r = Result()
+        r.x0, r.y0, r.e1, r.e2, r.sigma_w = x0, y0, e1, e2, sigma_w
+        self.L.orc_sersic_fit(_as_dp(I), None if iv is None else _as_dp(iv), I.shape[0],
+                              I.shape[1], ctypes.byref(opts or self.default_opts()), ctypes.byref(r))
+        return _res_dict(r)
+
+    def moment_step(self, I, xc, yc, g1, g2, sw, k_gain=0.75, ellip=True) -> dict:
+        I = _img(I)
+        out = np.zeros(8)
+        self.L.orc_moment_step(_as_dp(I), I.shape[0], I.shape[1], xc, yc, g1, g2, sw, k_gain,
+                               int(ellip), _as_dp(out))
+        return dict(dx=out[0], dy=out[1], dg1=out[2], dg2=out[3], e1=out[4], e2=out[5],
+                    sigw_new=out[6], ok=bool(out[7]))
+
+    def fit_eval(self, I, xc, yc, g1, g2, p, ivar=None):
+        """chi^2, J^T r and J^T J at p = (I0, r_e, n) with centre and g fixed."""
+        I = _img(I)
+        iv = None if ivar is None else _img(ivar)
+        pp = np.ascontiguousarray(p, dtype=np.float64)
+        out = np.zeros(13)
+        self.L.orc_fit_eval(_as_dp(I), None if iv is None else _as_dp(iv), I.shape[0], I.shape[1],
+                            xc, yc, g1, g2, _as_dp(pp), _as_dp(out))
+        return out[0], out[1:4].copy(), out[4:].reshape(3, 3).copy()
+
+    def batch(self, pix, offset, h, w, stage: str = "measure", ivar=None,
+              opts: Opts | None = None, init=None, threads: int = 0):
+        """Run a stage over a flat fp32 stamp buffer.  Returns (results, threads_used)."""
+        pix = np.ascontiguousarray(pix, dtype=np.float32)
+        offset = np.ascontiguousarray(offset, dtype=np.int64)
+        h = np.ascontiguousarray(h, dtype=np.int32)
+        w = np.ascontiguousarray(w, dtype=np.int32)
+        iv = None if ivar is None else np.ascontiguousarray(ivar, dtype=np.float32)
+        out = np.zeros(offset.size, dtype=RESULT_DTYPE) if init is None else \
+            np.ascontiguousarray(init, dtype=RESULT_DTYPE).copy()
+        used = self.L.orc_batch(pix.ctypes.data, offset.ctypes.data, h.ctypes.data, w.ctypes.data,
+                                offset.size, None if iv is None else iv.ctypes.data,
+                                ctypes.byref(opts or self.default_opts()), STAGES[stage],
+                                out.ctypes.data, threads)
+        return out, used
+
+
+def _as_dp(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _img(I) -> np.ndarray:
+    return np.ascontiguousarray(I, dtype=np.float64)
+
+
+def _res_dict(r: Result) -> dict:
+    return {k: getattr(r, k) for k, _ in Result._fields_}
+
+
+_default = None
+
+
+def get() -> Oracle:
+    """The oracle built from the committed source."""
+    global _default
+    if _default is None:
+        _default = Oracle(build())
+    return _default
+
+
+def compile_variant(source_text: str, out_dir: str) -> Oracle:
+    """Compile a modified copy of the oracle source (used to plant mistakes in tests)."""
+    src = os.path.join(out_dir, "fse_oracle_variant.c")
+    lib_path = os.path.join(out_dir, "libfse_oracle_variant.so")
+    with open(src, "w") as f:
+        f.write(source_text)
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11",
+                           "-D_GNU_SOURCE", "-o", lib_path, src, "-lm"])
+    return Oracle(lib_path)
+
+
+def source_text() -> str:
+    with open(_SRC) as f:
+        return f.read()
+
+
+STAGES = {"measure": 0, "centroid": 1, "ellipticity": 2, "fit": 3}
+
+
+def __getattr__(name):
+    """Module-level access to the default oracle's methods (oracle.measure(...), ...)."""
+    if name in ("default_opts", "sersic_b", "sersic_db", "gamma_p", "sersic_flux", "measure",
+                "centroid", "ellipticity", "sersic_fit", "moment_step", "fit_eval", "batch"):
+        return getattr(get(), name)
+    raise AttributeError(name)

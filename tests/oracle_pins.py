@@ -1,0 +1,288 @@
+"""Pins that tie the FP64 oracle to facts outside itself.
+
+Each pin takes an ``oracle.Oracle`` and raises AssertionError if the oracle
+disagrees with what the paper or the mathematics fixes.  The pin tests run
+them on the committed oracle; the mutation tests run them on copies with a
+planted mistake and require that at least one pin fails.
+
+Sources of truth used here: closed forms stated in the paper (Sec. 2 gain k,
+Eq. 10 half-light b(n), Eq. 13 closed-form I0), library routines
+(scipy.special.gammainc / gammaincinv, scipy.integrate.quad), exact symmetry
+of sampled images, the published asymptotic series of b(n), brute-force
+search, finite differences, and the chi^2 distribution of a correct fit.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+from scipy import integrate, special
+
+from paper_1203_0571_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_facts.json")
+
+
+def facts() -> dict:
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def _gauss(h, w, xc, yc, g1, g2, s_R, I0=100.0):
+    """Noiseless elliptical Gaussian exp(-R^2(g)/2 s_R^2) sampled at pixel centres."""
+    # a Sérsic n = 0.5 profile is a Gaussian: b = ln 2, r = R/(1-|g|)
+    re = s_R * math.sqrt(2 * math.log(2)) / (1 - math.hypot(g1, g2))
+    return synth.single_stamp(h, w, n=0.5, re=re, g1=g1, g2=g2, xc=xc, yc=yc, I0=I0)
+
+
+# ---------------------------------------------------------------- b(n), P(a,x)
+def pin_gamma_p_library(O):
+    """P(a, x) equals scipy.special.gammainc over the range the fit uses."""
+    for a in (0.1, 0.4, 1.0, 2.5, 7.0, 20.0):
+        for x in (1e-3, 0.1, 1.0, a, a + 1.5, 3 * a + 5, 60.0):
+            got, want = O.gamma_p(a, x), special.gammainc(a, x)
+            assert abs(got - want) <= 1e-13, (a, x, got, want)
+
+
+def pin_sersic_b(O):
+    """b(n) is the half-light constant of Eq. 10: b(0.5) = ln 2, the n = 1 and
+    n = 1.5 closed forms of P, and P(2n, b(n)) = 1/2 by the library."""
+    f = facts()
+    assert abs(O.sersic_b(0.5) - f["sersic_b_half"]["value"]) <= 2e-16
+    b = O.sersic_b(1.0)
+    assert abs(1 - math.exp(-b) * (1 + b) - 0.5) <= 1e-15
+    b = O.sersic_b(1.5)
+    assert abs(1 - math.exp(-b) * (1 + b + b * b / 2) - 0.5) <= 1e-15
+    for n in np.linspace(0.2, 10.0, 50):
+        assert abs(special.gammainc(2 * n, O.sersic_b(n)) - 0.5) <= 1e-13, n
+
+
+def pin_sersic_db(O):
+    """b'(n): the published large-n series b = 2n - 1/3 + 4/(405 n) + 46/(25515 n^2)
+    + 131/(1148175 n^3) - 2194697/(30690717750 n^4) ... (Ciotti & Bertin 1999) differentiated term by term, and a
+    central difference of the library's inverse gamma at moderate n."""
+    for n in (20.0, 40.0):
+        series = (2 - 4 / (405 * n ** 2) - 92 / (25515 * n ** 3) - 393 / (1148175 * n ** 4)
+                  + 4 * 2194697 / (30690717750 * n ** 5))
+        assert abs(O.sersic_db(n) - series) <= 2e-9, (n, O.sersic_db(n), series)
+    for n in (0.3, 0.7, 1.0, 2.0, 4.5):
+        h = 1e-5
+        fd = (special.gammaincinv(2 * (n + h), 0.5) - special.gammaincinv(2 * (n - h), 0.5)) / (2 * h)
+        assert abs(O.sersic_db(n) - fd) <= 1e-7 * max(1.0, abs(fd)), (n, O.sersic_db(n), fd)
+
+
+# ---------------------------------------------------------------- flux
+def pin_flux_closed_form(O):
+    """F = 2 pi n Gamma(2n) b^-2n I0 r_e^2 q equals the numerically integrated
+    Eq. 10 profile over the plane (elliptical area element q 2 pi r dr)."""
+    for (I0, re, n, gabs) in ((3.0, 2.0, 0.5, 0.0), (1.0, 4.0, 1.0, 0.3), (7.0, 3.0, 2.5, 0.6),
+                              (2.0, 5.0, 4.0, 0.1), (1.0, 1.5, 8.0, 0.45)):
+        b = special.gammaincinv(2 * n, 0.5)
+        q = (1 - gabs) / (1 + gabs)
+        # integrate in t = (r/r_e)^(1/n): r dr = r_e^2 n t^(2n-1) dt
+        val, _ = integrate.quad(lambda t: t ** (2 * n - 1) * math.exp(-b * t), 0, np.inf,
+                                epsabs=0, epsrel=1e-13, limit=200)
+        want = 2 * math.pi * q * I0 * re * re * n * val
+        got = O.sersic_flux(I0, re, n, gabs)
+        assert abs(got / want - 1) <= 1e-9, (n, got, want)
+
+
+def pin_flux_pixel_sum(O):
+    """The closed-form flux equals the sum of a finely super-sampled stamp that
+    holds essentially all of the light (n = 1, r_e = 4 px in 128 x 128)."""
+    img = synth.single_stamp(128, 128, n=1.0, re=4.0, g1=0.2, g2=-0.15, xc=63.3, yc=64.1,
+                             I0=10.0, supersample=8)
+    got = O.sersic_flux(10.0, 4.0, 1.0, math.hypot(0.2, -0.15))
+    assert abs(img.sum() / got - 1) <= 1e-4, (img.sum(), got)
+
+
+# ---------------------------------------------------------------- moments
+def pin_centroid_symmetric(O):
+    """A point-symmetric sampled image has its weighted-centroid fixed point at the
+    symmetry centre exactly, for any weight size and ellipticity (Sec. 2 fixed point
+    sum I W theta = 0)."""
+    rng = np.random.default_rng(5)
+    for (n, re, g1, g2) in ((1.0, 3.0, 0.0, 0.0), (3.0, 5.0, 0.25, -0.3), (0.5, 2.5, -0.4, 0.1)):
+        img = synth.single_stamp(64, 64, n=n, re=re, g1=g1, g2=g2, xc=31.5, yc=31.5, I0=1000.0)
+        noise = rng.normal(size=img.shape)
+        img = img + 0.5 * (noise + noise[::-1, ::-1])
+        r = O.centroid(img)
+        assert r["status"] & 1, r
+        assert abs(r["x0"] - 31.5) <= 1e-10 and abs(r["y0"] - 31.5) <= 1e-10, r
+        r = O.measure(img)
+        assert r["status"] & 1, r
+        assert abs(r["x0"] - 31.5) <= 1e-10 and abs(r["y0"] - 31.5) <= 1e-10, r
+
+
+def pin_centroid_gain(O):
+    """Sec. 2: one pass with a circular Gaussian weight of size s_w on a circular
+    Gaussian of size s offset by (dx, dy) gives <x>/N = k dx with
+    k = s_w^2/(s^2 + s_w^2); k = 0.5 when s = s_w; and the fixed gain 0.75 then
+    shrinks the offset by a factor 3."""
+    f = facts()
+    for (s, sw) in ((4.0, 3.0), (3.0, 3.0), (2.5, 5.0)):
+        img = _gauss(96, 96, 48.3, 47.6, 0.0, 0.0, s)
+        st = O.moment_step(img, 48.0, 48.0, 0.0, 0.0, sw, k_gain=1.0, ellip=False)
+        k = sw * sw / (s * s + sw * sw)
+        assert abs(st["dx"] - 0.3 * k) <= 1e-10 and abs(st["dy"] + 0.4 * k) <= 1e-10, (st, k)
+        if s == sw:
+            assert abs(k - f["centroid_gain_matched"]["value"]) < 1e-15
+            st = O.moment_step(img, 48.0, 48.0, 0.0, 0.0, sw, k_gain=0.75, ellip=False)
+            left = (0.3 - st["dx"]) / 0.3
+            assert abs(left - f["centroid_contraction_k075"]["value"]) <= 1e-9, left
+
+
+def pin_ellipticity_exact(O):
+    """For an elliptical profile f(R(g)) the weight W(R(g_w)) at g_w = g makes the
+    product a sheared circular function, so e^obs = 2g/(1+g^2) = e_w and g is the
+    fixed point of Eq. 9.  Checked on well-sampled elliptical Gaussians."""
+    for (g1, g2, s_R, xc, yc) in ((0.3, -0.25, 7.0, 63.2, 64.7), (-0.5, 0.3, 4.0, 64.4, 63.1),
+                                  (0.05, 0.02, 6.0, 62.9, 63.6)):
+        img = _gauss(128, 128, xc, yc, g1, g2, s_R)
+        r = O.measure(img)
+        assert r["status"] & 1, r
+        assert abs(r["x0"] - xc) <= 1e-9 and abs(r["y0"] - yc) <= 1e-9, r
+        assert abs(r["e1"] - g1) <= 1e-9 and abs(r["e2"] - g2) <= 1e-9, r
+        gg = g1 * g1 + g2 * g2
+        st = O.moment_step(img, xc, yc, g1, g2, r["sigma_w"])
+        assert abs(st["e1"] - 2 * g1 / (1 + gg)) <= 1e-12 and abs(st["e2"] - 2 * g2 / (1 + gg)) <= 1e-12
+
+
+def pin_ellipticity_step_newton(O):
+    """The step of Eq. 9 with P^SH from Eqs. A5-A6 plus B7-B14 is first-order exact:
+    from g_w = g + d it returns -d up to O(d^2), and at g_w = 0 on a slightly sheared
+    round profile it returns the shear (the KSB limit).  A dropped or mistyped term in
+    the appendices leaves an O(1) relative error instead."""
+    g = (0.3, -0.25)
+    c = 63.5
+    img = _gauss(128, 128, c, c, g[0], g[1], 7.0)
+    errs = {}
+    for d in (1e-3, 1e-4):
+        worst = 0.0
+        for dirn in ((1.0, 0.0), (0.0, 1.0), (0.6, -0.8)):
+            st = O.moment_step(img, c, c, g[0] + d * dirn[0], g[1] + d * dirn[1], 6.5)
+            err = math.hypot(st["dg1"] + d * dirn[0], st["dg2"] + d * dirn[1]) / d
+            worst = max(worst, err)
+        errs[d] = worst
+    assert errs[1e-4] <= 3e-4, errs
+    assert 5.0 <= errs[1e-3] / errs[1e-4] <= 20.0, errs
+    for gam in (1e-4,):
+        img2 = _gauss(128, 128, c, c, gam, -0.5 * gam, 7.0)
+        st = O.moment_step(img2, c, c, 0.0, 0.0, 7.0)
+        assert abs(st["dg1"] / gam - 1) <= 1e-6 and abs(st["dg2"] / (-0.5 * gam) - 1) <= 1e-6, st
+
+
+def pin_matched_sigma_w(O):
+    """Mode 0 (matched weight, Sec. 4.2.1): for an elliptical Gaussian of size s the
+    rule sigma_w^2 = sum I W R^2 / sum I W converges to sigma_w = s."""
+    for (g1, g2, s_R) in ((0.0, 0.0, 5.0), (0.2, 0.3, 6.0)):
+        img = _gauss(128, 128, 63.7, 64.2, g1, g2, s_R)
+        r = O.measure(img, opts=O.default_opts(sigw_mode=0))
+        assert r["status"] & 1, r
+        assert abs(r["sigma_w"] - s_R) <= 1e-9, r
+        assert abs(r["e1"] - g1) <= 1e-9 and abs(r["e2"] - g2) <= 1e-9, r
+
+
+def pin_stages_chain(O):
+    """fse_centroid then fse_ellipticity reach the same fixed point as the single
+    chain of Sec. 4.1 (the fixed point does not depend on the path)."""
+    rng = np.random.default_rng(11)
+    for (n, re, g1, g2) in ((1.5, 3.0, 0.2, 0.1), (3.0, 4.0, -0.3, 0.25)):
+        img = synth.single_stamp(48, 48, n=n, re=re, g1=g1, g2=g2, xc=23.4, yc=24.3, I0=300.0)
+        img = img + rng.normal(size=img.shape)
+        full = O.measure(img)
+        c = O.centroid(img)
+        e = O.ellipticity(img, c["x0"], c["y0"], c["sigma_w"])
+        for k in ("x0", "y0", "e1", "e2"):
+            assert abs(full[k] - e[k]) <= 1e-9, (k, full[k], e[k])
+
+
+# ---------------------------------------------------------------- fit
+def pin_fit_noiseless(O):
+    """A noiseless Eq. 10 stamp (rendered independently, scipy b(n)) fitted with the
+    true centre and ellipticity returns the true (I0, r_e, n)."""
+    for (n, re, g1, g2, I0) in ((0.6, 2.5, 0.1, 0.2, 500.0), (1.3, 6.0, -0.3, 0.1, 80.0),
+                                (3.0, 4.0, 0.25, -0.35, 2e3), (5.5, 5.0, 0.0, 0.4, 1e4)):
+        img = synth.single_stamp(48, 48, n=n, re=re, g1=g1, g2=g2, xc=23.3, yc=24.6, I0=I0)
+        r = O.sersic_fit(img, 23.3, 24.6, g1, g2, re / 1.1774)
+        assert r["status"] & 2, r
+        for k, v in (("I0", I0), ("re", re), ("n", n)):
+            assert abs(r[k] / v - 1) <= 1e-8, (k, r[k], v)
+
+
+def pin_fit_gradient_fd(O):
+    """The fit's J^T r is half the gradient of the oracle's own chi^2 (Eq. 11):
+    central finite differences in FP64."""
+    img = synth.single_stamp(32, 32, n=2.2, re=3.5, g1=0.2, g2=-0.1, xc=15.3, yc=16.2, I0=800.0,
+                             noise_sigma=1.0, seed=3)
+    p = np.array([700.0, 3.2, 2.5])
+    chi2, g, H = O.fit_eval(img, 15.3, 16.2, 0.2, -0.1, p)
+    for a in range(3):
+        h = 1e-5 * p[a]
+        pp, pm = p.copy(), p.copy()
+        pp[a] += h
+        pm[a] -= h
+        fd = (O.fit_eval(img, 15.3, 16.2, 0.2, -0.1, pp)[0] - O.fit_eval(img, 15.3, 16.2, 0.2, -0.1, pm)[0]) / (2 * h)
+        assert abs(2 * g[a] - fd) <= 1e-6 * abs(fd) + 1e-6, (a, 2 * g[a], fd)
+    # J^T J diagonal is positive and Cauchy-Schwarz holds
+    assert all(H[a, a] > 0 for a in range(3))
+    assert H[0, 1] ** 2 <= H[0, 0] * H[1, 1] * (1 + 1e-12)
+
+
+def pin_fit_minimum(O):
+    """At the fit's optimum the gradient of chi^2 vanishes (so I0 is the closed form
+    of Eq. 13), and no point of a brute-force (r_e, n) grid with I0 profiled has a
+    lower chi^2 (tiny 12 x 12 stamps)."""
+    rng = np.random.default_rng(2)
+    for trial in range(3):
+        n0, re0 = rng.uniform(0.8, 2.5), rng.uniform(1.5, 2.5)
+        img = synth.single_stamp(12, 12, n=n0, re=re0, g1=0.1, g2=0.05, xc=5.6, yc=5.3, I0=400.0,
+                                 noise_sigma=1.0, seed=20 + trial)
+        r = O.sersic_fit(img, 5.6, 5.3, 0.1, 0.05, 1.6)
+        assert r["status"] & 2, r
+        p = np.array([r["I0"], r["re"], r["n"]])
+        chi2, g, H = O.fit_eval(img, 5.6, 5.3, 0.1, 0.05, p)
+        for a in range(3):
+            assert abs(g[a]) <= 1e-7 * math.sqrt(H[a, a] * max(chi2, 1.0)), (a, g, H)
+        best = np.inf
+        for re_ in np.linspace(0.5 * p[1], 1.5 * p[1], 61):
+            for n_ in np.linspace(max(0.2, 0.5 * p[2]), min(10.0, 1.5 * p[2]), 61):
+                c1, g1_, H1 = O.fit_eval(img, 5.6, 5.3, 0.1, 0.05, [1.0, re_, n_])
+                I0 = (H1[0, 0] - g1_[0]) / H1[0, 0]          # sum I E / sum E^2
+                c = O.fit_eval(img, 5.6, 5.3, 0.1, 0.05, [I0, re_, n_])[0]
+                best = min(best, c)
+        assert r["chi2"] <= best * (1 + 1e-12), (r["chi2"], best)
+
+
+def pin_fit_chi2_distribution(O):
+    """With the exact model family and the true centre and ellipticity, chi^2_min
+    follows chi^2 with N-3 degrees of freedom (noise sigma = 1)."""
+    vals = []
+    N = 24 * 24
+    for s in range(120):
+        img = synth.single_stamp(24, 24, n=1.5, re=3.0, g1=0.2, g2=0.1, xc=11.7, yc=12.2,
+                                 I0=200.0, noise_sigma=1.0, seed=100 + s)
+        r = O.sersic_fit(img, 11.7, 12.2, 0.2, 0.1, 2.2)
+        vals.append(r["chi2"] / (N - 3))
+    m = float(np.mean(vals))
+    assert abs(m - 1.0) <= 4 * math.sqrt(2.0 / (N - 3)) / math.sqrt(len(vals)), m
+
+
+def pin_edge_cases(O):
+    """Status codes: non-finite pixels, empty flux, out-of-range sizes."""
+    img = np.ones((8, 8))
+    img[3, 4] = np.nan
+    assert O.measure(img)["status"] & 16
+    assert O.measure(np.zeros((8, 8)))["status"] & (2048 | 64)
+    res, _ = O.batch(np.zeros(4, np.float32), [0], [0], [4])
+    assert res["status"][0] & 32
+    res, _ = O.batch(np.zeros(129 * 129, np.float32), [0], [129], [129])
+    assert res["status"][0] & 32
+
+
+ALL_PINS = [pin_gamma_p_library, pin_sersic_b, pin_sersic_db, pin_flux_closed_form,
+            pin_flux_pixel_sum, pin_centroid_symmetric, pin_centroid_gain, pin_ellipticity_exact,
+            pin_ellipticity_step_newton, pin_matched_sigma_w, pin_stages_chain, pin_fit_noiseless,
+            pin_fit_gradient_fd, pin_fit_minimum, pin_fit_chi2_distribution, pin_edge_cases]

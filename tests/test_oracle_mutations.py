@@ -1,0 +1,68 @@
+"""Plant plausible mistakes in a copy of the oracle and check that a pin catches each.
+
+Every mutation is a textual edit of oracle/fse_oracle.c compiled into a
+temporary library (CPU only); the committed oracle is never touched.  A
+mutation that no pin detects would mean the pins leave that part of the
+oracle unchecked.
+"""
+import pytest
+
+import oracle_pins as P
+
+MUTATIONS = {
+    # Eq. A1: sign of the cross term of the elliptical radius
+    "R2_cross_sign": ("         - 4.0 * g2 * t1 * t2;", "         + 4.0 * g2 * t1 * t2;"),
+    # Sec. 2: weight exp(-R^2/2 sigma_w^2) loses its factor 2
+    "weight_width": ("double c = 1.0 / (2.0 * sw * sw);", "double c = 1.0 / (sw * sw);"),
+    # Eqs. 5-6: gain k dropped from the centroid step
+    "centroid_gain": ("s.dx = mx / (k_gain * N);", "s.dx = mx / N;"),
+    # Eq. A5: transposed operand in the X^SH_21 integrand
+    "XSH21_operand": ("X21 += f * (4.0 * Wp * p12 * a1);", "X21 += f * (4.0 * Wp * p12 * a2);"),
+    # Eq. B9: dropped W' term of P_1
+    "P1_dropped_term": ("P1 += f * (4.0 * W * d1 + 2.0 * Wp * d1 * b1);", "P1 += f * (4.0 * W * d1);"),
+    # Eq. A6: e^SH loses the factor 2 on e
+    "eSH_factor": ("2.0 * e1 + 2.0 * eS1 / T", "e1 + 2.0 * eS1 / T"),
+    # Eq. 8: wrong index in P^SH = X - e e^SH
+    "PSH_index": ("X[0][1] - e1 * eSH[1]", "X[0][1] - e2 * eSH[1]"),
+    # Eq. 9: e_w taken as g_w instead of 2 g_w/(1+g_w^2)
+    "e_w_convention": ("double r1 = e1 - 2.0 * gw1 / (1.0 + gg);", "double r1 = e1 - gw1;"),
+    # incomplete gamma series: off-by-one in the denominator
+    "gamma_series": ("term *= x / (a + k);", "term *= x / (a + k + 1);"),
+    # incomplete gamma continued fraction: sign inside a_n
+    "gamma_cf": ("double an = -i * (i - a);", "double an = -i * (i + a);"),
+    # b'(n): Richardson combination swapped
+    "db_richardson": ("return (4.0 * d2 - d1) / 3.0;", "return (4.0 * d1 - d2) / 3.0;"),
+    # flux closed form: dropped factor n
+    "flux_n": ("return 2.0 * M_PI * n * exp(", "return 2.0 * M_PI * exp("),
+    # flux closed form: axis ratio without the (1+|g|)
+    "flux_q": ("double q = (1.0 - gabs) / (1.0 + gabs);\n    return", "double q = (1.0 - gabs);\n    return"),
+    # Sérsic radius not divided by (1 - |g|)
+    "sersic_radius": ("r[i * w + j] = sqrt(R2 > 0.0 ? R2 : 0.0) / (1.0 - gabs);",
+                      "r[i * w + j] = sqrt(R2 > 0.0 ? R2 : 0.0);"),
+    # dm/dr_e loses the 1/n
+    "jac_re": ("J[1] = m * b * u / (n * re);", "J[1] = m * b * u / re;"),
+    # dm/dn: sign of the b' term
+    "jac_n_sign": ("(b * log(x) / (n * n) - db)", "(b * log(x) / (n * n) + db)"),
+    # Eq. 13: amplitude normalised by sqrt
+    "I0_closed_form": ("double I0 = sIf / sff;                                   /* Eq. 13 */",
+                       "double I0 = sIf / sqrt(sff);                             /* Eq. 13 */"),
+    # start-up: ties / argmax replaced by argmin
+    "brightest_pixel": ("if (I[p] > I[best]) best = p;", "if (I[p] < I[best]) best = p;"),
+    # non-finite input no longer flagged
+    "nonfinite_check": ("if (!isfinite(I[p])) { *status |= ORC_NONFINITE; return 0; }", ""),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_mutation_is_caught(oracle, tmp_path, name):
+    old, new = MUTATIONS[name]
+    src = oracle.source_text()
+    assert old in src, f"mutation site for {name} no longer in the oracle source"
+    variant = oracle.compile_variant(src.replace(old, new), str(tmp_path))
+    failed = []
+    for pin in P.ALL_PINS:
+        try:
+            pin(variant)
+        except AssertionError:
+            failed.append(pin.__name__)
+    assert failed, f"no pin detects mutation {name}"
