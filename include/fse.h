@@ -1,0 +1,205 @@
+/*
+ * fse.h -- C ABI of libfse, a GB300 (sm_103a) implementation of the fast
+ * shape estimator of Li, Xin & Cui (2012), "Fast Shape Estimation for
+ * Galaxies and Stars":
+ *   1. centroid from Gaussian-weighted first moments with a fixed gain
+ *      (Sec. 2, Eqs. 2-6);
+ *   2. ellipticity from the KSB shear polarisability with an elliptical
+ *      weight, iterated until the weight's ellipticity matches the object's
+ *      (Sec. 3, Eqs. 7-9; Appendix A, Eqs. A1-A6; Appendix B, Eqs. B7-B14);
+ *   3. a fit of the Sérsic profile (Eq. 10) over (r_e, n), with the amplitude
+ *      I0 at its closed form (Eq. 13) and chi^2 as in Eq. 11 (Sec. 4.1),
+ * applied to many postage stamps at once.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - A stamp is h x w pixels, row-major.  Pixel (row i, column j) has its
+ *    centre at (x = j, y = i) in stamp coordinates.
+ *  - Pixels of all stamps sit in one flat buffer; stamp s starts at element
+ *    idx[s].offset.  Stamps may be unaligned, of different sizes, and in any
+ *    order.  1 <= h*w <= opts->max_pix <= FSE_MAX_PIX; a stamp outside that
+ *    range is reported with FSE_ST_BAD_SIZE and no other work.
+ *  - Pixel type FSE_F32: float.  FSE_BF16: bfloat16, decoded as
+ *    (float)pix * scale[s] with one float scale per stamp.
+ *  - inv_var (optional, may be NULL): per-pixel 1/sigma_i^2 as float, laid out
+ *    like the pixels; NULL means sigma_i = 1.  It weights chi^2 (Eq. 11) and
+ *    the amplitude of Eq. 13; the moments do not use it.
+ *  - Ellipticity g = (e1, e2) is the shear-type ellipticity of Eq. A1:
+ *      R^2 = [(1-e1)^2+e2^2] dx^2 + [(1+e1)^2+e2^2] dy^2 - 4 e2 dx dy,
+ *    the Sérsic radius is r = R / (1-|g|) (so r_e is the half-light radius
+ *    along the major axis) and the axis ratio is q = (1-|g|)/(1+|g|).
+ *  - Device entry points take DEVICE pointers owned by the caller (pix, scale,
+ *    idx, inv_var, out) and a HOST pointer to the options (NULL = defaults).
+ *    They are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream); out is complete when the stream reaches that point.
+ *  - Return codes describe the call, never a stamp: FSE_OK, or FSE_EINVAL
+ *    (bad argument; nothing launched), FSE_ENOMEM, FSE_ECUDA (a CUDA error;
+ *    fse_last_error() gives the text), FSE_ETIMEOUT (a bounded device wait
+ *    expired), FSE_EUNSUPPORTED.  Per-stamp problems go to fse_result.status.
+ *    No call aborts, traps or prints.
+ *  - count == 0 is a no-op returning FSE_OK.
+ *  - One fse_ctx may be used from one host thread at a time; calls that
+ *    overlap on the GPU must use different streams (up to 64 in flight).
+ */
+#ifndef FSE_H
+#define FSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FSE_OK            0
+#define FSE_EINVAL        1
+#define FSE_ENOMEM        2
+#define FSE_ECUDA         3
+#define FSE_ETIMEOUT      4
+#define FSE_EUNSUPPORTED  5
+
+#define FSE_MAX_PIX       (128 * 128)
+
+/* fse_result.status bits */
+#define FSE_ST_MOM_CONVERGED  (1u << 0)  /* centroid/ellipticity reached the stop rule      */
+#define FSE_ST_FIT_CONVERGED  (1u << 1)  /* profile fit reached its stop rule               */
+#define FSE_ST_MOM_MAXITER    (1u << 2)  /* moment loop hit max_iter_mom                    */
+#define FSE_ST_FIT_MAXITER    (1u << 3)  /* fit hit max_iter_fit                            */
+#define FSE_ST_NONFINITE      (1u << 4)  /* a NaN/Inf pixel: stamp skipped                  */
+#define FSE_ST_BAD_SIZE       (1u << 5)  /* h*w outside [1, max_pix]: stamp skipped         */
+#define FSE_ST_MOM_FAILED     (1u << 6)  /* sum I W <= 0, T <= 0, |g| >= 0.95, centre left
+                                            the stamp or P^SH singular: no fit              */
+#define FSE_ST_FIT_BOUND      (1u << 7)  /* r_e or n ended on a bound                       */
+#define FSE_ST_FIT_SINGULAR   (1u << 8)  /* damped normal equations singular                */
+#define FSE_ST_NONPOS_FLUX    (1u << 9)  /* fitted I0 <= 0                                   */
+#define FSE_ST_SIGW_CLAMPED   (1u << 10) /* sigma_w clamped to [0.5, min(h,w)/2]            */
+#define FSE_ST_INIT_FALLBACK  (1u << 11) /* stamp total <= 0: sigma_w from r50 = 1.1774 px  */
+#define FSE_ST_TIMEOUT        (1u << 12) /* a bounded device wait expired for this stamp    */
+
+typedef struct fse_ctx fse_ctx;
+
+/* Stamp index entry (16 bytes).  offset counts elements (not bytes). */
+typedef struct {
+    int64_t offset;
+    int32_t h;
+    int32_t w;
+} fse_stamp;
+
+enum { FSE_F32 = 0, FSE_BF16 = 1 };
+
+/* Options (host struct; fse_opts_default fills the defaults below). */
+typedef struct {
+    size_t  size;           /* sizeof(fse_opts), for versioning                         */
+    double  tol_pos;        /* stop when |centroid step| <= tol_pos px        (1e-6)    */
+    double  tol_g;          /* ... and |ellipticity step| <= tol_g            (1e-6)    */
+    double  tol_sig;        /* ... and |sigma_w step|/sigma_w <= tol_sig, mode 0 (1e-6) */
+    double  tol_fit;        /* fit stops when max relative (r_e, n) step <= tol_fit (1e-6) */
+    int32_t max_iter_mom;   /* moment iterations                              (60)      */
+    int32_t max_iter_fit;   /* fit iterations                                 (60)      */
+    double  k_gain;         /* centroid gain k of Sec. 2                      (0.75)    */
+    int32_t sigw_mode;      /* 1: sigma_w = r50/sqrt(2 ln 2) fixed; 0: matched-weight
+                               rule sigma_w^2 = sum I W R^2 / sum I W (Sec. 4.2.1)  (1)  */
+    int32_t max_pix;        /* upper bound of h*w over the batch; sets the shared-memory
+                               tile (0 = FSE_MAX_PIX)                         (0)       */
+    double  n_min, n_max;   /* bounds on n                                    (0.2, 10) */
+    double  re_min;         /* lower bound on r_e, px                         (0.2)     */
+    double  re_max_frac;    /* upper bound on r_e = re_max_frac * max(h, w)   (2)       */
+    double  lm_lambda0;     /* initial Levenberg-Marquardt damping            (1e-3)    */
+    uint32_t flags;         /* reserved, 0                                              */
+    int32_t warps_per_cta;  /* launch shape (0 = library choice)                        */
+} fse_opts;
+
+/* Per-stamp result (64 bytes). */
+typedef struct {
+    float    x0, y0;        /* centroid, stamp pixel coordinates                        */
+    float    e1, e2;        /* ellipticity g                                            */
+    float    I0;            /* central intensity, Eq. 13 at the optimum                 */
+    float    re;            /* half-light radius along the major axis, px               */
+    float    n;             /* Sérsic index                                              */
+    float    flux;          /* 2 pi n Gamma(2n) b^-2n I0 r_e^2 q                        */
+    double   chi2;          /* Eq. 11 at the optimum                                     */
+    int32_t  npix;          /* h*w                                                      */
+    int32_t  it_mom;        /* moment iterations (weighted passes)                      */
+    int32_t  it_fit;        /* fit passes: profile evaluations after the start pass     */
+    uint32_t status;        /* FSE_ST_* bits                                            */
+    float    sigma_w;       /* weight size used by the moments, px                      */
+    float    r50;           /* growth-curve half-light radius of the start-up, px       */
+} fse_result;
+
+/* Create a context on CUDA device `device`: selects the device, builds the
+ * device table of the Sérsic b(n) (root of P(2n, b) = 1/2, Eq. 10) and b'(n),
+ * and allocates a small workspace.  *ctx is NULL on failure. */
+int fse_create(fse_ctx **ctx, int device);
+
+/* Release the context and its device memory (synchronises the device). */
+void fse_destroy(fse_ctx *ctx);
+
+/* Text of the last error of this context ("" if none).  Owned by ctx. */
+const char *fse_last_error(const fse_ctx *ctx);
+
+/* Defaults listed in fse_opts. */
+void fse_opts_default(fse_opts *opts);
+
+/* Sec. 2 alone (Eqs. 2-6): per stamp, start at the brightest pixel (ties: the
+ * lowest row-major index), take sigma_w from the growth-curve half-light
+ * radius r50 around it (Sec. 4.1), and iterate x_c += <x>/(k N) with a
+ * circular Gaussian weight to the stop rule.  Writes x0, y0, sigma_w, r50,
+ * npix, it_mom, status; zeroes the other fields of out[s]. */
+int fse_centroid(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
+                 const fse_stamp *idx, int64_t count, const float *inv_var,
+                 const fse_opts *opts, fse_result *out, void *stream);
+
+/* Secs. 2-3 together (Eqs. 5-9, A1-A6, B7-B14): from out[s].x0, y0 and
+ * sigma_w, iterate the centroid step and the ellipticity step
+ * dg = (1-|g_w|^2) (P^SH)^-1 (e^obs - e_w), starting from g_w = 0 (the
+ * circular-weight KSB estimate), to the stop rule.  Reads and rewrites
+ * x0, y0 and sigma_w; writes e1, e2, it_mom and the moment status bits. */
+int fse_ellipticity(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
+                    const fse_stamp *idx, int64_t count, const float *inv_var,
+                    const fse_opts *opts, fse_result *inout, void *stream);
+
+/* Sec. 4.1 fit (Eqs. 10-13) with centre and ellipticity held at out[s].x0,
+ * y0, e1, e2: start at r_e = 1.1774 sigma_w / (1-|g|) and the best n of
+ * {0.5, 1, 2, 4}, then Levenberg-Marquardt over (r_e, n) with I0 at its
+ * closed form.  Writes I0, re, n, flux, chi2, it_fit and the fit status bits. */
+int fse_sersic_fit(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
+                   const fse_stamp *idx, int64_t count, const float *inv_var,
+                   const fse_opts *opts, fse_result *inout, void *stream);
+
+/* The whole chain of Sec. 4.1 (start-up, centroid + ellipticity from the
+ * brightest pixel, fit) in one persistent launch. */
+int fse_fit_batch(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
+                  const fse_stamp *idx, int64_t count, const float *inv_var,
+                  const fse_opts *opts, fse_result *out, void *stream);
+
+/* The same chain launched once per stamp (one warp per launch).  A baseline
+ * for measurement only; results are identical to fse_fit_batch. */
+int fse_fit_batch_plain(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
+                        const fse_stamp *idx, int64_t count, const float *inv_var,
+                        const fse_opts *opts, fse_result *out, void *stream);
+
+/* fse_fit_batch on HOST buffers: pix (npix_total elements of dtype), scale
+ * (count floats or NULL), idx, inv_var (or NULL) and out are host pointers
+ * (page-locked memory lets the copies overlap the kernels).  The call copies
+ * the inputs to context-owned device buffers in chunks, runs the chain, copies
+ * the results back and returns when out[] is complete.  npix_total bounds
+ * every idx[s].offset + h*w. */
+int fse_fit_batch_host(fse_ctx *ctx, const void *pix, int64_t npix_total, int dtype,
+                       const float *scale, const fse_stamp *idx, int64_t count,
+                       const float *inv_var, const fse_opts *opts, fse_result *out,
+                       void *stream);
+
+/* Evaluate the device b(n) table (Eq. 10: P(2n, b) = 1/2) and its derivative
+ * at count values n[i] in [0.2, 10] (device pointers, doubles).  For tests. */
+int fse_sersic_b(fse_ctx *ctx, const double *n, double *b, double *db, int64_t count,
+                 void *stream);
+
+/* Wait for `stream` and report a bounded device wait that expired during any
+ * earlier call of this context (FSE_ETIMEOUT), or FSE_OK.  Clears the flag. */
+int fse_sync_check(fse_ctx *ctx, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSE_H */

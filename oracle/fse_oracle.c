@@ -504,6 +504,7 @@ static void fit_stamp(const double *I, const double *ivar, int h, int w, const o
      * nu *= 2, where rho = actual / predicted decrease of chi^2. */
     double H[2][2], g[2];
     double chi2 = profiled_eval(&d, th[0], th[1], &I0, H, g);
+    int evals = 1;
     double lambda = o->lm_lambda0, nu = 2.0;
     int it, converged = 0;
     for (it = 1; it <= o->max_iter_fit; ++it) {
@@ -523,6 +524,7 @@ static void fit_stamp(const double *I, const double *ivar, int h, int w, const o
         if (step <= o->tol_fit) { converged = 1; break; }
         double Hq[2][2], gq[2], I0q;
         double chi2q = profiled_eval(&d, q[0], q[1], &I0q, Hq, gq);
+        ++evals;
         /* predicted decrease of the Gauss-Newton model chi^2 + 2 g.s + s.H.s */
         double pred = -(2.0 * (g[0] * s[0] + g[1] * s[1])
                         + s[0] * (H[0][0] * s[0] + H[0][1] * s[1])
@@ -544,7 +546,7 @@ static void fit_stamp(const double *I, const double *ivar, int h, int w, const o
         }
     }
     if (converged) res->status |= ORC_FIT_CONVERGED;
-    else if (it > o->max_iter_fit) { res->status |= ORC_FIT_MAXITER; it = o->max_iter_fit; }
+    else if (it > o->max_iter_fit) res->status |= ORC_FIT_MAXITER;
     if (th[0] <= o->re_min || th[0] >= re_max || th[1] <= o->n_min || th[1] >= o->n_max)
         res->status |= ORC_FIT_BOUND;
     if (!(I0 > 0.0)) res->status |= ORC_NONPOS_FLUX;
@@ -552,7 +554,7 @@ static void fit_stamp(const double *I, const double *ivar, int h, int w, const o
     res->re = th[0];
     res->n = th[1];
     res->chi2 = chi2;
-    res->it_fit = it;
+    res->it_fit = evals;   /* profile evaluations after the start */
     res->flux = orc_sersic_flux(I0, th[0], th[1], gabs);
     free(r);
 }

@@ -1,0 +1,271 @@
+"""ctypes binding of libfse (include/fse.h): argument marshalling only.
+
+Every computation runs in the CUDA kernels behind the C ABI.  There is no
+CPU path: if libfse.so cannot be built or loaded the import of a compute
+entry point raises.
+
+Names follow the ABI: ``Context.fit_batch`` calls ``fse_fit_batch``,
+``Context.centroid`` calls ``fse_centroid`` and so on; the module-level
+``fse_*`` functions take the context as their first argument, like the C
+calls.  Device arrays are torch CUDA tensors; the stream is the current
+torch stream unless one is given.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import _build
+
+FSE_OK, FSE_EINVAL, FSE_ENOMEM, FSE_ECUDA, FSE_ETIMEOUT, FSE_EUNSUPPORTED = range(6)
+FSE_F32, FSE_BF16 = 0, 1
+FSE_MAX_PIX = 128 * 128
+
+ST = dict(MOM_CONVERGED=1 << 0, FIT_CONVERGED=1 << 1, MOM_MAXITER=1 << 2, FIT_MAXITER=1 << 3,
+          NONFINITE=1 << 4, BAD_SIZE=1 << 5, MOM_FAILED=1 << 6, FIT_BOUND=1 << 7,
+          FIT_SINGULAR=1 << 8, NONPOS_FLUX=1 << 9, SIGW_CLAMPED=1 << 10, INIT_FALLBACK=1 << 11,
+          TIMEOUT=1 << 12)
+
+# exported symbols, in the order include/fse.h declares them
+EXPORTS = ["fse_create", "fse_destroy", "fse_last_error", "fse_opts_default", "fse_centroid",
+           "fse_ellipticity", "fse_sersic_fit", "fse_fit_batch", "fse_fit_batch_plain",
+           "fse_fit_batch_host", "fse_sersic_b", "fse_sync_check"]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("size", ctypes.c_size_t), ("tol_pos", ctypes.c_double), ("tol_g", ctypes.c_double),
+                ("tol_sig", ctypes.c_double), ("tol_fit", ctypes.c_double),
+                ("max_iter_mom", ctypes.c_int32), ("max_iter_fit", ctypes.c_int32),
+                ("k_gain", ctypes.c_double), ("sigw_mode", ctypes.c_int32),
+                ("max_pix", ctypes.c_int32), ("n_min", ctypes.c_double), ("n_max", ctypes.c_double),
+                ("re_min", ctypes.c_double), ("re_max_frac", ctypes.c_double),
+                ("lm_lambda0", ctypes.c_double), ("flags", ctypes.c_uint32),
+                ("warps_per_cta", ctypes.c_int32)]
+
+
+RESULT_DTYPE = np.dtype([("x0", "<f4"), ("y0", "<f4"), ("e1", "<f4"), ("e2", "<f4"), ("I0", "<f4"),
+                         ("re", "<f4"), ("n", "<f4"), ("flux", "<f4"), ("chi2", "<f8"),
+                         ("npix", "<i4"), ("it_mom", "<i4"), ("it_fit", "<i4"), ("status", "<u4"),
+                         ("sigma_w", "<f4"), ("r50", "<f4")])
+assert RESULT_DTYPE.itemsize == 64
+STAMP_DTYPE = np.dtype([("offset", "<i8"), ("h", "<i4"), ("w", "<i4")])
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True) -> ctypes.CDLL:
+    """Load libfse.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libfse.so not found at {path}; run paper_1203_0571_gb300._build.build()")
+    L = ctypes.CDLL(path)
+    L.fse_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int]
+    L.fse_destroy.argtypes = [_vp]
+    L.fse_destroy.restype = None
+    L.fse_last_error.argtypes = [_vp]
+    L.fse_last_error.restype = ctypes.c_char_p
+    L.fse_opts_default.argtypes = [ctypes.POINTER(Opts)]
+    L.fse_opts_default.restype = None
+    dev_sig = [_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int64, _vp, ctypes.POINTER(Opts), _vp, _vp]
+    for f in ("fse_centroid", "fse_ellipticity", "fse_sersic_fit", "fse_fit_batch",
+              "fse_fit_batch_plain"):
+        getattr(L, f).argtypes = dev_sig
+        getattr(L, f).restype = ctypes.c_int
+    L.fse_fit_batch_host.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int, _vp, _vp,
+                                     ctypes.c_int64, _vp, ctypes.POINTER(Opts), _vp, _vp]
+    L.fse_fit_batch_host.restype = ctypes.c_int
+    L.fse_sersic_b.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, _vp]
+    L.fse_sersic_b.restype = ctypes.c_int
+    L.fse_sync_check.argtypes = [_vp, _vp]
+    L.fse_sync_check.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    load().fse_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(f"fse_opts has no field {k}")
+        setattr(o, k, v)
+    return o
+
+
+class FseError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libfse error {code}: {msg}")
+        self.code = code
+
+
+def make_index(offset, h, w, device="cuda") -> torch.Tensor:
+    """fse_stamp array as an int64 tensor [N, 2]: (offset, h | w << 32)."""
+    off = torch.as_tensor(offset, dtype=torch.int64)
+    hh = torch.as_tensor(h, dtype=torch.int64)
+    ww = torch.as_tensor(w, dtype=torch.int64)
+    return torch.stack([off, hh | (ww << 32)], dim=1).contiguous().to(device)
+
+
+def results(out: torch.Tensor) -> np.ndarray:
+    """Copy a result tensor (uint8 [N, 64]) to a numpy structured array."""
+    return out.detach().cpu().contiguous().numpy().view(RESULT_DTYPE).reshape(-1)
+
+
+def _stream(stream) -> _vp:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return _vp(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t):
+    return None if t is None else _vp(t.data_ptr())
+
+
+def _dtype_of(pix: torch.Tensor) -> int:
+    if pix.dtype == torch.float32:
+        return FSE_F32
+    if pix.dtype == torch.bfloat16:
+        return FSE_BF16
+    raise TypeError("pixels must be float32 or bfloat16")
+
+
+class Context:
+    """An fse_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        L = load()
+        h = _vp()
+        rc = L.fse_create(ctypes.byref(h), int(device))
+        if rc != FSE_OK:
+            raise FseError(rc, f"fse_create(device={device}) failed")
+        self._h = h
+        self.device = int(device)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().fse_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int):
+        if rc != FSE_OK:
+            raise FseError(rc, load().fse_last_error(self._h).decode())
+
+    def _dev_call(self, fname, pix, index, out, scale, inv_var, opts, stream):
+        n = int(index.shape[0])
+        if out is None:
+            out = torch.zeros((n, 64), dtype=torch.uint8, device=pix.device)
+        rc = getattr(load(), fname)(self._h, _ptr(pix), _dtype_of(pix), _ptr(scale), _ptr(index), n,
+                                    _ptr(inv_var), ctypes.byref(opts or default_opts()), _ptr(out),
+                                    _stream(stream))
+        self._check(rc)
+        return out
+
+    # --- the C ABI, one method per entry point --------------------------------
+    def centroid(self, pix, index, *, scale=None, inv_var=None, opts=None, out=None, stream=None):
+        """fse_centroid: Sec. 2 centroid. Returns the result tensor (uint8 [N, 64])."""
+        return self._dev_call("fse_centroid", pix, index, out, scale, inv_var, opts, stream)
+
+    def ellipticity(self, pix, index, inout, *, scale=None, inv_var=None, opts=None, stream=None):
+        """fse_ellipticity: Secs. 2-3 from inout's centre and sigma_w (in place)."""
+        return self._dev_call("fse_ellipticity", pix, index, inout, scale, inv_var, opts, stream)
+
+    def sersic_fit(self, pix, index, inout, *, scale=None, inv_var=None, opts=None, stream=None):
+        """fse_sersic_fit: Sec. 4.1 fit with inout's centre and ellipticity (in place)."""
+        return self._dev_call("fse_sersic_fit", pix, index, inout, scale, inv_var, opts, stream)
+
+    def fit_batch(self, pix, index, *, scale=None, inv_var=None, opts=None, out=None, stream=None):
+        """fse_fit_batch: the whole chain in one persistent launch."""
+        return self._dev_call("fse_fit_batch", pix, index, out, scale, inv_var, opts, stream)
+
+    def fit_batch_plain(self, pix, index, *, scale=None, inv_var=None, opts=None, out=None,
+                        stream=None):
+        """fse_fit_batch_plain: the same chain, one launch per stamp."""
+        return self._dev_call("fse_fit_batch_plain", pix, index, out, scale, inv_var, opts, stream)
+
+    def fit_batch_host(self, pix: np.ndarray | torch.Tensor, index: np.ndarray | torch.Tensor, *,
+                       scale=None, inv_var=None, opts=None, out=None, stream=None) -> np.ndarray:
+        """fse_fit_batch_host: host buffers in, host results out (synchronous)."""
+        if isinstance(pix, torch.Tensor):
+            assert pix.device.type == "cpu" and pix.is_contiguous()
+            dtype = _dtype_of(pix)
+            pix_ptr, npix = pix.data_ptr(), pix.numel()
+        else:
+            assert pix.dtype == np.float32 and pix.flags.c_contiguous
+            dtype, pix_ptr, npix = FSE_F32, pix.ctypes.data, pix.size
+        idx_ptr, n = (index.data_ptr(), index.shape[0]) if isinstance(index, torch.Tensor) else \
+            (index.ctypes.data, index.shape[0])
+        if out is None:
+            out = np.zeros(n, dtype=RESULT_DTYPE)
+        out_ptr = out.data_ptr() if isinstance(out, torch.Tensor) else out.ctypes.data
+        sp = None if scale is None else _vp(scale.data_ptr() if isinstance(scale, torch.Tensor)
+                                             else scale.ctypes.data)
+        ivp = None if inv_var is None else _vp(inv_var.data_ptr() if isinstance(inv_var, torch.Tensor)
+                                                else inv_var.ctypes.data)
+        rc = load().fse_fit_batch_host(self._h, _vp(pix_ptr), int(npix), dtype, sp, _vp(idx_ptr),
+                                       int(n), ivp, ctypes.byref(opts or default_opts()),
+                                       _vp(out_ptr), _stream(stream))
+        self._check(rc)
+        return out
+
+    def sersic_b(self, n: torch.Tensor, stream=None):
+        """fse_sersic_b: (b(n), b'(n)) from the device table, float64 CUDA tensors."""
+        n = n.to(torch.float64).contiguous()
+        b = torch.empty_like(n)
+        db = torch.empty_like(n)
+        self._check(load().fse_sersic_b(self._h, _ptr(n), _ptr(b), _ptr(db), n.numel(),
+                                        _stream(stream)))
+        return b, db
+
+    def sync_check(self, stream=None):
+        """fse_sync_check: wait for the stream and raise if a bounded device wait expired."""
+        self._check(load().fse_sync_check(self._h, _stream(stream)))
+
+
+# module-level forms with the ABI's names (context first)
+def fse_centroid(ctx: Context, *a, **k):
+    return ctx.centroid(*a, **k)
+
+
+def fse_ellipticity(ctx: Context, *a, **k):
+    return ctx.ellipticity(*a, **k)
+
+
+def fse_sersic_fit(ctx: Context, *a, **k):
+    return ctx.sersic_fit(*a, **k)
+
+
+def fse_fit_batch(ctx: Context, *a, **k):
+    return ctx.fit_batch(*a, **k)
+
+
+def fse_fit_batch_plain(ctx: Context, *a, **k):
+    return ctx.fit_batch_plain(*a, **k)
+
+
+def fse_fit_batch_host(ctx: Context, *a, **k):
+    return ctx.fit_batch_host(*a, **k)
+
+
+def fse_sersic_b(ctx: Context, *a, **k):
+    return ctx.sersic_b(*a, **k)
+
+
+def fse_sync_check(ctx: Context, *a, **k):
+    return ctx.sync_check(*a, **k)

@@ -1,0 +1,471 @@
+// fse_api.cu -- the C ABI of libfse (declared in include/fse.h): context,
+// argument checks, launch selection, the host-buffer pipeline and the
+// per-stamp launch form.  No computation of the method happens here; every
+// step of the estimator runs in the kernels of fse_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "fse.h"
+#include "fse_internal.h"
+
+struct fse_ctx {
+    int device = 0;
+    char err[512] = {0};
+    unsigned int* d_queue = nullptr;   // kQueues work counters
+    unsigned int* d_err = nullptr;     // sticky error word written by the kernels
+    unsigned next_queue = 0;
+    cudaStream_t aux_stream = nullptr; // second stream of the host-buffer pipeline
+    // grow-only device staging of fse_fit_batch_host
+    void* d_pix = nullptr;
+    size_t pix_cap = 0;
+    fse_stamp* d_idx = nullptr;
+    size_t idx_cap = 0;
+    fse_result* d_out = nullptr;
+    size_t out_cap = 0;
+    float* d_scale = nullptr;
+    size_t scale_cap = 0;
+    float* d_ivar = nullptr;
+    size_t ivar_cap = 0;
+};
+
+namespace {
+
+constexpr int kQueues = 64;
+std::mutex g_table_mutex;
+bool g_table_built[256];
+
+int set_error(fse_ctx* ctx, int code, const char* fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof ctx->err, fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int cuda_fail(fse_ctx* ctx, cudaError_t e, const char* what) {
+    return set_error(ctx, FSE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Makes ctx->device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int check_opts(fse_ctx* ctx, const fse_opts* o) {
+    if (o->size != sizeof(fse_opts)) return set_error(ctx, FSE_EINVAL, "opts.size must be sizeof(fse_opts)");
+    if (!(o->tol_pos > 0 && o->tol_g > 0 && o->tol_sig > 0 && o->tol_fit > 0))
+        return set_error(ctx, FSE_EINVAL, "tolerances must be positive");
+    if (o->max_iter_mom < 1 || o->max_iter_mom > 100000 || o->max_iter_fit < 1 || o->max_iter_fit > 100000)
+        return set_error(ctx, FSE_EINVAL, "max_iter must be in [1, 100000]");
+    if (!(o->k_gain > 0 && o->k_gain <= 4)) return set_error(ctx, FSE_EINVAL, "k_gain must be in (0, 4]");
+    if (o->sigw_mode != 0 && o->sigw_mode != 1) return set_error(ctx, FSE_EINVAL, "sigw_mode must be 0 or 1");
+    if (o->max_pix < 0 || o->max_pix > FSE_MAX_PIX)
+        return set_error(ctx, FSE_EINVAL, "max_pix must be in [0, %d]", FSE_MAX_PIX);
+    const double tab_lo = fse::kBnLo + 2 * fse::kBnStep;
+    const double tab_hi = fse::kBnLo + (fse::kBnNodes - 3) * fse::kBnStep;
+    if (!(o->n_min >= tab_lo && o->n_max <= tab_hi && o->n_min < o->n_max))
+        return set_error(ctx, FSE_EINVAL, "n bounds must satisfy %.4f <= n_min < n_max <= %.4f", tab_lo, tab_hi);
+    if (!(o->re_min > 0 && o->re_max_frac > 0)) return set_error(ctx, FSE_EINVAL, "r_e bounds must be positive");
+    if (!(o->lm_lambda0 > 0)) return set_error(ctx, FSE_EINVAL, "lm_lambda0 must be positive");
+    const int w = o->warps_per_cta;
+    if (!(w == 0 || w == 1 || w == 2 || w == 4 || w == 8 || w == 16))
+        return set_error(ctx, FSE_EINVAL, "warps_per_cta must be 0, 1, 2, 4, 8 or 16");
+    return FSE_OK;
+}
+
+fse::DevOpts dev_opts(const fse_opts& o) {
+    fse::DevOpts d;
+    d.tol_pos = static_cast<float>(o.tol_pos);
+    d.tol_g = static_cast<float>(o.tol_g);
+    d.tol_sig = static_cast<float>(o.tol_sig);
+    d.tol_fit = static_cast<float>(o.tol_fit);
+    d.max_iter_mom = o.max_iter_mom;
+    d.max_iter_fit = o.max_iter_fit;
+    d.k_gain = static_cast<float>(o.k_gain);
+    d.sigw_mode = o.sigw_mode;
+    d.max_pix = o.max_pix > 0 ? o.max_pix : FSE_MAX_PIX;
+    d.n_min = static_cast<float>(o.n_min);
+    d.n_max = static_cast<float>(o.n_max);
+    d.re_min = static_cast<float>(o.re_min);
+    d.re_max_frac = static_cast<float>(o.re_max_frac);
+    d.lm_lambda0 = static_cast<float>(o.lm_lambda0);
+    return d;
+}
+
+int default_warps(int max_pix) {
+    int wpc = 0, per_sm = 0;
+    fse::choose_launch(max_pix, &wpc, &per_sm);
+    return wpc;
+}
+
+// Common checks of the device entry points; fills `a` on success.
+int prepare(fse_ctx* ctx, const void* pix, int dtype, const float* scale, const fse_stamp* idx,
+            int64_t count, const float* inv_var, const fse_opts* opts, fse_result* out, int stage,
+            fse::LaunchArgs* a) {
+    if (!ctx) return FSE_EINVAL;
+    if (count < 0 || count > 0x7fffffffLL) return set_error(ctx, FSE_EINVAL, "count out of range");
+    if (dtype != FSE_F32 && dtype != FSE_BF16) return set_error(ctx, FSE_EINVAL, "unknown dtype %d", dtype);
+    fse_opts def;
+    fse_opts_default(&def);
+    const fse_opts& o = opts ? *opts : def;
+    int rc = check_opts(ctx, &o);
+    if (rc) return rc;
+    if (count > 0) {
+        if (!pix || !idx || !out) return set_error(ctx, FSE_EINVAL, "pix, idx and out must not be NULL");
+        if (!is_device_ptr(pix) || !is_device_ptr(idx) || !is_device_ptr(out) ||
+            (scale && !is_device_ptr(scale)) || (inv_var && !is_device_ptr(inv_var)))
+            return set_error(ctx, FSE_EINVAL, "pix, scale, idx, inv_var and out must be device pointers");
+    }
+    memset(a, 0, sizeof *a);
+    a->pix = pix;
+    a->dtype = dtype;
+    a->scale = scale;
+    a->idx = idx;
+    a->count = count;
+    a->inv_var = inv_var;
+    a->out = out;
+    a->err = ctx->d_err;
+    a->opts = dev_opts(o);
+    a->stage = stage;
+    a->warps_per_cta = o.warps_per_cta > 0 ? o.warps_per_cta : default_warps(a->opts.max_pix);
+    return FSE_OK;
+}
+
+int run(fse_ctx* ctx, fse::LaunchArgs& a, cudaStream_t stream) {
+    if (a.count == 0) return FSE_OK;
+    a.queue = ctx->d_queue + (ctx->next_queue++ % kQueues);
+    cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "work counter reset");
+    e = fse::launch_estimator(a, stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "estimator launch");
+    return FSE_OK;
+}
+
+int stage_entry(fse_ctx* ctx, const void* pix, int dtype, const float* scale, const fse_stamp* idx,
+                int64_t count, const float* inv_var, const fse_opts* opts, fse_result* out,
+                void* stream, int stage) {
+    if (!ctx) return FSE_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return set_error(ctx, FSE_ECUDA, "cannot select device %d", ctx->device);
+    fse::LaunchArgs a;
+    int rc = prepare(ctx, pix, dtype, scale, idx, count, inv_var, opts, out, stage, &a);
+    if (rc) return rc;
+    return run(ctx, a, static_cast<cudaStream_t>(stream));
+}
+
+template <typename T>
+int grow(fse_ctx* ctx, T** p, size_t* cap, size_t n) {
+    if (n <= *cap) return FSE_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(ctx, FSE_ENOMEM, "device staging of %zu bytes: %s", n * sizeof(T),
+                         cudaGetErrorString(e));
+    }
+    *cap = n;
+    return FSE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fse_opts_default(fse_opts* o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->size = sizeof(fse_opts);
+    o->tol_pos = 1e-6;
+    o->tol_g = 1e-6;
+    o->tol_sig = 1e-6;
+    o->tol_fit = 1e-6;
+    o->max_iter_mom = 60;
+    o->max_iter_fit = 60;
+    o->k_gain = 0.75;
+    o->sigw_mode = 1;
+    o->max_pix = 0;
+    o->n_min = 0.2;
+    o->n_max = 10.0;
+    o->re_min = 0.2;
+    o->re_max_frac = 2.0;
+    o->lm_lambda0 = 1e-3;
+    o->flags = 0;
+    o->warps_per_cta = 0;
+}
+
+int fse_create(fse_ctx** out, int device) {
+    if (!out) return FSE_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev || device >= 256) {
+        cudaGetLastError();
+        return FSE_EINVAL;
+    }
+    fse_ctx* ctx = new fse_ctx();
+    ctx->device = device;
+    DeviceGuard g(device);
+    if (!g.ok) { delete ctx; return FSE_ECUDA; }
+    if (cudaMalloc(&ctx->d_queue, kQueues * sizeof(unsigned int)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_err, sizeof(unsigned int)) != cudaSuccess) {
+        cudaGetLastError();
+        fse_destroy(ctx);
+        return FSE_ENOMEM;
+    }
+    if (cudaMemset(ctx->d_err, 0, sizeof(unsigned int)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        fse_destroy(ctx);
+        return FSE_ECUDA;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_table_mutex);
+        if (!g_table_built[device]) {
+            cudaError_t e = fse::build_bn_table(nullptr);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                fse_destroy(ctx);
+                return FSE_ECUDA;
+            }
+            g_table_built[device] = true;
+        }
+    }
+    *out = ctx;
+    return FSE_OK;
+}
+
+void fse_destroy(fse_ctx* ctx) {
+    if (!ctx) return;
+    {
+        DeviceGuard g(ctx->device);
+        cudaDeviceSynchronize();
+        cudaFree(ctx->d_queue);
+        cudaFree(ctx->d_err);
+        cudaFree(ctx->d_pix);
+        cudaFree(ctx->d_idx);
+        cudaFree(ctx->d_out);
+        cudaFree(ctx->d_scale);
+        cudaFree(ctx->d_ivar);
+        if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+        cudaGetLastError();
+    }
+    delete ctx;
+}
+
+const char* fse_last_error(const fse_ctx* ctx) { return ctx ? ctx->err : "null context"; }
+
+int fse_centroid(fse_ctx* ctx, const void* pix, int dtype, const float* scale, const fse_stamp* idx,
+                 int64_t count, const float* inv_var, const fse_opts* opts, fse_result* out,
+                 void* stream) {
+    return stage_entry(ctx, pix, dtype, scale, idx, count, inv_var, opts, out, stream,
+                       fse::kStageCentroid);
+}
+
+int fse_ellipticity(fse_ctx* ctx, const void* pix, int dtype, const float* scale,
+                    const fse_stamp* idx, int64_t count, const float* inv_var, const fse_opts* opts,
+                    fse_result* inout, void* stream) {
+    return stage_entry(ctx, pix, dtype, scale, idx, count, inv_var, opts, inout, stream,
+                       fse::kStageEllipticity);
+}
+
+int fse_sersic_fit(fse_ctx* ctx, const void* pix, int dtype, const float* scale,
+                   const fse_stamp* idx, int64_t count, const float* inv_var, const fse_opts* opts,
+                   fse_result* inout, void* stream) {
+    return stage_entry(ctx, pix, dtype, scale, idx, count, inv_var, opts, inout, stream,
+                       fse::kStageFit);
+}
+
+int fse_fit_batch(fse_ctx* ctx, const void* pix, int dtype, const float* scale, const fse_stamp* idx,
+                  int64_t count, const float* inv_var, const fse_opts* opts, fse_result* out,
+                  void* stream) {
+    return stage_entry(ctx, pix, dtype, scale, idx, count, inv_var, opts, out, stream,
+                       fse::kStageAll);
+}
+
+int fse_fit_batch_plain(fse_ctx* ctx, const void* pix, int dtype, const float* scale,
+                        const fse_stamp* idx, int64_t count, const float* inv_var,
+                        const fse_opts* opts, fse_result* out, void* stream) {
+    if (!ctx) return FSE_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return set_error(ctx, FSE_ECUDA, "cannot select device %d", ctx->device);
+    fse::LaunchArgs a;
+    int rc = prepare(ctx, pix, dtype, scale, idx, count, inv_var, opts, out, fse::kStageAll, &a);
+    if (rc) return rc;
+    a.warps_per_cta = 1;
+    a.num_ctas = 1;
+    a.static_assign = 1;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int64_t i = 0; i < count; ++i) {
+        fse::LaunchArgs b = a;
+        b.idx = idx + i;
+        b.out = out + i;
+        b.count = 1;
+        b.scale = scale ? scale + i : nullptr;
+        cudaError_t e = fse::launch_estimator(b, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "per-stamp launch");
+    }
+    return FSE_OK;
+}
+
+int fse_fit_batch_host(fse_ctx* ctx, const void* pix, int64_t npix_total, int dtype,
+                       const float* scale, const fse_stamp* idx, int64_t count,
+                       const float* inv_var, const fse_opts* opts, fse_result* out, void* stream) {
+    if (!ctx) return FSE_EINVAL;
+    if (count == 0) return FSE_OK;
+    if (!pix || !idx || !out || count < 0 || count > 0x7fffffffLL || npix_total < 0)
+        return set_error(ctx, FSE_EINVAL, "bad host arguments");
+    if (dtype != FSE_F32 && dtype != FSE_BF16) return set_error(ctx, FSE_EINVAL, "unknown dtype %d", dtype);
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return set_error(ctx, FSE_ECUDA, "cannot select device %d", ctx->device);
+    fse_opts o;
+    if (opts) o = *opts; else fse_opts_default(&o);
+    int rc = check_opts(ctx, &o);
+    if (rc) return rc;
+    const size_t esz = dtype == FSE_BF16 ? 2 : 4;
+    // tile size from the index, and every stamp inside the buffer
+    int64_t maxp = 1;
+    for (int64_t s = 0; s < count; ++s) {
+        const int64_t a = static_cast<int64_t>(idx[s].h) * idx[s].w;
+        if (idx[s].h >= 1 && idx[s].w >= 1 && a <= FSE_MAX_PIX) {
+            if (idx[s].offset < 0 || idx[s].offset + a > npix_total)
+                return set_error(ctx, FSE_EINVAL, "stamp %lld lies outside the pixel buffer", (long long)s);
+            maxp = std::max(maxp, a);
+        }
+    }
+    if (o.max_pix == 0) o.max_pix = static_cast<int32_t>(maxp);
+    if ((rc = grow(ctx, reinterpret_cast<char**>(&ctx->d_pix), &ctx->pix_cap, npix_total * esz)) ||
+        (rc = grow(ctx, &ctx->d_idx, &ctx->idx_cap, count)) ||
+        (rc = grow(ctx, &ctx->d_out, &ctx->out_cap, count)) ||
+        (scale && (rc = grow(ctx, &ctx->d_scale, &ctx->scale_cap, count))) ||
+        (inv_var && (rc = grow(ctx, &ctx->d_ivar, &ctx->ivar_cap, npix_total))))
+        return rc;
+    const cudaStream_t s0 = static_cast<cudaStream_t>(stream);
+    const cudaStream_t streams[2] = {s0, ctx->aux_stream};
+    cudaEvent_t ev0, ev1;
+    cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&ev1, cudaEventDisableTiming);
+    cudaEventRecord(ev0, s0);
+    cudaStreamWaitEvent(ctx->aux_stream, ev0, 0);
+    // chunks of consecutive stamps; each chunk copies the pixel span it covers
+    const int64_t nchunk = std::min<int64_t>(count, count >= 8192 ? 8 : 1);
+    const int64_t per = (count + nchunk - 1) / nchunk;
+    cudaError_t e = cudaSuccess;
+    for (int64_t c = 0; c < nchunk && e == cudaSuccess; ++c) {
+        const int64_t s_lo = c * per, s_hi = std::min(count, s_lo + per);
+        if (s_lo >= s_hi) break;
+        int64_t p_lo = INT64_MAX, p_hi = 0;
+        for (int64_t s = s_lo; s < s_hi; ++s) {
+            const int64_t a = static_cast<int64_t>(idx[s].h) * idx[s].w;
+            if (idx[s].h < 1 || idx[s].w < 1 || a > FSE_MAX_PIX) continue;
+            p_lo = std::min(p_lo, idx[s].offset);
+            p_hi = std::max(p_hi, idx[s].offset + a);
+        }
+        const cudaStream_t st = streams[c & 1];
+        e = cudaMemcpyAsync(ctx->d_idx + s_lo, idx + s_lo, (s_hi - s_lo) * sizeof(fse_stamp),
+                            cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && p_hi > p_lo)
+            e = cudaMemcpyAsync(static_cast<char*>(ctx->d_pix) + p_lo * esz,
+                                static_cast<const char*>(pix) + p_lo * esz, (p_hi - p_lo) * esz,
+                                cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && scale)
+            e = cudaMemcpyAsync(ctx->d_scale + s_lo, scale + s_lo, (s_hi - s_lo) * sizeof(float),
+                                cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && inv_var && p_hi > p_lo)
+            e = cudaMemcpyAsync(ctx->d_ivar + p_lo, inv_var + p_lo, (p_hi - p_lo) * sizeof(float),
+                                cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) break;
+        fse::LaunchArgs a;
+        memset(&a, 0, sizeof a);
+        a.pix = ctx->d_pix;
+        a.dtype = dtype;
+        a.scale = scale ? ctx->d_scale + s_lo : nullptr;
+        a.idx = ctx->d_idx + s_lo;
+        a.count = s_hi - s_lo;
+        a.inv_var = inv_var ? ctx->d_ivar : nullptr;
+        a.out = ctx->d_out + s_lo;
+        a.err = ctx->d_err;
+        a.opts = dev_opts(o);
+        a.stage = fse::kStageAll;
+        a.warps_per_cta = o.warps_per_cta > 0 ? o.warps_per_cta : default_warps(a.opts.max_pix);
+        rc = run(ctx, a, st);
+        if (rc) {
+            cudaEventDestroy(ev0);
+            cudaEventDestroy(ev1);
+            return rc;
+        }
+        e = cudaMemcpyAsync(out + s_lo, ctx->d_out + s_lo, (s_hi - s_lo) * sizeof(fse_result),
+                            cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev1, ctx->aux_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, ev1, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s0);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "host-buffer pipeline");
+    unsigned int flag = 0;
+    e = cudaMemcpy(&flag, ctx->d_err, sizeof flag, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "error word read");
+    if (flag) {
+        cudaMemset(ctx->d_err, 0, sizeof(unsigned int));
+        return set_error(ctx, FSE_ETIMEOUT, "a bounded device wait expired");
+    }
+    return FSE_OK;
+}
+
+int fse_sersic_b(fse_ctx* ctx, const double* n, double* b, double* db, int64_t count, void* stream) {
+    if (!ctx) return FSE_EINVAL;
+    if (count == 0) return FSE_OK;
+    if (count < 0 || !n || !b) return set_error(ctx, FSE_EINVAL, "bad arguments");
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return set_error(ctx, FSE_ECUDA, "cannot select device %d", ctx->device);
+    if (!is_device_ptr(n) || !is_device_ptr(b) || (db && !is_device_ptr(db)))
+        return set_error(ctx, FSE_EINVAL, "n, b and db must be device pointers");
+    cudaError_t e = fse::eval_bn(n, b, db, count, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "b(n) evaluation");
+    return FSE_OK;
+}
+
+int fse_sync_check(fse_ctx* ctx, void* stream) {
+    if (!ctx) return FSE_EINVAL;
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronise");
+    unsigned int flag = 0;
+    e = cudaMemcpy(&flag, ctx->d_err, sizeof flag, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "error word read");
+    if (flag) {
+        cudaMemset(ctx->d_err, 0, sizeof(unsigned int));
+        return set_error(ctx, FSE_ETIMEOUT, "a bounded device wait expired");
+    }
+    return FSE_OK;
+}
+
+}  // extern "C"

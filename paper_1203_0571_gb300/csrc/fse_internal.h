@@ -1,0 +1,64 @@
+// Internal interface between the C ABI layer (fse_api.cu) and the kernels
+// (fse_kernels.cu).  Not installed; the public interface is include/fse.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fse.h"
+
+namespace fse {
+
+// Which part of the chain a launch runs.
+enum Stage : int {
+    kStageCentroid = 1,     // start-up + Sec. 2 centroid (circular weight)
+    kStageEllipticity = 2,  // Secs. 2-3 from a given centre and sigma_w
+    kStageFit = 3,          // Sec. 4.1 fit with centre and g fixed
+    kStageAll = 4,          // whole chain
+};
+
+// Options as the kernels see them (fp32 where the per-pixel code uses them).
+struct DevOpts {
+    float tol_pos, tol_g, tol_sig, tol_fit;
+    int max_iter_mom, max_iter_fit;
+    float k_gain;
+    int sigw_mode;
+    int max_pix;
+    float n_min, n_max, re_min, re_max_frac;
+    float lm_lambda0;
+};
+
+struct LaunchArgs {
+    const void* pix;
+    int dtype;
+    const float* scale;
+    const fse_stamp* idx;
+    int64_t count;
+    const float* inv_var;
+    fse_result* out;
+    unsigned int* queue;     // persistent-kernel work counter (zeroed before launch)
+    unsigned int* err;       // sticky error word (bounded waits that expired)
+    DevOpts opts;
+    int stage;
+    int warps_per_cta;
+    int num_ctas;            // 0 = library choice
+    int static_assign;       // 1: warp w of the grid takes stamp w only (no counter)
+};
+
+// Number of nodes of the b(n) table and its range.
+constexpr double kBnLo = 0.125;
+constexpr double kBnStep = 1.0 / 256.0;
+constexpr int kBnNodes = 2600;   // covers [0.125, 10.27]
+
+// Builds the b(n), b'(n) table of the current device (idempotent per device).
+cudaError_t build_bn_table(cudaStream_t stream);
+// Evaluates the table at count points (device arrays).
+cudaError_t eval_bn(const double* n, double* b, double* db, int64_t count, cudaStream_t stream);
+// Launches the estimator kernel; returns the launch error.
+cudaError_t launch_estimator(const LaunchArgs& a, cudaStream_t stream);
+// Shared memory a warp needs for stamps of up to max_pix pixels.
+size_t smem_per_warp(int max_pix);
+// Largest warps-per-CTA / CTAs-per-SM choice for a tile size.
+void choose_launch(int max_pix, int* warps_per_cta, int* ctas_per_sm);
+
+}  // namespace fse

@@ -1,0 +1,1020 @@
+// fse_kernels.cu -- sm_103a kernels of the fast shape estimator
+// (Li, Xin & Cui 2012): weighted-moment centroid (Sec. 2), KSB ellipticity
+// with an elliptical weight (Sec. 3, Appendices A and B) and the Sérsic
+// profile fit with I0 at its closed form (Sec. 4.1, Eqs. 10-13).
+//
+// Execution model: one persistent launch; every warp owns one stamp at a time
+// and takes the next from an atomic work counter.  The stamp is staged once
+// HBM -> shared memory (1-D TMA bulk copy for its 16-byte-aligned body, plain
+// loads for the ragged ends) and every later pass (start-up, moment
+// iterations, fit iterations) reads shared memory only.  Per pixel the work is
+// fp32 (MUFU ex2 for the weight and the profile); per-lane partial sums are
+// reduced with xor shuffles, which give every lane the same total, so all
+// lanes run the scalar update redundantly and stay in lock-step.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "fse_internal.h"
+
+namespace fse {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr double kLn2 = 0.6931471805599453;
+constexpr double kSqrt2Ln2 = 1.1774100225154747;   // half-light radius / sigma of a Gaussian
+constexpr double kPi = 3.141592653589793;
+constexpr unsigned kWaitLimit = 1u << 22;          // bounded mbarrier polls
+
+// (b(n), b'(n)) at n_k = kBnLo + k kBnStep, built once per device.
+__device__ double2 g_bn[kBnNodes];
+
+// ------------------------------------------------------------------ PTX
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_bulk_load(void* dst, const void* src, uint32_t bytes,
+                                              uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// ------------------------------------------------------------------ reductions
+template <int N>
+__device__ __forceinline__ void warp_allsum(float (&v)[N]) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[i] += __shfl_xor_sync(kFull, v[i], off);
+    }
+}
+
+__device__ __forceinline__ long long warp_allsum_ll(long long v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+    return v;
+}
+
+// ------------------------------------------------------------------ b(n)
+// Digamma for z > 0: recurrence up to z >= 10, then the asymptotic series
+// psi(z) ~ ln z - 1/(2z) - sum B_2k / (2k z^2k) (Abramowitz & Stegun 6.3.18).
+__device__ double digamma(double z) {
+    double acc = 0.0;
+    while (z < 10.0) {
+        acc -= 1.0 / z;
+        z += 1.0;
+    }
+    const double r = 1.0 / (z * z);
+    const double tail =
+        r * (1.0 / 12 - r * (1.0 / 120 - r * (1.0 / 252 - r * (1.0 / 240 - r * (1.0 / 132)))));
+    return acc + log(z) - 0.5 / z - tail;
+}
+
+// P(a, x) (regularised lower incomplete gamma) and dP/da from the series
+// P = sum_k T_k, T_k = x^(a+k) e^-x / Gamma(a+k+1), with
+// dT_k/da = T_k (ln x - psi(a+k+1)) and psi(a+k+1) = psi(a+k) + 1/(a+k).
+__device__ void gamma_p_series(double a, double x, double* P, double* dPda) {
+    const double lx = log(x);
+    double T = exp(a * lx - x - lgamma(a + 1.0));
+    double psi = digamma(a + 1.0);
+    double sum = T, dsum = T * (lx - psi);
+    for (int k = 1; k < 4000; ++k) {
+        T *= x / (a + k);
+        psi += 1.0 / (a + k);
+        sum += T;
+        dsum += T * (lx - psi);
+        if (T < 1e-18 * sum) break;
+    }
+    *P = sum;
+    *dPda = dsum;
+}
+
+// b(n): Newton on P(2n, b) = 1/2 from the large-n expansion, kept inside the
+// bracket (0, 2n) (the median of Gamma(2n) lies below its mean).  b'(n) by
+// implicit differentiation: b' = -dP/dn / dP/db = -2 dP/da / (b^(a-1) e^-b / Gamma(a)).
+__global__ void build_bn_kernel() {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= kBnNodes) return;
+    const double n = kBnLo + k * kBnStep;
+    const double a = 2.0 * n;
+    double lo = 0.0, hi = a;
+    double b = a - 1.0 / 3.0 + 4.0 / (405.0 * n);
+    if (!(b > lo && b < hi)) b = 0.5 * a;
+    double P = 0.0, dPda = 0.0;
+    for (int it = 0; it < 100; ++it) {
+        gamma_p_series(a, b, &P, &dPda);
+        const double f = P - 0.5;
+        if (f > 0.0) hi = b; else lo = b;
+        const double dPdx = exp((a - 1.0) * log(b) - b - lgamma(a));
+        double nb = b - f / dPdx;
+        if (!(nb > lo && nb < hi)) nb = 0.5 * (lo + hi);
+        const bool done = fabs(nb - b) <= 4e-16 * b;
+        b = nb;
+        if (done) break;
+    }
+    gamma_p_series(a, b, &P, &dPda);
+    const double dPdx = exp((a - 1.0) * log(b) - b - lgamma(a));
+    g_bn[k] = make_double2(b, -2.0 * dPda / dPdx);
+}
+
+// Cubic Hermite interpolation of the table (b from b and b' at the nodes;
+// b' as the derivative of that cubic).
+__device__ __forceinline__ void bn_eval(double n, double* b, double* db) {
+    double x = (n - kBnLo) * (1.0 / kBnStep);
+    int k = static_cast<int>(floor(x));
+    k = k < 0 ? 0 : (k > kBnNodes - 2 ? kBnNodes - 2 : k);
+    const double t = x - k;
+    const double2 p0 = g_bn[k], p1 = g_bn[k + 1];
+    const double h = kBnStep;
+    const double t2 = t * t, t3 = t2 * t;
+    *b = (2 * t3 - 3 * t2 + 1) * p0.x + (t3 - 2 * t2 + t) * h * p0.y + (-2 * t3 + 3 * t2) * p1.x +
+         (t3 - t2) * h * p1.y;
+    *db = ((6 * t2 - 6 * t) * p0.x + (3 * t2 - 4 * t + 1) * h * p0.y + (-6 * t2 + 6 * t) * p1.x +
+           (3 * t2 - 2 * t) * h * p1.y) /
+          h;
+}
+
+__global__ void eval_bn_kernel(const double* n, double* b, double* db, int64_t count) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    double bb, dd;
+    bn_eval(n[i], &bb, &dd);
+    b[i] = bb;
+    if (db) db[i] = dd;
+}
+
+// ------------------------------------------------------------------ per-warp layout
+// [pixels: max_pix + 4 floats][aux: max(max_pix, 512) floats][ivar: max_pix + 4 (opt)][mbarrier]
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+__host__ __device__ inline size_t pix_bytes(int max_pix) { return align16((size_t)(max_pix + 4) * 4); }
+__host__ __device__ inline size_t aux_bytes(int max_pix) {
+    return align16((size_t)(max_pix > 512 ? max_pix : 512) * 4);
+}
+__host__ __device__ inline size_t warp_bytes(int max_pix, bool ivar) {
+    return pix_bytes(max_pix) + aux_bytes(max_pix) + (ivar ? pix_bytes(max_pix) : 0) + 16;
+}
+
+// Pixel iterator: lane handles p = lane, lane + 32, ... of a w-wide stamp.
+struct PixelWalk {
+    int row, col, dr, dc, w;
+    __device__ PixelWalk(int lane, int w_) : w(w_) {
+        row = lane / w;
+        col = lane - row * w;
+        dr = 32 / w;
+        dc = 32 - dr * w;
+    }
+    __device__ __forceinline__ void next() {
+        col += dc;
+        row += dr;
+        if (col >= w) {
+            col -= w;
+            ++row;
+        }
+    }
+};
+
+// Stage a stamp (npix elements at gsrc) into shared memory.  The 16-byte
+// aligned body moves with one bulk TMA copy completing on `bar`; the head
+// and tail are loaded by lanes.  Returns false if the bounded wait expired.
+// Floats: the stamp starts at buf + pad with pad chosen so that the body's
+// shared address is 16-byte aligned too.  BF16: the raw 2-byte values are
+// staged in `raw` first and decoded (times scale) into the float buffer.
+template <int DT>
+__device__ bool stage_stamp(float* buf, float** stamp, float* raw, const void* gsrc, int npix,
+                            float scale, uint64_t* bar, uint32_t* phase, int lane) {
+    constexpr int esz = DT == FSE_BF16 ? 2 : 4;
+    const uintptr_t ga = reinterpret_cast<uintptr_t>(gsrc);
+    int head = static_cast<int>(((16 - (ga & 15)) & 15) / esz);
+    if ((ga & (esz - 1)) != 0) head = npix;          // not element aligned: no TMA
+    if (head > npix) head = npix;
+    constexpr int vec = 16 / esz;
+    const int body = ((npix - head) / vec) * vec;
+    const int tail = head + body;
+    char* dst_base;
+    int pad;
+    if (DT == FSE_BF16) {
+        // raw bf16 staging: element i at raw_bytes + 2*(pad + i), (pad + head) % 8 == 0
+        pad = (8 - (head & 7)) & 7;
+        dst_base = reinterpret_cast<char*>(raw);
+        *stamp = buf;
+    } else {
+        pad = (4 - (head & 3)) & 3;
+        dst_base = reinterpret_cast<char*>(buf);
+        *stamp = buf + pad;
+    }
+    // order this warp's earlier generic-proxy accesses to the buffer before
+    // the async-proxy (TMA) write into it
+    fence_proxy_async();
+    __syncwarp();
+    bool ok = true;
+    if (body > 0) {
+        if (lane == 0) {
+            mbar_expect_tx(bar, static_cast<uint32_t>(body * esz));
+            tma_bulk_load(dst_base + (size_t)(pad + head) * esz,
+                          static_cast<const char*>(gsrc) + (size_t)head * esz,
+                          static_cast<uint32_t>(body * esz), bar);
+        }
+    }
+    if (DT == FSE_BF16) {
+        const __nv_bfloat16* g = static_cast<const __nv_bfloat16*>(gsrc);
+        __nv_bfloat16* r = reinterpret_cast<__nv_bfloat16*>(dst_base) + pad;
+        for (int i = lane; i < head; i += 32) r[i] = g[i];
+        for (int i = tail + lane; i < npix; i += 32) r[i] = g[i];
+    } else {
+        const float* g = static_cast<const float*>(gsrc);
+        float* s = *stamp;
+        for (int i = lane; i < head; i += 32) s[i] = __ldg(g + i);
+        for (int i = tail + lane; i < npix; i += 32) s[i] = __ldg(g + i);
+    }
+    if (body > 0) {
+        ok = false;
+        for (unsigned it = 0; it < kWaitLimit; ++it) {
+            if (mbar_try_wait(bar, *phase & 1u)) {
+                ok = true;
+                break;
+            }
+        }
+        ++*phase;
+    }
+    __syncwarp();
+    if (DT == FSE_BF16) {
+        const __nv_bfloat16* r = reinterpret_cast<const __nv_bfloat16*>(dst_base) + pad;
+        float* s = *stamp;
+        for (int i = lane; i < npix; i += 32) s[i] = __bfloat162float(r[i]) * scale;
+        __syncwarp();
+    }
+    return __all_sync(kFull, ok);
+}
+
+// ------------------------------------------------------------------ moments
+struct MomState {
+    int xi, yi;      // integer part of the centre
+    float xf, yf;    // fractional part, |.| <= 0.5 after renormalisation
+    float g1, g2;    // weight ellipticity g_w
+    float sw;        // weight size sigma_w
+};
+
+// One weighted pass: S0 = sum f W, S1 = sum f W theta, the three second and
+// five fourth moments of f W (f = pixel value).  Everything the centroid step
+// (Eqs. 5-6) and the ellipticity step (Eqs. 8-9 with A5-A6, B7-B14) needs is a
+// linear combination of these eleven sums.
+__device__ __forceinline__ void moment_pass(const float* __restrict__ s, int w, int npix, int lane,
+                                            const MomState& st, float (&acc)[11]) {
+    const float gg = st.g1 * st.g1 + st.g2 * st.g2;
+    const float A = 1.f + gg - 2.f * st.g1;
+    const float B = 1.f + gg + 2.f * st.g1;
+    const float G4 = 4.f * st.g2;
+    const float cw = -kLog2e / (2.f * st.sw * st.sw);
+#pragma unroll
+    for (int i = 0; i < 11; ++i) acc[i] = 0.f;
+    PixelWalk pw(lane, w);
+    const float fxf = st.xf, fyf = st.yf;
+    for (int p = lane; p < npix; p += 32) {
+        const float t1 = static_cast<float>(pw.col - st.xi) - fxf;
+        const float t2 = static_cast<float>(pw.row - st.yi) - fyf;
+        const float t11 = t1 * t1, t22 = t2 * t2, t12 = t1 * t2;
+        const float R2 = fmaf(A, t11, fmaf(B, t22, -G4 * t12));
+        const float f = s[p] * ex2(R2 * cw);
+        acc[0] += f;
+        acc[1] = fmaf(f, t1, acc[1]);
+        acc[2] = fmaf(f, t2, acc[2]);
+        acc[3] = fmaf(f, t11, acc[3]);
+        acc[4] = fmaf(f, t12, acc[4]);
+        acc[5] = fmaf(f, t22, acc[5]);
+        const float f11 = f * t11, f22 = f * t22;
+        acc[6] = fmaf(f11, t11, acc[6]);    // theta1^4
+        acc[7] = fmaf(f11, t12, acc[7]);    // theta1^3 theta2
+        acc[8] = fmaf(f11, t22, acc[8]);    // theta1^2 theta2^2
+        acc[9] = fmaf(f22, t12, acc[9]);    // theta1 theta2^3
+        acc[10] = fmaf(f22, t22, acc[10]);  // theta2^4
+        pw.next();
+    }
+    warp_allsum(acc);
+}
+
+struct MomStep {
+    float dx, dy, dg1, dg2, sw_new;
+    bool ok;
+};
+
+// The centroid step <x>/N = k dx (Eqs. 5-6) and the ellipticity step
+// dg = (1-|g_w|^2) (P^SH)^-1 (e^obs - e_w) (Eq. 9) with
+// P^SH = X^SH + dX^SH - e (e^SH + de^SH)^T (Eq. 8, A5, A6, B7, B8), evaluated
+// from the eleven weighted moments.  W' = dW/dR^2 = -c W with c = 1/(2 s_w^2).
+__device__ __forceinline__ MomStep moment_step(const float (&m)[11], const MomState& st,
+                                               float k_gain, bool ellip) {
+    MomStep r;
+    r.ok = false;
+    r.dx = r.dy = r.dg1 = r.dg2 = 0.f;
+    r.sw_new = st.sw;
+    const float S0 = m[0];
+    const float Q11 = m[3], Q12 = m[4], Q22 = m[5];
+    const float F40 = m[6], F31 = m[7], F22 = m[8], F13 = m[9], F04 = m[10];
+    const float g1 = st.g1, g2 = st.g2;
+    const float gg = g1 * g1 + g2 * g2;
+    const float A = 1.f + gg - 2.f * g1, B = 1.f + gg + 2.f * g1;
+    if (!(S0 > 0.f)) return r;
+    r.dx = m[1] / (k_gain * S0);
+    r.dy = m[2] / (k_gain * S0);
+    const float SR2 = A * Q11 + B * Q22 - 4.f * g2 * Q12;      // sum f W R^2
+    r.sw_new = SR2 > 0.f ? sqrtf(SR2 / S0) : 0.f;
+    if (!ellip) {
+        r.ok = isfinite(r.dx) && isfinite(r.dy);
+        return r;
+    }
+    const float T = Q11 + Q22;
+    if (!(T > 0.f)) return r;
+    const float iT = 1.f / T;
+    const float e1 = (Q11 - Q22) * iT, e2 = 2.f * Q12 * iT;
+    const float c = 1.f / (2.f * st.sw * st.sw);
+    const float ApB = A + B, AmB = A - B;
+    const float F31m13 = F31 - F13, F31p13 = F31 + F13;
+    // Appendix A: sum f W chi_a psi_b and sum f W theta^2 psi_b
+    const float c1p1 = A * F40 - ApB * F22 + B * F04;
+    const float c1p2 = ApB * F31m13 - 2.f * g2 * (F40 - F04);
+    const float c2p1 = 2.f * (A * F31 - B * F13);
+    const float c2p2 = 2.f * ApB * F22 - 4.f * g2 * F31p13;
+    const float t2p1 = A * F40 + AmB * F22 - B * F04;
+    const float t2p2 = ApB * F31p13 - 2.f * g2 * (F40 + 2.f * F22 + F04);
+    float X11 = 2.f - 2.f * c * c1p1 * iT;
+    float X12 = -2.f * c * c1p2 * iT;
+    float X21 = -2.f * c * c2p1 * iT;
+    float X22 = 2.f - 2.f * c * c2p2 * iT;
+    float eS1 = 2.f * e1 - 2.f * c * t2p1 * iT;
+    float eS2 = 2.f * e2 - 2.f * c * t2p2 * iT;
+    // Appendix B: sum f P_1 ... P_6
+    const float D = Q11 - Q22;
+    const float P1 = 4.f * D - 2.f * c * (A * F40 - AmB * F22 - B * F04 - 4.f * g2 * F31m13);
+    const float P2 = 4.f * Q12 - 2.f * c * (AmB * F31m13 + 2.f * g2 * (F40 - 2.f * F22 + F04));
+    const float P3 = 8.f * Q12 - 4.f * c * (A * F31 + B * F13 - 4.f * g2 * F22);
+    const float P4 = -2.f * D - 4.f * c * (AmB * F22 + 2.f * g2 * F31m13);
+    const float P5 = 4.f * T - 2.f * c * (A * F40 + ApB * F22 + B * F04 - 4.f * g2 * F31p13);
+    const float P6 = -2.f * c * (AmB * F31p13 + 2.f * g2 * (F40 - F04));
+    X11 += (-g1 * P1 - g2 * P2) * iT;
+    X12 += (g1 * P2 - g2 * P1) * iT;
+    X21 += (-g1 * P3 - g2 * P4) * iT;
+    X22 += (g1 * P4 - g2 * P3) * iT;
+    eS1 += (-g1 * P5 - g2 * P6) * iT;
+    eS2 += (g1 * P6 - g2 * P5) * iT;
+    const float P11 = X11 - e1 * eS1, P12 = X12 - e1 * eS2;
+    const float P21 = X21 - e2 * eS1, P22 = X22 - e2 * eS2;
+    const float det = P11 * P22 - P12 * P21;
+    if (!(fabsf(det) > 0.f) || !isfinite(det)) return r;
+    const float ew = 2.f / (1.f + gg);
+    const float r1 = e1 - ew * g1, r2 = e2 - ew * g2;
+    const float sc = (1.f - gg) / det;
+    r.dg1 = sc * (P22 * r1 - P12 * r2);
+    r.dg2 = sc * (-P21 * r1 + P11 * r2);
+    r.ok = isfinite(r.dg1) && isfinite(r.dg2) && isfinite(r.dx) && isfinite(r.dy);
+    return r;
+}
+
+// Iterate to the stop rule.  Returns the number of passes; sets status bits.
+__device__ int moment_iterate(const float* s, int h, int w, int npix, int lane, const DevOpts& o,
+                              bool ellip, MomState& st, uint32_t& status) {
+    const float sw_max = 0.5f * static_cast<float>(h < w ? h : w);
+    int it;
+    for (it = 1; it <= o.max_iter_mom; ++it) {
+        float m[11];
+        moment_pass(s, w, npix, lane, st, m);
+        const MomStep d = moment_step(m, st, o.k_gain, ellip);
+        if (!d.ok) {
+            status |= FSE_ST_MOM_FAILED;
+            break;
+        }
+        st.xf += d.dx;
+        st.yf += d.dy;
+        if (fabsf(st.xf) > 0.5f) {
+            const float rr = rintf(st.xf);
+            st.xi += static_cast<int>(rr);
+            st.xf -= rr;
+        }
+        if (fabsf(st.yf) > 0.5f) {
+            const float rr = rintf(st.yf);
+            st.yi += static_cast<int>(rr);
+            st.yf -= rr;
+        }
+        if (ellip) {
+            // |g| < 1: a step past (1 + |g_w|)/2 is shortened radially to it
+            const float cap = 0.5f * (1.f + sqrtf(st.g1 * st.g1 + st.g2 * st.g2));
+            float n1 = st.g1 + d.dg1, n2 = st.g2 + d.dg2;
+            const float nn = sqrtf(n1 * n1 + n2 * n2);
+            if (nn > cap) {
+                n1 *= cap / nn;
+                n2 *= cap / nn;
+            }
+            st.g1 = n1;
+            st.g2 = n2;
+        }
+        float dsig = 0.f;
+        if (o.sigw_mode == 0) {
+            float ns = d.sw_new;
+            if (ns < 0.5f) { ns = 0.5f; status |= FSE_ST_SIGW_CLAMPED; }
+            if (ns > sw_max) { ns = sw_max; status |= FSE_ST_SIGW_CLAMPED; }
+            dsig = fabsf(ns - st.sw) / st.sw;
+            st.sw = ns;
+        }
+        const float xc = static_cast<float>(st.xi) + st.xf, yc = static_cast<float>(st.yi) + st.yf;
+        if (st.g1 * st.g1 + st.g2 * st.g2 >= 0.95f * 0.95f || xc < -0.5f ||
+            xc > static_cast<float>(w) - 0.5f || yc < -0.5f || yc > static_cast<float>(h) - 0.5f) {
+            status |= FSE_ST_MOM_FAILED;
+            break;
+        }
+        if (fabsf(d.dx) <= o.tol_pos && fabsf(d.dy) <= o.tol_pos && fabsf(d.dg1) <= o.tol_g &&
+            fabsf(d.dg2) <= o.tol_g && dsig <= o.tol_sig) {
+            status |= FSE_ST_MOM_CONVERGED;
+            break;
+        }
+    }
+    if (it > o.max_iter_mom) {
+        status |= FSE_ST_MOM_MAXITER;
+        it = o.max_iter_mom;
+    }
+    return it;
+}
+
+// ------------------------------------------------------------------ start-up
+struct InitOut {
+    int peak;        // brightest pixel (lowest index on ties)
+    float r50;
+    bool finite;
+    bool fallback;   // stamp total <= 0
+};
+
+// Brightest pixel, and the half-light radius r50 from the growth curve around
+// it (Sec. 4.1): pixels are binned in rings of integer radius k (k-1 < d <= k)
+// and the enclosed sum is tracked until it reaches half the stamp total; r50
+// interpolates linearly in the ring that crosses.  Sums are exact 64-bit
+// fixed point (pixel * 2^S), so the crossing ring does not depend on the
+// summation order.
+__device__ InitOut stamp_init(const float* s, int h, int w, int npix, int lane,
+                              unsigned long long* hist) {
+    InitOut o;
+    float vmax = -INFINITY, amax = 0.f;
+    int imax = 0x7fffffff;
+    bool fin = true;
+    for (int p = lane; p < npix; p += 32) {
+        const float v = s[p];
+        fin = fin && isfinite(v);
+        if (v > vmax) { vmax = v; imax = p; }
+        amax = fmaxf(amax, fabsf(v));
+    }
+    o.finite = __all_sync(kFull, fin);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float ov = __shfl_xor_sync(kFull, vmax, off);
+        const int oi = __shfl_xor_sync(kFull, imax, off);
+        if (ov > vmax || (ov == vmax && oi < imax)) { vmax = ov; imax = oi; }
+        amax = fmaxf(amax, __shfl_xor_sync(kFull, amax, off));
+    }
+    o.peak = imax;
+    o.fallback = false;
+    o.r50 = static_cast<float>(kSqrt2Ln2);
+    if (!o.finite) return o;
+    const int pr = imax / w, pc = imax - (imax / w) * w;
+    // fixed-point scale 2^S with amax * npix * 2^S < 2^62
+    int e;
+    frexpf(amax * static_cast<float>(npix), &e);
+    int S = 62 - e;
+    S = S > 100 ? 100 : (S < -100 ? -100 : S);
+    const float fs = ldexpf(1.f, S);
+    const int dh = (h - 1 > pr ? h - 1 - pr : pr), dw = (w - 1 > pc ? w - 1 - pc : pc);
+    const int kmax = static_cast<int>(ceilf(sqrtf(static_cast<float>(dh * dh + dw * dw)))) + 1;
+    for (int k = lane; k <= kmax; k += 32) hist[k] = 0ull;
+    __syncwarp();
+    long long tot = 0;
+    PixelWalk pw(lane, w);
+    for (int p = lane; p < npix; p += 32) {
+        const long long q = __float2ll_rn(s[p] * fs);
+        tot += q;
+        const int di = pw.row - pr, dj = pw.col - pc;
+        const int d2 = di * di + dj * dj;
+        int k = static_cast<int>(sqrtf(static_cast<float>(d2)));
+        k += (k * k < d2) ? 1 : 0;
+        atomicAdd(&hist[k], static_cast<unsigned long long>(q));
+        pw.next();
+    }
+    tot = warp_allsum_ll(tot);
+    __syncwarp();
+    if (tot <= 0) {
+        o.fallback = true;
+        return o;
+    }
+    // warp scan over the rings: lane owns rings [lane*ch, lane*ch + ch)
+    const int nb = kmax + 1;
+    const int ch = (nb + 31) / 32;
+    const int k0 = lane * ch;
+    long long own = 0;
+    for (int k = k0; k < k0 + ch && k < nb; ++k) own += static_cast<long long>(hist[k]);
+    long long incl = own;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const long long o2 = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += o2;
+    }
+    long long run = incl - own;     // enclosed sum before ring k0
+    int kc = -1;
+    long long prev = 0, cur = 0;
+    for (int k = k0; k < k0 + ch && k < nb; ++k) {
+        const long long nxt = run + static_cast<long long>(hist[k]);
+        if (2 * nxt >= tot) {
+            kc = k;
+            prev = run;
+            cur = nxt;
+            break;
+        }
+        run = nxt;
+    }
+    const unsigned hit = __ballot_sync(kFull, kc >= 0);
+    const int src = hit ? __ffs(hit) - 1 : 0;
+    kc = __shfl_sync(kFull, kc, src);
+    prev = __shfl_sync(kFull, prev, src);
+    cur = __shfl_sync(kFull, cur, src);
+    if (kc <= 0) {
+        o.r50 = kc == 0 ? static_cast<float>(0.25 * static_cast<double>(tot) / static_cast<double>(cur))
+                        : static_cast<float>(kSqrt2Ln2);
+    } else {
+        const double half = 0.5 * static_cast<double>(tot);
+        o.r50 = static_cast<float>((kc - 1) + (half - static_cast<double>(prev)) /
+                                                  static_cast<double>(cur - prev));
+    }
+    __syncwarp();
+    return o;
+}
+
+// ------------------------------------------------------------------ fit
+// One pass of the profile over the stamp at (I0g, r_e, n).  With
+// a = log2(r/r_e), u = 2^(a/n) = (r/r_e)^(1/n), E = exp(-b u), v = E u and the
+// residual r = I0g E - I, the ten sums below give chi^2, the normal equations
+// of (I0, r_e, n) and, after eliminating I0 at its closed form (Eq. 13), the
+// reduced 2x2 problem in (r_e, n):
+//   dm/dr_e = I0 b v / (n r_e),  dm/dn = I0 (b ln2 / n^2) v a - I0 b'(n) v.
+struct FitEval {
+    double I0;       // Eq. 13 at (r_e, n)
+    double chi2;     // Eq. 11 at that I0
+    double g[2];     // J^T r of the reduced problem
+    double H[3];     // J^T J of the reduced problem (00, 01, 11)
+};
+
+template <bool IVAR>
+__device__ FitEval fit_eval(const float* __restrict__ s, const float* __restrict__ L,
+                            const float* __restrict__ sq, int npix, int lane, double I0g,
+                            double re, double n, double lq) {
+    double b, db;
+    bn_eval(n, &b, &db);
+    const float inv_n = static_cast<float>(1.0 / n);
+    const float nbl = static_cast<float>(-b * 1.4426950408889634);
+    const float c0 = static_cast<float>(log2(re) + lq);
+    const float I0f = static_cast<float>(I0g);
+    float acc[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) acc[i] = 0.f;
+    for (int p = lane; p < npix; p += 32) {
+        const float a = L[p] - c0;
+        const float u = ex2(a * inv_n);
+        float E = ex2(u * nbl);
+        float r = fmaf(I0f, E, -s[p]);
+        if (IVAR) {
+            const float q = sq[p];
+            E *= q;
+            r *= q;
+        }
+        const float v = E * u, va = v * a;
+        acc[0] = fmaf(E, E, acc[0]);
+        acc[1] = fmaf(E, v, acc[1]);
+        acc[2] = fmaf(E, va, acc[2]);
+        acc[3] = fmaf(v, v, acc[3]);
+        acc[4] = fmaf(v, va, acc[4]);
+        acc[5] = fmaf(va, va, acc[5]);
+        acc[6] = fmaf(E, r, acc[6]);
+        acc[7] = fmaf(v, r, acc[7]);
+        acc[8] = fmaf(va, r, acc[8]);
+        acc[9] = fmaf(r, r, acc[9]);
+    }
+    warp_allsum(acc);
+    FitEval f;
+    const double sEE = acc[0], sEv = acc[1], sEva = acc[2], svv = acc[3], svva = acc[4],
+                 svaa = acc[5], sEr = acc[6], svr = acc[7], svar = acc[8], srr = acc[9];
+    const double d = -sEr / sEE;                 // I0* - I0g
+    f.I0 = I0g + d;
+    f.chi2 = srr + d * sEr;                      // = sum (I0* E - I)^2
+    const double k2 = f.I0 * b / (n * re);
+    const double kA = f.I0 * b * kLn2 / (n * n);
+    const double kB = f.I0 * db;
+    const double svr_s = svr + d * sEv, svar_s = svar + d * sEva;
+    const double Cvv = svv - sEv * sEv / sEE;
+    const double Cvva = svva - sEv * sEva / sEE;
+    const double Cvaa = svaa - sEva * sEva / sEE;
+    f.g[0] = k2 * svr_s;
+    f.g[1] = kA * svar_s - kB * svr_s;
+    f.H[0] = k2 * k2 * Cvv;
+    f.H[1] = k2 * (kA * Cvva - kB * Cvv);
+    f.H[2] = kA * kA * Cvaa - 2.0 * kA * kB * Cvva + kB * kB * Cvv;
+    return f;
+}
+
+// Start: r_e from the weight size, n the candidate of {0.5, 1, 2, 4} with the
+// lowest chi^2 at its closed-form I0 (chi^2 = sum I^2 - (sum I E)^2 / sum E^2).
+template <bool IVAR>
+__device__ void fit_start(const float* __restrict__ s, const float* __restrict__ L,
+                          const float* __restrict__ sq, int npix, int lane, double re0, double lq,
+                          double* n0, double* I00) {
+    const double nc[4] = {0.5, 1.0, 2.0, 4.0};
+    float inv_n[4], nbl[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        double b, db;
+        bn_eval(nc[c], &b, &db);
+        inv_n[c] = static_cast<float>(1.0 / nc[c]);
+        nbl[c] = static_cast<float>(-b * 1.4426950408889634);
+    }
+    const float c0 = static_cast<float>(log2(re0) + lq);
+    float acc[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) acc[i] = 0.f;
+    for (int p = lane; p < npix; p += 32) {
+        const float a = L[p] - c0;
+        float I = s[p];
+        const float q = IVAR ? sq[p] : 1.f;
+        if (IVAR) I *= q;
+        acc[8] = fmaf(I, I, acc[8]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float E = ex2(ex2(a * inv_n[c]) * nbl[c]);
+            if (IVAR) E *= q;
+            acc[2 * c] = fmaf(E, E, acc[2 * c]);
+            acc[2 * c + 1] = fmaf(E, I, acc[2 * c + 1]);
+        }
+    }
+    warp_allsum(acc);
+    int best = 0;
+    double bc = INFINITY;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const double sEE = acc[2 * c], sEI = acc[2 * c + 1];
+        const double chi2 = static_cast<double>(acc[8]) - sEI * sEI / sEE;
+        if (sEE > 0.0 && chi2 < bc) {
+            bc = chi2;
+            best = c;
+        }
+    }
+    *n0 = nc[best];
+    *I00 = acc[2 * best] > 0.f ? static_cast<double>(acc[2 * best + 1]) / acc[2 * best] : 1.0;
+}
+
+struct FitOut {
+    double I0, re, n, chi2, flux;
+    int iters;
+};
+
+// Levenberg-Marquardt over theta = (r_e, n) with I0 at its closed form after
+// every pass; damping by the gain ratio rho (Nielsen 1999).
+template <bool IVAR>
+__device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, int w, int npix,
+                             int lane, const DevOpts& o, const MomState& st, uint32_t& status) {
+    // per-pixel 0.5 log2 R^2 about the fixed centre with the fixed ellipticity
+    const float g1 = st.g1, g2 = st.g2;
+    const float gg = g1 * g1 + g2 * g2;
+    const float A = 1.f + gg - 2.f * g1, B = 1.f + gg + 2.f * g1, G4 = 4.f * g2;
+    {
+        PixelWalk pw(lane, w);
+        for (int p = lane; p < npix; p += 32) {
+            const float t1 = static_cast<float>(pw.col - st.xi) - st.xf;
+            const float t2 = static_cast<float>(pw.row - st.yi) - st.yf;
+            const float R2 = fmaf(A, t1 * t1, fmaf(B, t2 * t2, -G4 * (t1 * t2)));
+            L[p] = R2 > 0.f ? 0.5f * log2f(R2) : -1000.f;
+            pw.next();
+        }
+        __syncwarp();
+    }
+    const double gabs = sqrt(static_cast<double>(gg));
+    const double lq = log2(1.0 - gabs);          // log2 r = 0.5 log2 R^2 - log2(1 - |g|)
+    const double re_max = o.re_max_frac * static_cast<double>(h > w ? h : w);
+    const double re_min = o.re_min, n_min = o.n_min, n_max = o.n_max;
+    double re = kSqrt2Ln2 * static_cast<double>(st.sw) / (1.0 - gabs);
+    re = re < re_min ? re_min : (re > re_max ? re_max : re);
+    double n, I0g;
+    fit_start<IVAR>(s, L, sq, npix, lane, re, lq, &n, &I0g);
+    FitEval cur = fit_eval<IVAR>(s, L, sq, npix, lane, I0g, re, n, lq);
+    int evals = 1;
+    double lambda = o.lm_lambda0, nu = 2.0;
+    bool converged = false;
+    const bool finite0 = isfinite(cur.chi2) && isfinite(cur.g[0]) && isfinite(cur.g[1]) &&
+                         isfinite(cur.H[0]) && isfinite(cur.H[1]) && isfinite(cur.H[2]);
+    if (!finite0) status |= FSE_ST_FIT_SINGULAR;
+    int it;
+    for (it = 1; finite0 && it <= o.max_iter_fit; ++it) {
+        const double M00 = cur.H[0] * (1.0 + lambda), M11 = cur.H[2] * (1.0 + lambda);
+        const double M01 = cur.H[1];
+        const double det = M00 * M11 - M01 * M01;
+        if (!(det > 0.0) || !isfinite(det)) {
+            status |= FSE_ST_FIT_SINGULAR;
+            break;
+        }
+        const double d0 = (-M11 * cur.g[0] + M01 * cur.g[1]) / det;
+        const double d1 = (M01 * cur.g[0] - M00 * cur.g[1]) / det;
+        double qre = re + d0, qn = n + d1;
+        qre = qre < re_min ? re_min : (qre > re_max ? re_max : qre);
+        qn = qn < n_min ? n_min : (qn > n_max ? n_max : qn);
+        const double s0 = qre - re, s1 = qn - n;
+        const double step = fmax(fabs(s0) / re, fabs(s1) / n);
+        if (step <= o.tol_fit) {
+            converged = true;
+            break;
+        }
+        const double pred = -(2.0 * (cur.g[0] * s0 + cur.g[1] * s1) +
+                              s0 * (cur.H[0] * s0 + cur.H[1] * s1) +
+                              s1 * (cur.H[1] * s0 + cur.H[2] * s1));
+        const FitEval nxt = fit_eval<IVAR>(s, L, sq, npix, lane, cur.I0, qre, qn, lq);
+        ++evals;
+        if (nxt.chi2 < cur.chi2) {
+            const double rho = pred > 0.0 ? (cur.chi2 - nxt.chi2) / pred : 1.0;
+            const double t = 2.0 * rho - 1.0;
+            lambda *= fmax(1.0 / 3.0, 1.0 - t * t * t);
+            nu = 2.0;
+            re = qre;
+            n = qn;
+            cur = nxt;
+        } else {
+            lambda *= nu;
+            nu *= 2.0;
+            if (lambda > 1e15) {
+                converged = true;
+                break;
+            }
+        }
+    }
+    if (converged && isfinite(cur.chi2)) status |= FSE_ST_FIT_CONVERGED;
+    else if (finite0 && it > o.max_iter_fit) status |= FSE_ST_FIT_MAXITER;
+    if (re <= re_min || re >= re_max || n <= n_min || n >= n_max) status |= FSE_ST_FIT_BOUND;
+    if (!(cur.I0 > 0.0)) status |= FSE_ST_NONPOS_FLUX;
+    FitOut out;
+    out.I0 = cur.I0;
+    out.re = re;
+    out.n = n;
+    out.chi2 = cur.chi2;
+    out.iters = evals;
+    double b, db;
+    bn_eval(n, &b, &db);
+    const double q = (1.0 - gabs) / (1.0 + gabs);
+    out.flux = 2.0 * kPi * n * exp(lgamma(2.0 * n) - 2.0 * n * log(b)) * cur.I0 * re * re * q;
+    return out;
+}
+
+// ------------------------------------------------------------------ kernel
+template <int STAGE, int DT, bool IVAR>
+__global__ void __launch_bounds__(512) estimator_kernel(LaunchArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int max_pix = a.opts.max_pix;
+    unsigned char* wbase = smem + static_cast<size_t>(warp) * warp_bytes(max_pix, IVAR);
+    float* pixbuf = reinterpret_cast<float*>(wbase);
+    float* aux = reinterpret_cast<float*>(wbase + pix_bytes(max_pix));
+    float* ivbuf = IVAR ? reinterpret_cast<float*>(wbase + pix_bytes(max_pix) + aux_bytes(max_pix))
+                        : nullptr;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(wbase + warp_bytes(max_pix, IVAR) - 16);
+    if (lane == 0) mbar_init(bar);
+    __syncwarp();
+    if (lane == 0) fence_proxy_async();
+    __syncwarp();
+    uint32_t phase = 0;
+    const DevOpts& o = a.opts;
+
+    for (int round = 0;; ++round) {
+        unsigned sidx = 0;
+        if (a.static_assign) {
+            // one stamp per warp, no work counter (used by the per-stamp launches)
+            if (round > 0) break;
+            sidx = blockIdx.x * (blockDim.x >> 5) + warp;
+        } else {
+            if (lane == 0) sidx = atomicAdd(a.queue, 1u);
+            sidx = __shfl_sync(kFull, sidx, 0);
+        }
+        if (sidx >= static_cast<unsigned long long>(a.count)) break;
+        const int64_t si = static_cast<int64_t>(sidx);
+        const fse_stamp ix = a.idx[si];
+        const int h = ix.h, w = ix.w;
+        const long long npl = static_cast<long long>(h) * w;
+        fse_result res;
+        if (STAGE == kStageEllipticity || STAGE == kStageFit) {
+            res = a.out[si];
+        } else {
+            res = fse_result{};
+        }
+        uint32_t status = (STAGE == kStageEllipticity || STAGE == kStageFit)
+                              ? (res.status & (FSE_ST_SIGW_CLAMPED | FSE_ST_INIT_FALLBACK |
+                                               (STAGE == kStageFit ? (FSE_ST_MOM_CONVERGED |
+                                                                      FSE_ST_MOM_MAXITER)
+                                                                   : 0u)))
+                              : 0u;
+        res.npix = static_cast<int32_t>(npl > 0x7fffffff ? 0x7fffffff : npl);
+        bool skip = false;
+        if (h < 1 || w < 1 || npl > max_pix) {
+            status |= FSE_ST_BAD_SIZE;
+            skip = true;
+        }
+        float* s = pixbuf;
+        if (!skip) {
+            const char* g = static_cast<const char*>(a.pix) + ix.offset * (DT == FSE_BF16 ? 2 : 4);
+            const float scale = (DT == FSE_BF16 && a.scale) ? a.scale[si] : 1.f;
+            const bool ok = stage_stamp<DT>(pixbuf, &s, aux, g, static_cast<int>(npl), scale, bar,
+                                            &phase, lane);
+            if (IVAR && ok) {
+                const float* gv = a.inv_var + ix.offset;
+                for (int p = lane; p < npl; p += 32) ivbuf[p] = sqrtf(fmaxf(__ldg(gv + p), 0.f));
+                __syncwarp();
+            }
+            if (!ok) {
+                // the copy did not complete within the bound: report and stop this warp
+                if (lane == 0) {
+                    atomicOr(a.err, 1u);
+                    res.status = status | FSE_ST_TIMEOUT;
+                    a.out[si] = res;
+                }
+                return;
+            }
+        }
+        const int npix = static_cast<int>(npl);
+        MomState st;
+        if (!skip && (STAGE == kStageCentroid || STAGE == kStageAll)) {
+            const InitOut in =
+                stamp_init(s, h, w, npix, lane, reinterpret_cast<unsigned long long*>(aux));
+            if (!in.finite) {
+                status |= FSE_ST_NONFINITE;
+                skip = true;
+            } else {
+                if (in.fallback) status |= FSE_ST_INIT_FALLBACK;
+                float sw = in.r50 / static_cast<float>(kSqrt2Ln2);
+                const float smax = 0.5f * static_cast<float>(h < w ? h : w);
+                if (sw < 0.5f) { sw = 0.5f; status |= FSE_ST_SIGW_CLAMPED; }
+                if (sw > smax) { sw = smax; status |= FSE_ST_SIGW_CLAMPED; }
+                st.xi = in.peak % w;
+                st.yi = in.peak / w;
+                st.xf = st.yf = 0.f;
+                st.g1 = st.g2 = 0.f;
+                st.sw = sw;
+                res.r50 = in.r50;
+                res.sigma_w = sw;
+            }
+        } else if (!skip) {
+            // centre (and for the fit, ellipticity) from the previous stage
+            bool fin = true;
+            for (int p = lane; p < npix; p += 32) fin = fin && isfinite(s[p]);
+            if (!__all_sync(kFull, fin)) {
+                status |= FSE_ST_NONFINITE;
+                skip = true;
+            }
+            const float rx = rintf(res.x0), ry = rintf(res.y0);
+            st.xi = static_cast<int>(rx);
+            st.yi = static_cast<int>(ry);
+            st.xf = res.x0 - rx;
+            st.yf = res.y0 - ry;
+            st.g1 = STAGE == kStageFit ? res.e1 : 0.f;
+            st.g2 = STAGE == kStageFit ? res.e2 : 0.f;
+            st.sw = res.sigma_w;
+            if (!(st.sw > 0.f) || !isfinite(res.x0) || !isfinite(res.y0)) {
+                status |= FSE_ST_MOM_FAILED;
+                skip = true;
+            }
+        }
+        if (!skip && STAGE != kStageFit) {
+            const bool ellip = STAGE != kStageCentroid;
+            res.it_mom = moment_iterate(s, h, w, npix, lane, o, ellip, st, status);
+            res.x0 = static_cast<float>(st.xi) + st.xf;
+            res.y0 = static_cast<float>(st.yi) + st.yf;
+            res.sigma_w = st.sw;
+            if (ellip) {
+                res.e1 = st.g1;
+                res.e2 = st.g2;
+            }
+            if (!(status & FSE_ST_MOM_CONVERGED)) skip = true;
+        }
+        if (!skip && (STAGE == kStageFit || STAGE == kStageAll)) {
+            const FitOut f = sersic_fit<IVAR>(s, aux, ivbuf, h, w, npix, lane, o, st, status);
+            res.I0 = static_cast<float>(f.I0);
+            res.re = static_cast<float>(f.re);
+            res.n = static_cast<float>(f.n);
+            res.flux = static_cast<float>(f.flux);
+            res.chi2 = f.chi2;
+            res.it_fit = f.iters;
+        }
+        res.status = status;
+        if (lane == 0) a.out[si] = res;
+        __syncwarp();
+    }
+}
+
+template <int STAGE, int DT, bool IVAR>
+cudaError_t launch_t(const LaunchArgs& a, cudaStream_t stream) {
+    const size_t spw = warp_bytes(a.opts.max_pix, IVAR);
+    const size_t smem = spw * a.warps_per_cta;
+    auto kern = estimator_kernel<STAGE, DT, IVAR>;
+    // the shared-memory opt-in is raised once per instantiation and size (per device)
+    static size_t opted[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev >= 64) return e != cudaSuccess ? e : cudaErrorInvalidDevice;
+    if (smem > opted[dev]) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        opted[dev] = smem;
+    }
+    long long grid = a.num_ctas;
+    if (grid <= 0) {
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * a.warps_per_cta, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        grid = static_cast<long long>(per_sm) * sms;
+    }
+    const long long need = (a.count + a.warps_per_cta - 1) / a.warps_per_cta;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    kern<<<static_cast<unsigned>(grid), 32 * a.warps_per_cta, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int STAGE>
+cudaError_t launch_stage(const LaunchArgs& a, cudaStream_t stream) {
+    const bool iv = a.inv_var != nullptr;
+    if (a.dtype == FSE_BF16)
+        return iv ? launch_t<STAGE, FSE_BF16, true>(a, stream) : launch_t<STAGE, FSE_BF16, false>(a, stream);
+    return iv ? launch_t<STAGE, FSE_F32, true>(a, stream) : launch_t<STAGE, FSE_F32, false>(a, stream);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host wrappers
+size_t smem_per_warp(int max_pix) { return warp_bytes(max_pix, false); }
+
+void choose_launch(int max_pix, int* warps_per_cta, int* ctas_per_sm) {
+    const size_t spw = warp_bytes(max_pix, false);
+    const size_t budget = 227 * 1024;
+    int wpc = 4;
+    while (wpc > 1 && spw * wpc > budget) wpc >>= 1;
+    *warps_per_cta = wpc;
+    *ctas_per_sm = static_cast<int>((228 * 1024) / (spw * wpc + 1024));
+}
+
+cudaError_t build_bn_table(cudaStream_t stream) {
+    build_bn_kernel<<<(kBnNodes + 127) / 128, 128, 0, stream>>>();
+    return cudaGetLastError();
+}
+
+cudaError_t eval_bn(const double* n, double* b, double* db, int64_t count, cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    eval_bn_kernel<<<static_cast<unsigned>((count + 255) / 256), 256, 0, stream>>>(n, b, db, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_estimator(const LaunchArgs& a, cudaStream_t stream) {
+    switch (a.stage) {
+        case kStageCentroid: return launch_stage<kStageCentroid>(a, stream);
+        case kStageEllipticity: return launch_stage<kStageEllipticity>(a, stream);
+        case kStageFit: return launch_stage<kStageFit>(a, stream);
+        default: return launch_stage<kStageAll>(a, stream);
+    }
+}
+
+}  // namespace fse

@@ -1,0 +1,83 @@
+"""The C ABI library builds, loads and exports what include/fse.h declares (CPU only)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1203_0571_gb300 import _build, binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fse.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return re.findall(r"^\s*(?:int|void|const char \*)\s*\*?\s*(fse_\w+)\s*\(", text, flags=re.M)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return binding.load()
+
+
+def test_header_declares_binding_exports():
+    assert declared_functions() == binding.EXPORTS
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", _build.LIB], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    for name in declared_functions():
+        assert name in exported, name
+        assert hasattr(lib, name)
+
+
+def test_struct_layout_matches_c(tmp_path):
+    """sizeof/offsetof of the ABI structs from a C compiler equal the ctypes/numpy views."""
+    src = tmp_path / "layout.c"
+    fields_r = [n for n in binding.RESULT_DTYPE.names]
+    fields_o = [f for f, _ in binding.Opts._fields_]
+    body = ['#include <stdio.h>', '#include <stddef.h>', '#include "fse.h"', 'int main(void){',
+            'printf("%zu %zu %zu\\n", sizeof(fse_result), sizeof(fse_opts), sizeof(fse_stamp));']
+    body += [f'printf("%zu ", offsetof(fse_result, {f}));' for f in fields_r]
+    body += ['printf("\\n");']
+    body += [f'printf("%zu ", offsetof(fse_opts, {f}));' for f in fields_o]
+    body += ['printf("\\n"); return 0; }']
+    src.write_text("\n".join(body))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    sizes = [int(x) for x in lines[0].split()]
+    assert sizes == [64, ctypes.sizeof(binding.Opts), 16]
+    assert [int(x) for x in lines[1].split()] == [binding.RESULT_DTYPE.fields[f][1] for f in fields_r]
+    assert [int(x) for x in lines[2].split()] == [getattr(binding.Opts, f).offset for f in fields_o]
+    assert binding.STAMP_DTYPE.itemsize == 16
+
+
+def test_opts_defaults(lib):
+    o = binding.default_opts()
+    assert o.size == ctypes.sizeof(binding.Opts)
+    assert o.k_gain == 0.75 and o.sigw_mode == 1 and o.max_pix == 0
+    assert o.n_min == 0.2 and o.n_max == 10.0
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert lib.fse_create(ctypes.byref(h), 0) != 0
+    assert not h.value
+
+
+def test_index_packing():
+    import torch
+    idx = binding.make_index([0, 1024, 5], [32, 16, 3], [32, 64, 7], device="cpu")
+    arr = idx.numpy().view(binding.STAMP_DTYPE).reshape(-1)
+    assert arr["offset"].tolist() == [0, 1024, 5]
+    assert arr["h"].tolist() == [32, 16, 3] and arr["w"].tolist() == [32, 64, 7]

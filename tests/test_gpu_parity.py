@@ -1,0 +1,222 @@
+"""CUDA path against the FP64 oracle, through the C ABI (needs a GB300).
+
+Parity gate: centroid 1e-4 px, e1/e2 1e-5, r_e/n/flux 1e-4 relative, chi^2
+1e-5 relative, over every stamp that enters the gate (see tests/parity.py).
+"""
+import numpy as np
+import pytest
+import torch
+
+import parity as PR
+from paper_1203_0571_gb300 import binding as B
+from paper_1203_0571_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    return B.Context(0)
+
+
+@pytest.fixture(scope="module")
+def O(oracle):
+    return oracle.get()
+
+
+def gpu_run(ctx, batch, fn="fit_batch", inout=None, **kw):
+    b = batch.to("cuda")
+    idx = B.make_index(b.offset, b.h, b.w)
+    if inout is not None:
+        out = torch.as_tensor(inout.view(np.uint8).reshape(-1, 64)).to("cuda")
+        getattr(ctx, fn)(b.pix, idx, out, scale=b.scale, **kw)
+    else:
+        out = getattr(ctx, fn)(b.pix, idx, scale=b.scale, **kw)
+    torch.cuda.synchronize()
+    return B.results(out)
+
+
+def assert_gate(rep, min_gated=0.85):
+    assert rep["gated"] >= min_gated * rep["n"], {k: v for k, v in rep.items() if not k.startswith("_")}
+    assert rep["within_tolerance"] == rep["gated"], (
+        rep["failing"], rep["max_err"], {k: v for k, v in rep.items() if k in ("n", "gated")})
+
+
+def test_bn_table(ctx, O):
+    n = torch.cat([torch.linspace(0.2, 10.0, 2001, dtype=torch.float64),
+                   0.2 + 9.8 * torch.rand(2000, dtype=torch.float64, generator=torch.Generator().manual_seed(1))])
+    b, db = ctx.sersic_b(n.cuda())
+    b, db = b.cpu().numpy(), db.cpu().numpy()
+    nn = n.numpy()
+    rb = np.array([O.sersic_b(x) for x in nn])
+    rdb = np.array([O.sersic_db(x) for x in nn])
+    assert np.max(np.abs(b / rb - 1)) <= 1e-10
+    assert np.max(np.abs(db / rdb - 1)) <= 1e-6
+
+
+def test_small_workload_chain(ctx, O):
+    batch = synth.make_workload(0)
+    g = gpu_run(ctx, batch)
+    ids = np.arange(batch.count)
+    o = PR.oracle_results(O, batch, ids)
+    rep = PR.compare(g, o, O=O, batch=batch, ids=ids)
+    PR.dump("small_chain", rep)
+    assert_gate(rep)
+
+
+def test_stage_centroid(ctx, O):
+    batch = synth.make_workload(0)
+    g = gpu_run(ctx, batch, "centroid")
+    o = PR.oracle_results(O, batch, np.arange(batch.count), stage="centroid")
+    rep = PR.compare(g, o, keys=("x0", "y0"), fit=False)
+    PR.dump("stage_centroid", rep)
+    assert_gate(rep, 0.95)
+    both = ((g["status"] & 1) & (o["status"] & 1)).astype(bool)
+    assert np.max(np.abs(g["r50"][both] / o["r50"][both] - 1)) <= 1e-6
+    assert np.max(np.abs(g["sigma_w"][both] / o["sigma_w"][both] - 1)) <= 1e-6
+
+
+def test_stage_ellipticity(ctx, O):
+    batch = synth.make_workload(0)
+    ids = np.arange(batch.count)
+    gc = gpu_run(ctx, batch, "centroid")
+    ge = gpu_run(ctx, batch, "ellipticity", inout=gc.copy())
+    oc = PR.oracle_results(O, batch, ids, stage="centroid")
+    oe = PR.oracle_results(O, batch, ids, stage="ellipticity", init=oc)
+    rep = PR.compare(ge, oe, keys=("x0", "y0", "e1", "e2"), fit=False)
+    PR.dump("stage_ellipticity", rep)
+    assert_gate(rep, 0.9)
+
+
+def test_stage_fit_isolated(ctx, O):
+    """The fit alone, both sides started from the oracle's centre and ellipticity."""
+    batch = synth.make_workload(0)
+    ids = np.arange(batch.count)
+    om = PR.oracle_results(O, batch, ids)
+    inout = np.zeros(batch.count, dtype=B.RESULT_DTYPE)
+    for k in ("x0", "y0", "e1", "e2", "sigma_w"):
+        inout[k] = om[k].astype(np.float32)
+    inout["status"] = om["status"] & 1
+    g = gpu_run(ctx, batch, "sersic_fit", inout=inout)
+    init = np.zeros(batch.count, dtype=om.dtype)
+    for k in ("x0", "y0", "e1", "e2", "sigma_w"):
+        init[k] = inout[k].astype(np.float64)      # the same fp32-rounded start
+    init["status"] = inout["status"]
+    o = PR.oracle_results(O, batch, ids, stage="fit", init=init)
+    rep = PR.compare(g, o, keys=("re", "n", "flux", "chi2"), O=O, batch=batch, ids=ids)
+    PR.dump("stage_fit", rep)
+    assert_gate(rep)
+
+
+def test_uniform_workload_full_size_sampled(ctx, O):
+    """100,000 stamps of 48x48 in the benchmark's launch; 400 sampled stamps checked."""
+    batch = synth.make_workload(1, device="cuda")
+    idx = B.make_index(batch.offset, batch.h, batch.w)
+    out = ctx.fit_batch(batch.pix, idx)
+    torch.cuda.synchronize()
+    g = B.results(out)
+    assert (g["npix"] == 48 * 48).all()
+    assert not (g["status"] & (B.ST["BAD_SIZE"] | B.ST["NONFINITE"] | B.ST["TIMEOUT"])).any()
+    conv = (g["status"] & 3) == 3
+    assert conv.mean() > 0.9
+    for k in ("x0", "y0", "e1", "e2", "I0", "re", "n", "flux", "chi2"):
+        assert np.isfinite(g[k][conv]).all(), k
+    ids = np.sort(np.random.default_rng(7).choice(batch.count, 400, replace=False))
+    cpu = synth.make_workload(1, ids=ids)
+    o = PR.oracle_results(O, cpu, np.arange(ids.size))
+    rep = PR.compare(g[ids], o, O=O, batch=cpu, ids=np.arange(ids.size))
+    PR.dump("uniform_sampled", rep)
+    assert_gate(rep)
+
+
+def test_ragged_unaligned(ctx, O):
+    batch = synth.make_workload(2, count=3000)
+    assert (batch.offset.numpy() % 4 != 0).mean() > 0.5      # most stamps start unaligned
+    g = gpu_run(ctx, batch)
+    ids = np.sort(np.random.default_rng(3).choice(batch.count, 300, replace=False))
+    o = PR.oracle_results(O, batch, ids)
+    rep = PR.compare(g[ids], o, O=O, batch=batch, ids=ids)
+    PR.dump("ragged", rep)
+    assert_gate(rep, 0.8)
+
+
+def test_bf16_pixels(ctx, O):
+    batch = synth.encode_bf16(synth.make_workload(4, count=400))
+    g = gpu_run(ctx, batch)
+    ids = np.arange(batch.count)
+    o = PR.oracle_results(O, batch, ids)
+    rep = PR.compare(g, o, O=O, batch=batch, ids=ids)
+    PR.dump("bf16", rep)
+    assert_gate(rep, 0.8)
+
+
+def test_inverse_variance(ctx, O):
+    batch = synth.make_workload(0)
+    ivar = (0.5 + 1.5 * torch.rand(batch.pix.numel(), generator=torch.Generator().manual_seed(4))).float()
+    b = batch.to("cuda")
+    idx = B.make_index(b.offset, b.h, b.w)
+    g = B.results(ctx.fit_batch(b.pix, idx, inv_var=ivar.cuda()))
+    ids = np.arange(batch.count)
+    iv = ivar.numpy()
+    o = PR.oracle_results(O, batch, ids, ivar=iv)
+    rep = PR.compare(g, o, O=O, batch=batch, ids=ids, ivar=iv)
+    PR.dump("inv_var", rep)
+    assert_gate(rep)
+
+
+def test_edge_cases(ctx, O):
+    rng = np.random.default_rng(0)
+    good = synth.single_stamp(32, 32, n=1.5, re=3.0, g1=0.2, g2=0.1, xc=15.3, yc=16.1, I0=500.0,
+                              noise_sigma=1.0, seed=1)
+    big = synth.single_stamp(128, 128, n=2.0, re=9.0, g1=-0.1, g2=0.3, xc=63.6, yc=64.2, I0=200.0,
+                             noise_sigma=1.0, seed=2)
+    nan = good.copy()
+    nan[5, 7] = np.nan
+    stamps = [good, nan, np.zeros((32, 32)), rng.normal(size=(1, 1)) + 5, rng.normal(size=(3, 5)) + 3,
+              np.ones((129, 129)), big, rng.normal(size=(17, 23)) + 1]
+    pix = np.concatenate([s.astype(np.float32).ravel() for s in stamps])
+    offs = np.cumsum([0] + [s.size for s in stamps[:-1]])
+    hs = np.array([s.shape[0] for s in stamps])
+    ws = np.array([s.shape[1] for s in stamps])
+    idx = B.make_index(offs, hs, ws)
+    g = B.results(ctx.fit_batch(torch.as_tensor(pix).cuda(), idx))
+    o, _ = O.batch(pix, offs, hs, ws)
+    assert g["status"][1] & B.ST["NONFINITE"] and o["status"][1] & 16
+    assert g["status"][2] & B.ST["INIT_FALLBACK"] and g["status"][2] & B.ST["MOM_FAILED"]
+    assert g["status"][5] == B.ST["BAD_SIZE"] and o["status"][5] == 32
+    for j in (0, 6):
+        rep = PR.compare(g[j:j + 1], o[j:j + 1])
+        assert rep["gated"] == 1 and rep["within_tolerance"] == 1, (j, rep["max_err"])
+    # moment-only agreement of the tiny stamps where both converge
+    for j in (3, 4, 7):
+        if (g["status"][j] & 1) and (o["status"][j] & 1):
+            assert abs(g["x0"][j] - o["x0"][j]) <= 1e-4 and abs(g["y0"][j] - o["y0"][j]) <= 1e-4
+    # an empty batch is a no-op
+    empty = ctx.fit_batch(torch.zeros(1, device="cuda"), B.make_index([], [], []))
+    assert empty.shape[0] == 0
+
+
+def test_plain_equals_batched(ctx):
+    batch = synth.make_workload(1, count=1000)
+    b = batch.to("cuda")
+    idx = B.make_index(b.offset, b.h, b.w)
+    o1 = ctx.fit_batch(b.pix, idx)
+    o2 = ctx.fit_batch_plain(b.pix, idx)
+    o3 = ctx.fit_batch(b.pix, idx, opts=B.default_opts(warps_per_cta=1))
+    o4 = ctx.fit_batch(b.pix, idx)
+    torch.cuda.synchronize()
+    assert torch.equal(o1, o2) and torch.equal(o1, o3) and torch.equal(o1, o4)
+
+
+def test_host_buffers_equal_device(ctx):
+    batch = synth.make_workload(1, count=10000)
+    b = batch.to("cuda")
+    idx = B.make_index(b.offset, b.h, b.w)
+    dev = B.results(ctx.fit_batch(b.pix, idx))
+    host_pix = batch.pix.pin_memory()
+    host_idx = B.make_index(batch.offset, batch.h, batch.w, device="cpu").pin_memory()
+    out = torch.zeros((batch.count, 64), dtype=torch.uint8).pin_memory()
+    ctx.fit_batch_host(host_pix, host_idx, out=out)
+    host = out.numpy().view(B.RESULT_DTYPE).reshape(-1)
+    assert host.tobytes() == dev.tobytes()
