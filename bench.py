@@ -228,6 +228,7 @@ def main():
     idx = B.make_index(batch.offset, batch.h, batch.w, device=f"cuda:{local}")
     out = torch.empty((n, 64), dtype=torch.uint8, device=f"cuda:{local}")
     stream = torch.cuda.current_stream()
+    opts = B.default_opts(max_pix=48 * 48)
 
     def barrier():
         torch.cuda.synchronize()
@@ -235,7 +236,7 @@ def main():
             torch.distributed.barrier()
 
     for _ in range(args.warmup):
-        ctx.fit_batch(batch.pix, idx, out=out, stream=stream)
+        ctx.fit_batch(batch.pix, idx, out=out, opts=opts, stream=stream)
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
@@ -247,7 +248,7 @@ def main():
     t0.record(stream)
     for a, b in ev:
         a.record(stream)
-        ctx.fit_batch(batch.pix, idx, out=out, stream=stream)
+        ctx.fit_batch(batch.pix, idx, out=out, opts=opts, stream=stream)
         b.record(stream)
     t1.record(stream)
     barrier()
@@ -288,11 +289,11 @@ def main():
     # the plain form: one launch per stamp, on the first stamps of the workload
     pn = min(args.plain_stamps, n)
     pout = torch.empty((pn, 64), dtype=torch.uint8, device=f"cuda:{local}")
-    ctx.fit_batch_plain(batch.pix, idx[:pn], out=pout)
+    ctx.fit_batch_plain(batch.pix, idx[:pn], out=pout, opts=opts)
     torch.cuda.synchronize()
     pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     pa.record(stream)
-    ctx.fit_batch_plain(batch.pix, idx[:pn], out=pout, stream=stream)
+    ctx.fit_batch_plain(batch.pix, idx[:pn], out=pout, opts=opts, stream=stream)
     pb.record(stream)
     torch.cuda.synchronize()
     plain = {"value": pn / (pa.elapsed_time(pb) / 1e3), "unit": UNIT, "stamps": pn,

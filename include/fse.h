@@ -106,7 +106,7 @@ typedef struct {
     double  re_max_frac;    /* upper bound on r_e = re_max_frac * max(h, w)   (2)       */
     double  lm_lambda0;     /* initial Levenberg-Marquardt damping            (1e-3)    */
     uint32_t flags;         /* reserved, 0                                              */
-    int32_t warps_per_cta;  /* launch shape (0 = library choice)                        */
+    int32_t warps_per_cta;  /* launch shape: 0 (library choice), 1, 2, 4 or 8                      */
 } fse_opts;
 
 /* Per-stamp result (64 bytes). */

@@ -94,8 +94,8 @@ int check_opts(fse_ctx* ctx, const fse_opts* o) {
     if (!(o->re_min > 0 && o->re_max_frac > 0)) return set_error(ctx, FSE_EINVAL, "r_e bounds must be positive");
     if (!(o->lm_lambda0 > 0)) return set_error(ctx, FSE_EINVAL, "lm_lambda0 must be positive");
     const int w = o->warps_per_cta;
-    if (!(w == 0 || w == 1 || w == 2 || w == 4 || w == 8 || w == 16))
-        return set_error(ctx, FSE_EINVAL, "warps_per_cta must be 0, 1, 2, 4, 8 or 16");
+    if (!(w == 0 || w == 1 || w == 2 || w == 4 || w == 8))
+        return set_error(ctx, FSE_EINVAL, "warps_per_cta must be 0, 1, 2, 4 or 8");
     return FSE_OK;
 }
 

@@ -47,8 +47,8 @@ struct LaunchArgs {
 
 // Number of nodes of the b(n) table and its range.
 constexpr double kBnLo = 0.125;
-constexpr double kBnStep = 1.0 / 256.0;
-constexpr int kBnNodes = 2600;   // covers [0.125, 10.27]
+constexpr double kBnStep = 1.0 / 512.0;
+constexpr int kBnNodes = 5200;   // covers [0.125, 10.28]
 
 // Builds the b(n), b'(n) table of the current device (idempotent per device).
 cudaError_t build_bn_table(cudaStream_t stream);

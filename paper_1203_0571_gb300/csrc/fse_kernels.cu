@@ -28,8 +28,10 @@ constexpr double kSqrt2Ln2 = 1.1774100225154747;   // half-light radius / sigma 
 constexpr double kPi = 3.141592653589793;
 constexpr unsigned kWaitLimit = 1u << 22;          // bounded mbarrier polls
 
-// (b(n), b'(n)) at n_k = kBnLo + k kBnStep, built once per device.
+// (b(n), b'(n)) at n_k = kBnLo + k kBnStep, built once per device in FP64;
+// g_bnf holds the same nodes rounded to fp32 for the fit's per-iteration use.
 __device__ double2 g_bn[kBnNodes];
+__device__ float2 g_bnf[kBnNodes];
 
 // ------------------------------------------------------------------ PTX
 __device__ __forceinline__ float ex2(float x) {
@@ -152,7 +154,9 @@ __global__ void build_bn_kernel() {
     }
     gamma_p_series(a, b, &P, &dPda);
     const double dPdx = exp((a - 1.0) * log(b) - b - lgamma(a));
-    g_bn[k] = make_double2(b, -2.0 * dPda / dPdx);
+    const double db = -2.0 * dPda / dPdx;
+    g_bn[k] = make_double2(b, db);
+    g_bnf[k] = make_float2(static_cast<float>(b), static_cast<float>(db));
 }
 
 // Cubic Hermite interpolation of the table (b from b and b' at the nodes;
@@ -170,6 +174,21 @@ __device__ __forceinline__ void bn_eval(double n, double* b, double* db) {
     *db = ((6 * t2 - 6 * t) * p0.x + (3 * t2 - 4 * t + 1) * h * p0.y + (-6 * t2 + 6 * t) * p1.x +
            (3 * t2 - 2 * t) * h * p1.y) /
           h;
+}
+
+// The same interpolation in fp32 from the rounded nodes (fit iterations).
+__device__ __forceinline__ void bn_eval_f(float n, float* b, float* db) {
+    const float x = (n - static_cast<float>(kBnLo)) * static_cast<float>(1.0 / kBnStep);
+    int k = static_cast<int>(floorf(x));
+    k = k < 0 ? 0 : (k > kBnNodes - 2 ? kBnNodes - 2 : k);
+    const float t = x - static_cast<float>(k);
+    const float2 p0 = g_bnf[k], p1 = g_bnf[k + 1];
+    const float h = static_cast<float>(kBnStep);
+    const float t2 = t * t, t3 = t2 * t;
+    *b = p0.x + t2 * (3.f - 2.f * t) * (p1.x - p0.x) + (t3 - 2.f * t2 + t) * h * p0.y +
+         (t3 - t2) * h * p1.y;
+    *db = (6.f * (t - t2) * (p1.x - p0.x) + (3.f * t2 - 4.f * t + 1.f) * h * p0.y +
+           (3.f * t2 - 2.f * t) * h * p1.y) * static_cast<float>(1.0 / kBnStep);
 }
 
 __global__ void eval_bn_kernel(const double* n, double* b, double* db, int64_t count) {
@@ -588,22 +607,21 @@ __device__ InitOut stamp_init(const float* s, int h, int w, int npix, int lane,
 // reduced 2x2 problem in (r_e, n):
 //   dm/dr_e = I0 b v / (n r_e),  dm/dn = I0 (b ln2 / n^2) v a - I0 b'(n) v.
 struct FitEval {
-    double I0;       // Eq. 13 at (r_e, n)
-    double chi2;     // Eq. 11 at that I0
-    double g[2];     // J^T r of the reduced problem
-    double H[3];     // J^T J of the reduced problem (00, 01, 11)
+    float I0;       // Eq. 13 at (r_e, n)
+    float chi2;     // Eq. 11 at that I0
+    float g[2];     // J^T r of the reduced problem
+    float H[3];     // J^T J of the reduced problem (00, 01, 11)
 };
 
 template <bool IVAR>
 __device__ FitEval fit_eval(const float* __restrict__ s, const float* __restrict__ L,
-                            const float* __restrict__ sq, int npix, int lane, double I0g,
-                            double re, double n, double lq) {
-    double b, db;
-    bn_eval(n, &b, &db);
-    const float inv_n = static_cast<float>(1.0 / n);
-    const float nbl = static_cast<float>(-b * 1.4426950408889634);
-    const float c0 = static_cast<float>(log2(re) + lq);
-    const float I0f = static_cast<float>(I0g);
+                            const float* __restrict__ sq, int npix, int lane, float I0g,
+                            float re, float n, float lq) {
+    float b, db;
+    bn_eval_f(n, &b, &db);
+    const float inv_n = 1.f / n;
+    const float nbl = -b * kLog2e;
+    const float c0 = log2f(re) + lq;
     float acc[10];
 #pragma unroll
     for (int i = 0; i < 10; ++i) acc[i] = 0.f;
@@ -611,7 +629,7 @@ __device__ FitEval fit_eval(const float* __restrict__ s, const float* __restrict
         const float a = L[p] - c0;
         const float u = ex2(a * inv_n);
         float E = ex2(u * nbl);
-        float r = fmaf(I0f, E, -s[p]);
+        float r = fmaf(I0g, E, -s[p]);
         if (IVAR) {
             const float q = sq[p];
             E *= q;
@@ -631,23 +649,24 @@ __device__ FitEval fit_eval(const float* __restrict__ s, const float* __restrict
     }
     warp_allsum(acc);
     FitEval f;
-    const double sEE = acc[0], sEv = acc[1], sEva = acc[2], svv = acc[3], svva = acc[4],
-                 svaa = acc[5], sEr = acc[6], svr = acc[7], svar = acc[8], srr = acc[9];
-    const double d = -sEr / sEE;                 // I0* - I0g
+    const float sEE = acc[0], sEv = acc[1], sEva = acc[2], svv = acc[3], svva = acc[4],
+                svaa = acc[5], sEr = acc[6], svr = acc[7], svar = acc[8], srr = acc[9];
+    const float iE = 1.f / sEE;
+    const float d = -sEr * iE;                  // I0* - I0g
     f.I0 = I0g + d;
-    f.chi2 = srr + d * sEr;                      // = sum (I0* E - I)^2
-    const double k2 = f.I0 * b / (n * re);
-    const double kA = f.I0 * b * kLn2 / (n * n);
-    const double kB = f.I0 * db;
-    const double svr_s = svr + d * sEv, svar_s = svar + d * sEva;
-    const double Cvv = svv - sEv * sEv / sEE;
-    const double Cvva = svva - sEv * sEva / sEE;
-    const double Cvaa = svaa - sEva * sEva / sEE;
+    f.chi2 = fmaf(d, sEr, srr);                 // = sum (I0* E - I)^2
+    const float k2 = f.I0 * b / (n * re);
+    const float kA = f.I0 * b * static_cast<float>(kLn2) * inv_n * inv_n;
+    const float kB = f.I0 * db;
+    const float svr_s = fmaf(d, sEv, svr), svar_s = fmaf(d, sEva, svar);
+    const float Cvv = svv - sEv * sEv * iE;
+    const float Cvva = svva - sEv * sEva * iE;
+    const float Cvaa = svaa - sEva * sEva * iE;
     f.g[0] = k2 * svr_s;
     f.g[1] = kA * svar_s - kB * svr_s;
     f.H[0] = k2 * k2 * Cvv;
     f.H[1] = k2 * (kA * Cvva - kB * Cvv);
-    f.H[2] = kA * kA * Cvaa - 2.0 * kA * kB * Cvva + kB * kB * Cvv;
+    f.H[2] = kA * kA * Cvaa - 2.f * kA * kB * Cvva + kB * kB * Cvv;
     return f;
 }
 
@@ -655,18 +674,18 @@ __device__ FitEval fit_eval(const float* __restrict__ s, const float* __restrict
 // lowest chi^2 at its closed-form I0 (chi^2 = sum I^2 - (sum I E)^2 / sum E^2).
 template <bool IVAR>
 __device__ void fit_start(const float* __restrict__ s, const float* __restrict__ L,
-                          const float* __restrict__ sq, int npix, int lane, double re0, double lq,
-                          double* n0, double* I00) {
-    const double nc[4] = {0.5, 1.0, 2.0, 4.0};
+                          const float* __restrict__ sq, int npix, int lane, float re0, float lq,
+                          float* n0, float* I00) {
+    const float nc[4] = {0.5f, 1.f, 2.f, 4.f};
     float inv_n[4], nbl[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        double b, db;
-        bn_eval(nc[c], &b, &db);
-        inv_n[c] = static_cast<float>(1.0 / nc[c]);
-        nbl[c] = static_cast<float>(-b * 1.4426950408889634);
+        float b, db;
+        bn_eval_f(nc[c], &b, &db);
+        inv_n[c] = 1.f / nc[c];
+        nbl[c] = -b * kLog2e;
     }
-    const float c0 = static_cast<float>(log2(re0) + lq);
+    const float c0 = log2f(re0) + lq;
     float acc[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) acc[i] = 0.f;
@@ -686,22 +705,22 @@ __device__ void fit_start(const float* __restrict__ s, const float* __restrict__
     }
     warp_allsum(acc);
     int best = 0;
-    double bc = INFINITY;
+    float bc = INFINITY;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        const double sEE = acc[2 * c], sEI = acc[2 * c + 1];
-        const double chi2 = static_cast<double>(acc[8]) - sEI * sEI / sEE;
-        if (sEE > 0.0 && chi2 < bc) {
+        const float sEE = acc[2 * c], sEI = acc[2 * c + 1];
+        const float chi2 = acc[8] - sEI * sEI / sEE;
+        if (sEE > 0.f && chi2 < bc) {
             bc = chi2;
             best = c;
         }
     }
     *n0 = nc[best];
-    *I00 = acc[2 * best] > 0.f ? static_cast<double>(acc[2 * best + 1]) / acc[2 * best] : 1.0;
+    *I00 = acc[2 * best] > 0.f ? acc[2 * best + 1] / acc[2 * best] : 1.f;
 }
 
 struct FitOut {
-    double I0, re, n, chi2, flux;
+    float I0, re, n, chi2, flux;
     int iters;
 };
 
@@ -725,58 +744,59 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
         }
         __syncwarp();
     }
-    const double gabs = sqrt(static_cast<double>(gg));
-    const double lq = log2(1.0 - gabs);          // log2 r = 0.5 log2 R^2 - log2(1 - |g|)
-    const double re_max = o.re_max_frac * static_cast<double>(h > w ? h : w);
-    const double re_min = o.re_min, n_min = o.n_min, n_max = o.n_max;
-    double re = kSqrt2Ln2 * static_cast<double>(st.sw) / (1.0 - gabs);
+    const float gabs = sqrtf(gg);
+    const float lq = log2f(1.f - gabs);          // log2 r = 0.5 log2 R^2 - log2(1 - |g|)
+    const float re_max = o.re_max_frac * static_cast<float>(h > w ? h : w);
+    const float re_min = o.re_min, n_min = o.n_min, n_max = o.n_max;
+    float re = static_cast<float>(kSqrt2Ln2) * st.sw / (1.f - gabs);
     re = re < re_min ? re_min : (re > re_max ? re_max : re);
-    double n, I0g;
+    float n, I0g;
     fit_start<IVAR>(s, L, sq, npix, lane, re, lq, &n, &I0g);
     FitEval cur = fit_eval<IVAR>(s, L, sq, npix, lane, I0g, re, n, lq);
     int evals = 1;
-    double lambda = o.lm_lambda0, nu = 2.0;
+    float lambda = o.lm_lambda0, nu = 2.f;
     bool converged = false;
     const bool finite0 = isfinite(cur.chi2) && isfinite(cur.g[0]) && isfinite(cur.g[1]) &&
                          isfinite(cur.H[0]) && isfinite(cur.H[1]) && isfinite(cur.H[2]);
     if (!finite0) status |= FSE_ST_FIT_SINGULAR;
     int it;
     for (it = 1; finite0 && it <= o.max_iter_fit; ++it) {
-        const double M00 = cur.H[0] * (1.0 + lambda), M11 = cur.H[2] * (1.0 + lambda);
-        const double M01 = cur.H[1];
-        const double det = M00 * M11 - M01 * M01;
-        if (!(det > 0.0) || !isfinite(det)) {
+        const float M00 = cur.H[0] * (1.f + lambda), M11 = cur.H[2] * (1.f + lambda);
+        const float M01 = cur.H[1];
+        const float det = M00 * M11 - M01 * M01;
+        if (!(det > 0.f) || !isfinite(det)) {
             status |= FSE_ST_FIT_SINGULAR;
             break;
         }
-        const double d0 = (-M11 * cur.g[0] + M01 * cur.g[1]) / det;
-        const double d1 = (M01 * cur.g[0] - M00 * cur.g[1]) / det;
-        double qre = re + d0, qn = n + d1;
+        const float idet = 1.f / det;
+        const float d0 = (-M11 * cur.g[0] + M01 * cur.g[1]) * idet;
+        const float d1 = (M01 * cur.g[0] - M00 * cur.g[1]) * idet;
+        float qre = re + d0, qn = n + d1;
         qre = qre < re_min ? re_min : (qre > re_max ? re_max : qre);
         qn = qn < n_min ? n_min : (qn > n_max ? n_max : qn);
-        const double s0 = qre - re, s1 = qn - n;
-        const double step = fmax(fabs(s0) / re, fabs(s1) / n);
+        const float s0 = qre - re, s1 = qn - n;
+        const float step = fmaxf(fabsf(s0) / re, fabsf(s1) / n);
         if (step <= o.tol_fit) {
             converged = true;
             break;
         }
-        const double pred = -(2.0 * (cur.g[0] * s0 + cur.g[1] * s1) +
-                              s0 * (cur.H[0] * s0 + cur.H[1] * s1) +
-                              s1 * (cur.H[1] * s0 + cur.H[2] * s1));
+        const float pred = -(2.f * (cur.g[0] * s0 + cur.g[1] * s1) +
+                             s0 * (cur.H[0] * s0 + cur.H[1] * s1) +
+                             s1 * (cur.H[1] * s0 + cur.H[2] * s1));
         const FitEval nxt = fit_eval<IVAR>(s, L, sq, npix, lane, cur.I0, qre, qn, lq);
         ++evals;
         if (nxt.chi2 < cur.chi2) {
-            const double rho = pred > 0.0 ? (cur.chi2 - nxt.chi2) / pred : 1.0;
-            const double t = 2.0 * rho - 1.0;
-            lambda *= fmax(1.0 / 3.0, 1.0 - t * t * t);
-            nu = 2.0;
+            const float rho = pred > 0.f ? (cur.chi2 - nxt.chi2) / pred : 1.f;
+            const float t = 2.f * rho - 1.f;
+            lambda *= fmaxf(1.f / 3.f, 1.f - t * t * t);
+            nu = 2.f;
             re = qre;
             n = qn;
             cur = nxt;
         } else {
             lambda *= nu;
-            nu *= 2.0;
-            if (lambda > 1e15) {
+            nu *= 2.f;
+            if (lambda > 1e15f) {
                 converged = true;
                 break;
             }
@@ -785,23 +805,24 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
     if (converged && isfinite(cur.chi2)) status |= FSE_ST_FIT_CONVERGED;
     else if (finite0 && it > o.max_iter_fit) status |= FSE_ST_FIT_MAXITER;
     if (re <= re_min || re >= re_max || n <= n_min || n >= n_max) status |= FSE_ST_FIT_BOUND;
-    if (!(cur.I0 > 0.0)) status |= FSE_ST_NONPOS_FLUX;
+    if (!(cur.I0 > 0.f)) status |= FSE_ST_NONPOS_FLUX;
     FitOut out;
     out.I0 = cur.I0;
     out.re = re;
     out.n = n;
     out.chi2 = cur.chi2;
     out.iters = evals;
-    double b, db;
-    bn_eval(n, &b, &db);
-    const double q = (1.0 - gabs) / (1.0 + gabs);
-    out.flux = 2.0 * kPi * n * exp(lgamma(2.0 * n) - 2.0 * n * log(b)) * cur.I0 * re * re * q;
+    float b, db;
+    bn_eval_f(n, &b, &db);
+    const float q = (1.f - gabs) / (1.f + gabs);
+    out.flux = 2.f * static_cast<float>(kPi) * n * expf(lgammaf(2.f * n) - 2.f * n * logf(b)) *
+               cur.I0 * re * re * q;
     return out;
 }
 
 // ------------------------------------------------------------------ kernel
 template <int STAGE, int DT, bool IVAR>
-__global__ void __launch_bounds__(512) estimator_kernel(LaunchArgs a) {
+__global__ void __launch_bounds__(256, 1) estimator_kernel(LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;

@@ -100,6 +100,12 @@ def compare(gpu, orc, keys=("x0", "y0", "e1", "e2", "re", "n", "flux", "chi2"), 
         "p99_err": {k: float(np.percentile(err[k][gate], 99)) if gate.any() else 0.0 for k in keys},
         "failing": [int(j) for j in np.nonzero(gate & ~ok)[0][:50]],
     }
+    bad = np.nonzero((gate & ~ok) | excluded_basin)[0][:40]
+    rep["detail"] = [{"j": int(j), "id": int(ids[j]) if ids is not None else int(j),
+                      "excluded_other_minimum": bool(excluded_basin[j]),
+                      "gpu": {k: float(gpu[k][j]) for k in gpu.dtype.names},
+                      "orc": {k: float(orc[k][j]) for k in orc.dtype.names},
+                      "err": {k: float(err[k][j]) for k in keys}} for j in bad]
     rep["_err"] = err
     rep["_gate"] = gate
     return rep
