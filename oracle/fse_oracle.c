@@ -329,8 +329,22 @@ static moment_step weighted_pass(const double *I, int h, int w, double xc, doubl
         }
     }
     if (!(N > 0.0)) return s;
-    s.dx = mx / (k_gain * N);                     /* Eqs. 5-6: <x>/N = k dx */
-    s.dy = my / (k_gain * N);
+    if (k_gain > 0.0) {
+        s.dx = mx / (k_gain * N);                 /* Eqs. 5-6: <x>/N = k dx */
+        s.dy = my / (k_gain * N);
+    } else {
+        /* k "determined iteratively" (Sec. 2): Newton on (<x>, <y>) = 0 with the
+         * derivative of the weighted first moments with respect to the centre,
+         * d<x>/dx_c = sum I [dW/dx_c theta_1 - W], dW/dx_c = 2 c W (A t1 - 2 g2 t2). */
+        double J11 = 2.0 * c * (A * Q11 - 2.0 * gw2 * Q12) - N;
+        double J12 = 2.0 * c * (B * Q12 - 2.0 * gw2 * Q11);
+        double J21 = 2.0 * c * (A * Q12 - 2.0 * gw2 * Q22);
+        double J22 = 2.0 * c * (B * Q22 - 2.0 * gw2 * Q12) - N;
+        double dj = J11 * J22 - J12 * J21;
+        if (!(dj > 0.0)) return s;
+        s.dx = -(J22 * mx - J12 * my) / dj;
+        s.dy = -(-J21 * mx + J11 * my) / dj;
+    }
     s.sigw_new = SWR2 > 0.0 ? sqrt(SWR2 / N) : 0.0;
     if (!ellip) { s.ok = 1; return s; }
     double T = Q11 + Q22;

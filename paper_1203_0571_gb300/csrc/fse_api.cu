@@ -83,7 +83,7 @@ int check_opts(fse_ctx* ctx, const fse_opts* o) {
         return set_error(ctx, FSE_EINVAL, "tolerances must be positive");
     if (o->max_iter_mom < 1 || o->max_iter_mom > 100000 || o->max_iter_fit < 1 || o->max_iter_fit > 100000)
         return set_error(ctx, FSE_EINVAL, "max_iter must be in [1, 100000]");
-    if (!(o->k_gain > 0 && o->k_gain <= 4)) return set_error(ctx, FSE_EINVAL, "k_gain must be in (0, 4]");
+    if (!(o->k_gain >= 0 && o->k_gain <= 4)) return set_error(ctx, FSE_EINVAL, "k_gain must be in [0, 4]");
     if (o->sigw_mode != 0 && o->sigw_mode != 1) return set_error(ctx, FSE_EINVAL, "sigw_mode must be 0 or 1");
     if (o->max_pix < 0 || o->max_pix > FSE_MAX_PIX)
         return set_error(ctx, FSE_EINVAL, "max_pix must be in [0, %d]", FSE_MAX_PIX);

@@ -40,6 +40,35 @@ __device__ __forceinline__ float ex2(float x) {
     return y;
 }
 
+// 2^x to about one ulp, for the final refinement pass: x = k + f with k an
+// integer and |f| <= 1/2, 2^f from the Taylor series of exp(f ln 2) to degree 7
+// (truncation below 6e-9 relative), then the exponent raised by k.
+__device__ __forceinline__ float exp2_acc(float x) {
+    if (!(x >= -126.f)) return 0.f;
+    if (x > 127.f) return INFINITY;
+    const float k = rintf(x);
+    const float f = x - k;
+    float p = 1.5252733804059841e-05f;
+    p = fmaf(p, f, 1.540353039338161e-04f);
+    p = fmaf(p, f, 1.3333558146428443e-03f);
+    p = fmaf(p, f, 9.618129107628477e-03f);
+    p = fmaf(p, f, 5.550410866482158e-02f);
+    p = fmaf(p, f, 2.4022650695910072e-01f);
+    p = fmaf(p, f, 6.931471805599453e-01f);
+    p = fmaf(p, f, 1.f);
+    return __int_as_float(__float_as_int(p) + (static_cast<int>(k) << 23));
+}
+
+// Double-float accumulation: (hi, lo) += b, carrying the exact rounding error
+// of hi + b (Knuth's two-sum) in lo.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float b) {
+    const float s = hi + b;
+    const float bb = s - hi;
+    const float e = (hi - (s - bb)) + (b - bb);
+    hi = s;
+    lo += e;
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -93,6 +122,26 @@ __device__ __forceinline__ long long warp_allsum_ll(long long v) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
     return v;
+}
+
+// Sum of (hi, lo) pairs over the warp.  Both partners of a butterfly form
+// hi + other.hi and its exact error in the same way, so every lane ends with
+// the same pair.
+template <int N>
+__device__ __forceinline__ void warp_allsum_df(float (&hi)[N], float (&lo)[N]) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const float oh = __shfl_xor_sync(kFull, hi[i], off);
+            const float ol = __shfl_xor_sync(kFull, lo[i], off);
+            const float s = hi[i] + oh;
+            const float bb = s - hi[i];
+            const float e = (hi[i] - (s - bb)) + (oh - bb);
+            lo[i] = (lo[i] + ol) + e;
+            hi[i] = s;
+        }
+    }
 }
 
 // ------------------------------------------------------------------ b(n)
@@ -354,6 +403,10 @@ struct MomStep {
     bool ok;
 };
 
+__device__ __forceinline__ void shear_polarizability(const float (&m)[11], const MomState& st,
+                                                     float e1, float e2, float* P11, float* P12,
+                                                     float* P21, float* P22);
+
 // The centroid step <x>/N = k dx (Eqs. 5-6) and the ellipticity step
 // dg = (1-|g_w|^2) (P^SH)^-1 (e^obs - e_w) (Eq. 9) with
 // P^SH = X^SH + dX^SH - e (e^SH + de^SH)^T (Eq. 8, A5, A6, B7, B8), evaluated
@@ -366,13 +419,28 @@ __device__ __forceinline__ MomStep moment_step(const float (&m)[11], const MomSt
     r.sw_new = st.sw;
     const float S0 = m[0];
     const float Q11 = m[3], Q12 = m[4], Q22 = m[5];
-    const float F40 = m[6], F31 = m[7], F22 = m[8], F13 = m[9], F04 = m[10];
     const float g1 = st.g1, g2 = st.g2;
     const float gg = g1 * g1 + g2 * g2;
     const float A = 1.f + gg - 2.f * g1, B = 1.f + gg + 2.f * g1;
     if (!(S0 > 0.f)) return r;
-    r.dx = m[1] / (k_gain * S0);
-    r.dy = m[2] / (k_gain * S0);
+    const float c = 1.f / (2.f * st.sw * st.sw);
+    if (k_gain > 0.f) {
+        // Eqs. 5-6 with the fixed gain k
+        r.dx = m[1] / (k_gain * S0);
+        r.dy = m[2] / (k_gain * S0);
+    } else {
+        // k determined from the current moments: the derivative of
+        // (sum I W theta_1, sum I W theta_2) with respect to the centre, which
+        // for a Gaussian profile is k = s_w^2 / (s^2 + s_w^2) (Sec. 2)
+        const float J11 = 2.f * c * (A * Q11 - 2.f * g2 * Q12) - S0;
+        const float J12 = 2.f * c * (B * Q12 - 2.f * g2 * Q11);
+        const float J21 = 2.f * c * (A * Q12 - 2.f * g2 * Q22);
+        const float J22 = 2.f * c * (B * Q22 - 2.f * g2 * Q12) - S0;
+        const float dj = J11 * J22 - J12 * J21;
+        if (!(dj > 0.f)) return r;
+        r.dx = -(J22 * m[1] - J12 * m[2]) / dj;
+        r.dy = -(-J21 * m[1] + J11 * m[2]) / dj;
+    }
     const float SR2 = A * Q11 + B * Q22 - 4.f * g2 * Q12;      // sum f W R^2
     r.sw_new = SR2 > 0.f ? sqrtf(SR2 / S0) : 0.f;
     if (!ellip) {
@@ -381,8 +449,32 @@ __device__ __forceinline__ MomStep moment_step(const float (&m)[11], const MomSt
     }
     const float T = Q11 + Q22;
     if (!(T > 0.f)) return r;
+    const float e1 = (Q11 - Q22) / T, e2 = 2.f * Q12 / T;
+    float P11, P12, P21, P22;
+    shear_polarizability(m, st, e1, e2, &P11, &P12, &P21, &P22);
+    const float det = P11 * P22 - P12 * P21;
+    if (!(fabsf(det) > 0.f) || !isfinite(det)) return r;
+    const float ew = 2.f / (1.f + gg);
+    const float r1 = e1 - ew * g1, r2 = e2 - ew * g2;
+    const float sc = (1.f - gg) / det;
+    r.dg1 = sc * (P22 * r1 - P12 * r2);
+    r.dg2 = sc * (-P21 * r1 + P11 * r2);
+    r.ok = isfinite(r.dg1) && isfinite(r.dg2) && isfinite(r.dx) && isfinite(r.dy);
+    return r;
+}
+
+// P^SH = X^SH + dX^SH - e (e^SH + de^SH)^T (Eq. 8 with A5, A6, B7, B8) from the
+// eleven weighted moments; W' = dW/dR^2 = -c W with c = 1/(2 s_w^2).
+__device__ __forceinline__ void shear_polarizability(const float (&m)[11], const MomState& st,
+                                                     float e1, float e2, float* P11, float* P12,
+                                                     float* P21, float* P22) {
+    const float Q11 = m[3], Q12 = m[4], Q22 = m[5];
+    const float F40 = m[6], F31 = m[7], F22 = m[8], F13 = m[9], F04 = m[10];
+    const float g1 = st.g1, g2 = st.g2;
+    const float gg = g1 * g1 + g2 * g2;
+    const float A = 1.f + gg - 2.f * g1, B = 1.f + gg + 2.f * g1;
+    const float T = Q11 + Q22;
     const float iT = 1.f / T;
-    const float e1 = (Q11 - Q22) * iT, e2 = 2.f * Q12 * iT;
     const float c = 1.f / (2.f * st.sw * st.sw);
     const float ApB = A + B, AmB = A - B;
     const float F31m13 = F31 - F13, F31p13 = F31 + F13;
@@ -413,23 +505,110 @@ __device__ __forceinline__ MomStep moment_step(const float (&m)[11], const MomSt
     X22 += (g1 * P4 - g2 * P3) * iT;
     eS1 += (-g1 * P5 - g2 * P6) * iT;
     eS2 += (g1 * P6 - g2 * P5) * iT;
-    const float P11 = X11 - e1 * eS1, P12 = X12 - e1 * eS2;
-    const float P21 = X21 - e2 * eS1, P22 = X22 - e2 * eS2;
-    const float det = P11 * P22 - P12 * P21;
-    if (!(fabsf(det) > 0.f) || !isfinite(det)) return r;
-    const float ew = 2.f / (1.f + gg);
-    const float r1 = e1 - ew * g1, r2 = e2 - ew * g2;
-    const float sc = (1.f - gg) / det;
-    r.dg1 = sc * (P22 * r1 - P12 * r2);
-    r.dg2 = sc * (-P21 * r1 + P11 * r2);
-    r.ok = isfinite(r.dg1) && isfinite(r.dg2) && isfinite(r.dx) && isfinite(r.dy);
-    return r;
+    *P11 = X11 - e1 * eS1;
+    *P12 = X12 - e1 * eS2;
+    *P21 = X21 - e2 * eS1;
+    *P22 = X22 - e2 * eS2;
+}
+
+// Final refinement of the fixed point: one pass with the pixel offsets theta
+// kept exactly as float pairs, W to about one ulp (exp2_acc) and the
+// zeroth, first and second moments accumulated in double-float, followed by
+// one step from these sums: a Newton step for the centre (the derivative of
+// the weighted first moments, i.e. k taken from the moments) and the step of
+// Eq. 9 for g.  The fp32 iteration stops within the noise of its own sums
+// (~1e-6 px); this pass removes most of that noise.
+__device__ void moment_refine(const float* __restrict__ s, int w, int npix, int lane, bool ellip,
+                              MomState& st) {
+    const float gg = st.g1 * st.g1 + st.g2 * st.g2;
+    const float A = 1.f + gg - 2.f * st.g1;
+    const float B = 1.f + gg + 2.f * st.g1;
+    const float G4 = 4.f * st.g2;
+    const float cw = -kLog2e / (2.f * st.sw * st.sw);
+    float dh[6], dl[6], cx[5], F[5];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) dh[i] = dl[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) cx[i] = F[i] = 0.f;
+    PixelWalk pw(lane, w);
+    for (int p = lane; p < npix; p += 32) {
+        const float k1 = static_cast<float>(pw.col - st.xi), k2 = static_cast<float>(pw.row - st.yi);
+        // theta = k - x_f exactly as hi + lo (|k| >= |x_f| unless k = 0, where lo = 0)
+        const float t1 = k1 - st.xf, t1l = -st.xf - (t1 - k1);
+        const float t2 = k2 - st.yf, t2l = -st.yf - (t2 - k2);
+        const float t11 = t1 * t1, t22 = t2 * t2, t12 = t1 * t2;
+        const float R2 = fmaf(A, t11, fmaf(B, t22, -G4 * t12));
+        const float f = s[p] * exp2_acc(R2 * cw);
+        df_add(dh[0], dl[0], f);
+        df_add(dh[1], dl[1], f * t1);
+        df_add(dh[2], dl[2], f * t2);
+        df_add(dh[3], dl[3], f * t11);
+        df_add(dh[4], dl[4], f * t12);
+        df_add(dh[5], dl[5], f * t22);
+        cx[0] = fmaf(f, t1l, cx[0]);
+        cx[1] = fmaf(f, t2l, cx[1]);
+        cx[2] = fmaf(2.f * f * t1, t1l, cx[2]);
+        cx[3] = fmaf(f, fmaf(t1, t2l, t1l * t2), cx[3]);
+        cx[4] = fmaf(2.f * f * t2, t2l, cx[4]);
+        const float f11 = f * t11, f22 = f * t22;
+        F[0] = fmaf(f11, t11, F[0]);
+        F[1] = fmaf(f11, t12, F[1]);
+        F[2] = fmaf(f11, t22, F[2]);
+        F[3] = fmaf(f22, t12, F[3]);
+        F[4] = fmaf(f22, t22, F[4]);
+        pw.next();
+    }
+    warp_allsum_df(dh, dl);
+    warp_allsum(cx);
+    warp_allsum(F);
+    const double M0 = static_cast<double>(dh[0]) + dl[0];
+    const double M1x = static_cast<double>(dh[1]) + dl[1] + cx[0];
+    const double M1y = static_cast<double>(dh[2]) + dl[2] + cx[1];
+    const double Q11 = static_cast<double>(dh[3]) + dl[3] + cx[2];
+    const double Q12 = static_cast<double>(dh[4]) + dl[4] + cx[3];
+    const double Q22 = static_cast<double>(dh[5]) + dl[5] + cx[4];
+    if (!(M0 > 0.0) || !(Q11 + Q22 > 0.0)) return;
+    const double c = 1.0 / (2.0 * static_cast<double>(st.sw) * st.sw);
+    const double g1 = st.g1, g2 = st.g2, Ad = A, Bd = B;
+    const double J11 = 2.0 * c * (Ad * Q11 - 2.0 * g2 * Q12) - M0;
+    const double J12 = 2.0 * c * (Bd * Q12 - 2.0 * g2 * Q11);
+    const double J21 = 2.0 * c * (Ad * Q12 - 2.0 * g2 * Q22);
+    const double J22 = 2.0 * c * (Bd * Q22 - 2.0 * g2 * Q12) - M0;
+    const double dj = J11 * J22 - J12 * J21;
+    if (!(dj > 0.0)) return;
+    const float dx = static_cast<float>(-(J22 * M1x - J12 * M1y) / dj);
+    const float dy = static_cast<float>(-(-J21 * M1x + J11 * M1y) / dj);
+    float dg1 = 0.f, dg2 = 0.f;
+    if (ellip) {
+        const double T = Q11 + Q22;
+        const double e1 = (Q11 - Q22) / T, e2 = 2.0 * Q12 / T;
+        const float m[11] = {static_cast<float>(M0), static_cast<float>(M1x), static_cast<float>(M1y),
+                             static_cast<float>(Q11), static_cast<float>(Q12), static_cast<float>(Q22),
+                             F[0], F[1], F[2], F[3], F[4]};
+        float P11, P12, P21, P22;
+        shear_polarizability(m, st, static_cast<float>(e1), static_cast<float>(e2), &P11, &P12, &P21, &P22);
+        const float det = P11 * P22 - P12 * P21;
+        if (!(fabsf(det) > 0.f) || !isfinite(det)) return;
+        const double ew = 2.0 / (1.0 + g1 * g1 + g2 * g2);
+        const float r1 = static_cast<float>(e1 - ew * g1), r2 = static_cast<float>(e2 - ew * g2);
+        const float sc = (1.f - gg) / det;
+        dg1 = sc * (P22 * r1 - P12 * r2);
+        dg2 = sc * (-P21 * r1 + P11 * r2);
+    }
+    // a refinement moves the point by at most the iteration's own noise
+    if (!(fabsf(dx) <= 1e-3f && fabsf(dy) <= 1e-3f && fabsf(dg1) <= 1e-3f && fabsf(dg2) <= 1e-3f))
+        return;
+    st.xf += dx;
+    st.yf += dy;
+    st.g1 += dg1;
+    st.g2 += dg2;
 }
 
 // Iterate to the stop rule.  Returns the number of passes; sets status bits.
 __device__ int moment_iterate(const float* s, int h, int w, int npix, int lane, const DevOpts& o,
                               bool ellip, MomState& st, uint32_t& status) {
     const float sw_max = 0.5f * static_cast<float>(h < w ? h : w);
+    float prev = 0.f;   // size of the previous step, for the contraction estimate
     int it;
     for (it = 1; it <= o.max_iter_mom; ++it) {
         float m[11];
@@ -477,8 +656,17 @@ __device__ int moment_iterate(const float* s, int h, int w, int npix, int lane, 
             status |= FSE_ST_MOM_FAILED;
             break;
         }
-        if (fabsf(d.dx) <= o.tol_pos && fabsf(d.dy) <= o.tol_pos && fabsf(d.dg1) <= o.tol_g &&
-            fabsf(d.dg2) <= o.tol_g && dsig <= o.tol_sig) {
+        // Stop when the distance left to the fixed point is below the
+        // tolerances.  For a slowly contracting iteration that distance is
+        // estimated as |step| rho / (1 - rho) with rho = |step_k| / |step_k-1|;
+        // steps below a quarter of the tolerances (where the fp32 sums' noise
+        // makes rho meaningless) always stop.
+        const float sz = fmaxf(fmaxf(fabsf(d.dx), fabsf(d.dy)) / o.tol_pos,
+                               fmaxf(fmaxf(fabsf(d.dg1), fabsf(d.dg2)) / o.tol_g, dsig / o.tol_sig));
+        const float rho = prev > 0.f ? fminf(sz / prev, 0.95f) : 0.f;
+        const float left = (sz > 0.25f && rho > 0.5f) ? sz * rho / (1.f - rho) : sz;
+        prev = sz;
+        if (left <= 1.f) {
             status |= FSE_ST_MOM_CONVERGED;
             break;
         }
@@ -487,6 +675,7 @@ __device__ int moment_iterate(const float* s, int h, int w, int npix, int lane, 
         status |= FSE_ST_MOM_MAXITER;
         it = o.max_iter_mom;
     }
+    if (status & FSE_ST_MOM_CONVERGED) moment_refine(s, w, npix, lane, ellip, st);
     return it;
 }
 
@@ -611,6 +800,7 @@ struct FitEval {
     float chi2;     // Eq. 11 at that I0
     float g[2];     // J^T r of the reduced problem
     float H[3];     // J^T J of the reduced problem (00, 01, 11)
+    float corr;     // (I0 - I0g)^2 sum E^2 / chi2: cancellation in chi2 when large
 };
 
 template <bool IVAR>
@@ -655,6 +845,7 @@ __device__ FitEval fit_eval(const float* __restrict__ s, const float* __restrict
     const float d = -sEr * iE;                  // I0* - I0g
     f.I0 = I0g + d;
     f.chi2 = fmaf(d, sEr, srr);                 // = sum (I0* E - I)^2
+    f.corr = d * d * sEE / fmaxf(f.chi2, 1e-30f);
     const float k2 = f.I0 * b / (n * re);
     const float kA = f.I0 * b * static_cast<float>(kLn2) * inv_n * inv_n;
     const float kB = f.I0 * db;
@@ -719,8 +910,100 @@ __device__ void fit_start(const float* __restrict__ s, const float* __restrict__
     *I00 = acc[2 * best] > 0.f ? acc[2 * best + 1] / acc[2 * best] : 1.f;
 }
 
+// Final refinement at the LM optimum: one pass with both exponentials to
+// about one ulp (exp2_acc), the residual sums sum E r, sum v r, sum v a r and
+// sum r^2 accumulated in double-float, then one Gauss-Newton step of the
+// reduced problem and chi^2 from its quadratic model.  The fp32 LM stops
+// within the noise of its own sums; this pass removes most of that noise.
+struct Refined {
+    double I0, re, n, chi2;
+    bool applied;
+};
+
+template <bool IVAR>
+__device__ Refined fit_refine(const float* __restrict__ s, const float* __restrict__ L,
+                              const float* __restrict__ sq, int npix, int lane, float I0g,
+                              float re, float n, float lq) {
+    float bf, dbf;
+    bn_eval_f(n, &bf, &dbf);
+    const float inv_n = 1.f / n;
+    const float nbl = -bf * kLog2e;
+    const float c0 = log2f(re) + lq;
+    float rh[10], rl[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) rh[i] = rl[i] = 0.f;
+    for (int p = lane; p < npix; p += 32) {
+        const float a = L[p] - c0;
+        const float u = exp2_acc(a * inv_n);
+        float E = exp2_acc(u * nbl);
+        float r = fmaf(I0g, E, -s[p]);
+        if (IVAR) {
+            const float q = sq[p];
+            E *= q;
+            r *= q;
+        }
+        const float v = E * u, va = v * a;
+        df_add(rh[0], rl[0], E * E);
+        df_add(rh[1], rl[1], E * v);
+        df_add(rh[2], rl[2], E * va);
+        df_add(rh[3], rl[3], v * v);
+        df_add(rh[4], rl[4], v * va);
+        df_add(rh[5], rl[5], va * va);
+        df_add(rh[6], rl[6], E * r);
+        df_add(rh[7], rl[7], v * r);
+        df_add(rh[8], rl[8], va * r);
+        df_add(rh[9], rl[9], r * r);
+    }
+    warp_allsum_df(rh, rl);
+    // The sums are exact to about 1e-14 relative; the quantities that vanish at
+    // the optimum (the gradient) are formed from them in fp32 only after the
+    // cancellation has happened inside the double-float sums.
+    float S[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) S[i] = rh[i] + rl[i];
+    const float sEE = S[0], sEv = S[1], sEva = S[2], svv = S[3], svva = S[4], svaa = S[5];
+    const float sEr = S[6], svr = S[7], svar = S[8];
+    Refined o;
+    const float d = -sEr / sEE;
+    const float I0 = I0g + d;
+    // chi^2 at I0*: sum r^2 + d sum E r, with sum r^2 kept as a float pair
+    const double chi2 = (static_cast<double>(rh[9]) + rl[9]) + static_cast<double>(d) * sEr;
+    const float k2 = I0 * bf / (n * re);
+    const float kA = I0 * bf * static_cast<float>(kLn2) * inv_n * inv_n;
+    const float kB = I0 * dbf;
+    const float svr_s = fmaf(d, sEv, svr), svar_s = fmaf(d, sEva, svar);
+    const float Cvv = svv - sEv * sEv / sEE;
+    const float Cvva = svva - sEv * sEva / sEE;
+    const float Cvaa = svaa - sEva * sEva / sEE;
+    const float g0 = k2 * svr_s, g1 = kA * svar_s - kB * svr_s;
+    const float H00 = k2 * k2 * Cvv, H01 = k2 * (kA * Cvva - kB * Cvv);
+    const float H11 = kA * kA * Cvaa - 2.f * kA * kB * Cvva + kB * kB * Cvv;
+    const float det = H00 * H11 - H01 * H01;
+    o.I0 = I0;
+    o.re = re;
+    o.n = n;
+    o.chi2 = chi2;
+    o.applied = false;
+    if (det > 0.f && isfinite(det) && isfinite(chi2)) {
+        const float d0 = (-H11 * g0 + H01 * g1) / det;
+        const float d1 = (H01 * g0 - H00 * g1) / det;
+        if (fabsf(d0) <= 1e-2f * re && fabsf(d1) <= 1e-2f * n) {
+            // I0 follows Eq. 13 to first order along the step
+            const float dI0 = -(k2 * sEv * d0 + (kA * sEva - kB * sEv) * d1) / sEE;
+            o.re = static_cast<double>(re) + d0;
+            o.n = static_cast<double>(n) + d1;
+            o.I0 = static_cast<double>(I0) + dI0;
+            o.chi2 = chi2 + static_cast<double>(2.f * (g0 * d0 + g1 * d1) + d0 * (H00 * d0 + H01 * d1) +
+                                                d1 * (H01 * d0 + H11 * d1));
+            o.applied = true;
+        }
+    }
+    return o;
+}
+
 struct FitOut {
-    float I0, re, n, chi2, flux;
+    float I0, re, n, flux;
+    double chi2;
     int iters;
 };
 
@@ -756,6 +1039,7 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
     int evals = 1;
     float lambda = o.lm_lambda0, nu = 2.f;
     bool converged = false;
+    int band_accepts = 0;
     const bool finite0 = isfinite(cur.chi2) && isfinite(cur.g[0]) && isfinite(cur.g[1]) &&
                          isfinite(cur.H[0]) && isfinite(cur.H[1]) && isfinite(cur.H[2]);
     if (!finite0) status |= FSE_ST_FIT_SINGULAR;
@@ -783,9 +1067,22 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
         const float pred = -(2.f * (cur.g[0] * s0 + cur.g[1] * s1) +
                              s0 * (cur.H[0] * s0 + cur.H[1] * s1) +
                              s1 * (cur.H[1] * s0 + cur.H[2] * s1));
-        const FitEval nxt = fit_eval<IVAR>(s, L, sq, npix, lane, cur.I0, qre, qn, lq);
+        FitEval nxt = fit_eval<IVAR>(s, L, sq, npix, lane, cur.I0, qre, qn, lq);
         ++evals;
-        if (nxt.chi2 < cur.chi2) {
+        if (nxt.corr > 0.5f) {
+            // the amplitude moved so far that chi^2 lost precision: evaluate again at I0*
+            nxt = fit_eval<IVAR>(s, L, sq, npix, lane, nxt.I0, qre, qn, lq);
+            ++evals;
+        }
+        // A step whose predicted decrease is below the resolution of the fp32
+        // chi^2 is accepted when chi^2 stays within that resolution (at most a
+        // few times), so that the iteration reaches the zero of the gradient
+        // instead of stalling on rejections it cannot resolve.
+        const float band = 1e-6f * cur.chi2;
+        const bool better = nxt.chi2 < cur.chi2;
+        const bool in_band = pred <= band && nxt.chi2 <= cur.chi2 + band && band_accepts < 4;
+        if (better || in_band) {
+            if (!better) ++band_accepts;
             const float rho = pred > 0.f ? (cur.chi2 - nxt.chi2) / pred : 1.f;
             const float t = 2.f * rho - 1.f;
             lambda *= fmaxf(1.f / 3.f, 1.f - t * t * t);
@@ -804,19 +1101,27 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
     }
     if (converged && isfinite(cur.chi2)) status |= FSE_ST_FIT_CONVERGED;
     else if (finite0 && it > o.max_iter_fit) status |= FSE_ST_FIT_MAXITER;
-    if (re <= re_min || re >= re_max || n <= n_min || n >= n_max) status |= FSE_ST_FIT_BOUND;
-    if (!(cur.I0 > 0.f)) status |= FSE_ST_NONPOS_FLUX;
     FitOut out;
     out.I0 = cur.I0;
     out.re = re;
     out.n = n;
     out.chi2 = cur.chi2;
+    if (converged && isfinite(cur.chi2) && re > re_min && re < re_max && n > n_min && n < n_max) {
+        const Refined rf = fit_refine<IVAR>(s, L, sq, npix, lane, cur.I0, re, n, lq);
+        out.I0 = static_cast<float>(rf.I0);
+        out.re = static_cast<float>(rf.re);
+        out.n = static_cast<float>(rf.n);
+        out.chi2 = rf.chi2;
+    }
+    if (out.re <= re_min || out.re >= re_max || out.n <= n_min || out.n >= n_max)
+        status |= FSE_ST_FIT_BOUND;
+    if (!(out.I0 > 0.f)) status |= FSE_ST_NONPOS_FLUX;
     out.iters = evals;
     float b, db;
-    bn_eval_f(n, &b, &db);
+    bn_eval_f(out.n, &b, &db);
     const float q = (1.f - gabs) / (1.f + gabs);
-    out.flux = 2.f * static_cast<float>(kPi) * n * expf(lgammaf(2.f * n) - 2.f * n * logf(b)) *
-               cur.I0 * re * re * q;
+    out.flux = 2.f * static_cast<float>(kPi) * out.n *
+               expf(lgammaf(2.f * out.n) - 2.f * out.n * logf(b)) * out.I0 * out.re * out.re * q;
     return out;
 }
 
