@@ -61,12 +61,15 @@ def library_path() -> str:
     return _build.LIB
 
 
-def load(build: bool = True) -> ctypes.CDLL:
-    """Load libfse.so (building it with nvcc first if it is missing or stale)."""
+def load(build: bool = True, path: str | None = None) -> ctypes.CDLL:
+    """Load libfse.so (building it with nvcc first if it is missing or stale).
+
+    `path` loads another build of the same ABI instead (for A/B comparisons)."""
     global _lib
-    if _lib is not None:
+    if _lib is not None and path is None:
         return _lib
-    path = _build.build() if build else _build.LIB
+    if path is None:
+        path = _build.build() if build else _build.LIB
     if not os.path.exists(path):
         raise RuntimeError(f"libfse.so not found at {path}; run paper_1203_0571_gb300._build.build()")
     L = ctypes.CDLL(path)
@@ -91,6 +94,13 @@ def load(build: bool = True) -> ctypes.CDLL:
     L.fse_sync_check.restype = ctypes.c_int
     _lib = L
     return L
+
+
+def use_library(path: str) -> ctypes.CDLL:
+    """Replace the loaded libfse with another build of the same ABI."""
+    global _lib
+    _lib = None
+    return load(path=path)
 
 
 def default_opts(**kw) -> Opts:

@@ -561,36 +561,45 @@ __device__ void moment_refine(const float* __restrict__ s, int w, int npix, int 
     warp_allsum_df(dh, dl);
     warp_allsum(cx);
     warp_allsum(F);
-    const double M0 = static_cast<double>(dh[0]) + dl[0];
-    const double M1x = static_cast<double>(dh[1]) + dl[1] + cx[0];
-    const double M1y = static_cast<double>(dh[2]) + dl[2] + cx[1];
-    const double Q11 = static_cast<double>(dh[3]) + dl[3] + cx[2];
-    const double Q12 = static_cast<double>(dh[4]) + dl[4] + cx[3];
-    const double Q22 = static_cast<double>(dh[5]) + dl[5] + cx[4];
-    if (!(M0 > 0.0) || !(Q11 + Q22 > 0.0)) return;
-    const double c = 1.0 / (2.0 * static_cast<double>(st.sw) * st.sw);
-    const double g1 = st.g1, g2 = st.g2, Ad = A, Bd = B;
-    const double J11 = 2.0 * c * (Ad * Q11 - 2.0 * g2 * Q12) - M0;
-    const double J12 = 2.0 * c * (Bd * Q12 - 2.0 * g2 * Q11);
-    const double J21 = 2.0 * c * (Ad * Q12 - 2.0 * g2 * Q22);
-    const double J22 = 2.0 * c * (Bd * Q22 - 2.0 * g2 * Q12) - M0;
-    const double dj = J11 * J22 - J12 * J21;
-    if (!(dj > 0.0)) return;
-    const float dx = static_cast<float>(-(J22 * M1x - J12 * M1y) / dj);
-    const float dy = static_cast<float>(-(-J21 * M1x + J11 * M1y) / dj);
+    // The first moments vanish at the fixed point; once accumulated exactly
+    // they are small numbers that fp32 carries to full relative precision.
+    const float M0 = dh[0] + dl[0];
+    const float M1x = dh[1] + (dl[1] + cx[0]);
+    const float M1y = dh[2] + (dl[2] + cx[1]);
+    const float Q11 = dh[3] + (dl[3] + cx[2]);
+    const float Q12 = dh[4] + (dl[4] + cx[3]);
+    const float Q22 = dh[5] + (dl[5] + cx[4]);
+    if (!(M0 > 0.f) || !(Q11 + Q22 > 0.f)) return;
+    const float c = 1.f / (2.f * st.sw * st.sw);
+    const float g1 = st.g1, g2 = st.g2;
+    const float J11 = 2.f * c * (A * Q11 - 2.f * g2 * Q12) - M0;
+    const float J12 = 2.f * c * (B * Q12 - 2.f * g2 * Q11);
+    const float J21 = 2.f * c * (A * Q12 - 2.f * g2 * Q22);
+    const float J22 = 2.f * c * (B * Q22 - 2.f * g2 * Q12) - M0;
+    const float dj = J11 * J22 - J12 * J21;
+    if (!(dj > 0.f)) return;
+    const float dx = -(J22 * M1x - J12 * M1y) / dj;
+    const float dy = -(-J21 * M1x + J11 * M1y) / dj;
     float dg1 = 0.f, dg2 = 0.f;
     if (ellip) {
-        const double T = Q11 + Q22;
-        const double e1 = (Q11 - Q22) / T, e2 = 2.0 * Q12 / T;
-        const float m[11] = {static_cast<float>(M0), static_cast<float>(M1x), static_cast<float>(M1y),
-                             static_cast<float>(Q11), static_cast<float>(Q12), static_cast<float>(Q22),
-                             F[0], F[1], F[2], F[3], F[4]};
+        // e - e_w = [ (Q11 - Q22, 2 Q12) (1 + |g|^2) - 2 g T ] / (T (1 + |g|^2)): the
+        // bracket cancels at the fixed point, so it is formed from the exact
+        // sums in fp64 (a few multiply-adds) before the fp32 division.
+        const double Q11d = static_cast<double>(dh[3]) + (static_cast<double>(dl[3]) + cx[2]);
+        const double Q22d = static_cast<double>(dh[5]) + (static_cast<double>(dl[5]) + cx[4]);
+        const double Q12d = static_cast<double>(dh[4]) + (static_cast<double>(dl[4]) + cx[3]);
+        const double Td = Q11d + Q22d;
+        const double opg = 1.0 + static_cast<double>(g1) * g1 + static_cast<double>(g2) * g2;
+        const float n1 = static_cast<float>((Q11d - Q22d) * opg - 2.0 * g1 * Td);
+        const float n2 = static_cast<float>(2.0 * Q12d * opg - 2.0 * g2 * Td);
+        const float T = Q11 + Q22;
+        const float den = T * (1.f + gg);
+        const float r1 = n1 / den, r2 = n2 / den;
+        const float m[11] = {M0, M1x, M1y, Q11, Q12, Q22, F[0], F[1], F[2], F[3], F[4]};
         float P11, P12, P21, P22;
-        shear_polarizability(m, st, static_cast<float>(e1), static_cast<float>(e2), &P11, &P12, &P21, &P22);
+        shear_polarizability(m, st, (Q11 - Q22) / T, 2.f * Q12 / T, &P11, &P12, &P21, &P22);
         const float det = P11 * P22 - P12 * P21;
         if (!(fabsf(det) > 0.f) || !isfinite(det)) return;
-        const double ew = 2.0 / (1.0 + g1 * g1 + g2 * g2);
-        const float r1 = static_cast<float>(e1 - ew * g1), r2 = static_cast<float>(e2 - ew * g2);
         const float sc = (1.f - gg) / det;
         dg1 = sc * (P22 * r1 - P12 * r2);
         dg2 = sc * (-P21 * r1 + P11 * r2);
@@ -675,7 +684,12 @@ __device__ int moment_iterate(const float* s, int h, int w, int npix, int lane, 
         status |= FSE_ST_MOM_MAXITER;
         it = o.max_iter_mom;
     }
-    if (status & FSE_ST_MOM_CONVERGED) moment_refine(s, w, npix, lane, ellip, st);
+    // two refinement steps: the first leaves ~1e-7 (the centre and g steps are
+    // taken separately), the second ~1e-8
+    if (status & FSE_ST_MOM_CONVERGED) {
+#pragma unroll 1
+        for (int r = 0; r < 2; ++r) moment_refine(s, w, npix, lane, ellip, st);
+    }
     return it;
 }
 
@@ -777,12 +791,12 @@ __device__ InitOut stamp_init(const float* s, int h, int w, int npix, int lane,
     prev = __shfl_sync(kFull, prev, src);
     cur = __shfl_sync(kFull, cur, src);
     if (kc <= 0) {
-        o.r50 = kc == 0 ? static_cast<float>(0.25 * static_cast<double>(tot) / static_cast<double>(cur))
+        o.r50 = kc == 0 ? 0.25f * static_cast<float>(tot) / static_cast<float>(cur)
                         : static_cast<float>(kSqrt2Ln2);
     } else {
-        const double half = 0.5 * static_cast<double>(tot);
-        o.r50 = static_cast<float>((kc - 1) + (half - static_cast<double>(prev)) /
-                                                  static_cast<double>(cur - prev));
+        // (half - prev) / (cur - prev) with the differences taken exactly in integers
+        o.r50 = static_cast<float>(kc - 1) + static_cast<float>(tot - 2 * prev) /
+                                                 (2.f * static_cast<float>(cur - prev));
     }
     __syncwarp();
     return o;
@@ -910,7 +924,7 @@ __device__ void fit_start(const float* __restrict__ s, const float* __restrict__
     *I00 = acc[2 * best] > 0.f ? acc[2 * best + 1] / acc[2 * best] : 1.f;
 }
 
-// Final refinement at the LM optimum: one pass with both exponentials to
+// Refinement at the LM optimum: a pass with both exponentials to
 // about one ulp (exp2_acc), the residual sums sum E r, sum v r, sum v a r and
 // sum r^2 accumulated in double-float, then one Gauss-Newton step of the
 // reduced problem and chi^2 from its quadratic model.  The fp32 LM stops
@@ -920,23 +934,57 @@ struct Refined {
     bool applied;
 };
 
+// Model values above this many noise sigmas carry an fp32 rounding (6e-8 of the
+// value) that is no longer small against the residual; the final refinement
+// evaluates chi^2 for those pixels in fp64.
+constexpr float kBrightSigma = 512.f;
+
 template <bool IVAR>
 __device__ Refined fit_refine(const float* __restrict__ s, const float* __restrict__ L,
-                              const float* __restrict__ sq, int npix, int lane, float I0g,
-                              float re, float n, float lq) {
+                              const float* __restrict__ sq, int w, int npix, int lane, float I0g,
+                              float re, float n, float lq, const MomState& st, bool final_pass) {
     float bf, dbf;
     bn_eval_f(n, &bf, &dbf);
     const float inv_n = 1.f / n;
     const float nbl = -bf * kLog2e;
     const float c0 = log2f(re) + lq;
+    // fp64 model constants for the bright pixels of the final pass
+    double bd = 0.0, dbd, lnre = 0.0, ln1g = 0.0, Ad = 0.0, Bd = 0.0, G4d = 0.0;
+    if (final_pass) {
+        bn_eval(static_cast<double>(n), &bd, &dbd);
+        lnre = log(static_cast<double>(re));
+        const double g1 = st.g1, g2 = st.g2, gg = g1 * g1 + g2 * g2;
+        ln1g = log(1.0 - sqrt(gg));
+        Ad = 1.0 + gg - 2.0 * g1;
+        Bd = 1.0 + gg + 2.0 * g1;
+        G4d = 4.0 * g2;
+    }
     float rh[10], rl[10];
 #pragma unroll
     for (int i = 0; i < 10; ++i) rh[i] = rl[i] = 0.f;
+    PixelWalk pw(lane, w);
     for (int p = lane; p < npix; p += 32) {
         const float a = L[p] - c0;
         const float u = exp2_acc(a * inv_n);
         float E = exp2_acc(u * nbl);
         float r = fmaf(I0g, E, -s[p]);
+        float rr_hi = 0.f, rr_lo = 0.f;
+        bool bright = false;
+        if (final_pass) {
+            const float q = IVAR ? sq[p] : 1.f;
+            if (fabsf(I0g * E) * q > kBrightSigma) {
+                const double t1 = static_cast<double>(pw.col - st.xi) - st.xf;
+                const double t2 = static_cast<double>(pw.row - st.yi) - st.yf;
+                const double R2 = Ad * t1 * t1 + Bd * t2 * t2 - G4d * t1 * t2;
+                const double ud = exp((0.5 * log(R2) - ln1g - lnre) / static_cast<double>(n));
+                const double rd = (static_cast<double>(I0g) * exp(-bd * ud) - s[p]) * q;
+                const double rrd = rd * rd;
+                rr_hi = static_cast<float>(rrd);
+                rr_lo = static_cast<float>(rrd - rr_hi);
+                bright = true;
+            }
+        }
+        pw.next();
         if (IVAR) {
             const float q = sq[p];
             E *= q;
@@ -952,7 +1000,12 @@ __device__ Refined fit_refine(const float* __restrict__ s, const float* __restri
         df_add(rh[6], rl[6], E * r);
         df_add(rh[7], rl[7], v * r);
         df_add(rh[8], rl[8], va * r);
-        df_add(rh[9], rl[9], r * r);
+        if (bright) {
+            df_add(rh[9], rl[9], rr_hi);
+            rl[9] += rr_lo;
+        } else {
+            df_add(rh[9], rl[9], r * r);
+        }
     }
     warp_allsum_df(rh, rl);
     // The sums are exact to about 1e-14 relative; the quantities that vanish at
@@ -1035,16 +1088,62 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
     re = re < re_min ? re_min : (re > re_max ? re_max : re);
     float n, I0g;
     fit_start<IVAR>(s, L, sq, npix, lane, re, lq, &n, &I0g);
-    FitEval cur = fit_eval<IVAR>(s, L, sq, npix, lane, I0g, re, n, lq);
-    int evals = 1;
+    // One evaluation site: every pass of the profile goes through the single
+    // fit_eval call at the top of this loop (first the start, then each trial
+    // step, and a repeat at I0* when the amplitude jumped).
+    FitEval cur;
+    cur.chi2 = INFINITY;
+    bool have_cur = false, retried = false, converged = false, finite0 = true;
+    float I0t = I0g, ret = re, nt = n, pred = 0.f;
     float lambda = o.lm_lambda0, nu = 2.f;
-    bool converged = false;
-    int band_accepts = 0;
-    const bool finite0 = isfinite(cur.chi2) && isfinite(cur.g[0]) && isfinite(cur.g[1]) &&
-                         isfinite(cur.H[0]) && isfinite(cur.H[1]) && isfinite(cur.H[2]);
-    if (!finite0) status |= FSE_ST_FIT_SINGULAR;
-    int it;
-    for (it = 1; finite0 && it <= o.max_iter_fit; ++it) {
+    int evals = 0, band_accepts = 0, it = 0;
+#pragma unroll 1
+    for (;;) {
+        const FitEval ev = fit_eval<IVAR>(s, L, sq, npix, lane, I0t, ret, nt, lq);
+        ++evals;
+        if (ev.corr > 0.5f && !retried) {
+            // the amplitude moved so far that chi^2 lost precision: evaluate again at I0*
+            I0t = ev.I0;
+            retried = true;
+            continue;
+        }
+        retried = false;
+        if (!have_cur) {
+            cur = ev;
+            have_cur = true;
+            finite0 = isfinite(cur.chi2) && isfinite(cur.g[0]) && isfinite(cur.g[1]) &&
+                      isfinite(cur.H[0]) && isfinite(cur.H[1]) && isfinite(cur.H[2]);
+            if (!finite0) {
+                status |= FSE_ST_FIT_SINGULAR;
+                break;
+            }
+        } else {
+            // A step whose predicted decrease is below the resolution of the fp32
+            // chi^2 is accepted when chi^2 stays within that resolution (at most a
+            // few times), so that the iteration reaches the zero of the gradient
+            // instead of stalling on rejections it cannot resolve.
+            const float band = 1e-6f * cur.chi2;
+            const bool better = ev.chi2 < cur.chi2;
+            const bool in_band = pred <= band && ev.chi2 <= cur.chi2 + band && band_accepts < 4;
+            if (better || in_band) {
+                if (!better) ++band_accepts;
+                const float rho = pred > 0.f ? (cur.chi2 - ev.chi2) / pred : 1.f;
+                const float t = 2.f * rho - 1.f;
+                lambda *= fmaxf(1.f / 3.f, 1.f - t * t * t);
+                nu = 2.f;
+                re = ret;
+                n = nt;
+                cur = ev;
+            } else {
+                lambda *= nu;
+                nu *= 2.f;
+                if (lambda > 1e15f) {
+                    converged = true;
+                    break;
+                }
+            }
+        }
+        if (++it > o.max_iter_fit) break;
         const float M00 = cur.H[0] * (1.f + lambda), M11 = cur.H[2] * (1.f + lambda);
         const float M01 = cur.H[1];
         const float det = M00 * M11 - M01 * M01;
@@ -1064,40 +1163,11 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
             converged = true;
             break;
         }
-        const float pred = -(2.f * (cur.g[0] * s0 + cur.g[1] * s1) +
-                             s0 * (cur.H[0] * s0 + cur.H[1] * s1) +
-                             s1 * (cur.H[1] * s0 + cur.H[2] * s1));
-        FitEval nxt = fit_eval<IVAR>(s, L, sq, npix, lane, cur.I0, qre, qn, lq);
-        ++evals;
-        if (nxt.corr > 0.5f) {
-            // the amplitude moved so far that chi^2 lost precision: evaluate again at I0*
-            nxt = fit_eval<IVAR>(s, L, sq, npix, lane, nxt.I0, qre, qn, lq);
-            ++evals;
-        }
-        // A step whose predicted decrease is below the resolution of the fp32
-        // chi^2 is accepted when chi^2 stays within that resolution (at most a
-        // few times), so that the iteration reaches the zero of the gradient
-        // instead of stalling on rejections it cannot resolve.
-        const float band = 1e-6f * cur.chi2;
-        const bool better = nxt.chi2 < cur.chi2;
-        const bool in_band = pred <= band && nxt.chi2 <= cur.chi2 + band && band_accepts < 4;
-        if (better || in_band) {
-            if (!better) ++band_accepts;
-            const float rho = pred > 0.f ? (cur.chi2 - nxt.chi2) / pred : 1.f;
-            const float t = 2.f * rho - 1.f;
-            lambda *= fmaxf(1.f / 3.f, 1.f - t * t * t);
-            nu = 2.f;
-            re = qre;
-            n = qn;
-            cur = nxt;
-        } else {
-            lambda *= nu;
-            nu *= 2.f;
-            if (lambda > 1e15f) {
-                converged = true;
-                break;
-            }
-        }
+        pred = -(2.f * (cur.g[0] * s0 + cur.g[1] * s1) + s0 * (cur.H[0] * s0 + cur.H[1] * s1) +
+                 s1 * (cur.H[1] * s0 + cur.H[2] * s1));
+        I0t = cur.I0;
+        ret = qre;
+        nt = qn;
     }
     if (converged && isfinite(cur.chi2)) status |= FSE_ST_FIT_CONVERGED;
     else if (finite0 && it > o.max_iter_fit) status |= FSE_ST_FIT_MAXITER;
@@ -1107,11 +1177,17 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
     out.n = n;
     out.chi2 = cur.chi2;
     if (converged && isfinite(cur.chi2) && re > re_min && re < re_max && n > n_min && n < n_max) {
-        const Refined rf = fit_refine<IVAR>(s, L, sq, npix, lane, cur.I0, re, n, lq);
-        out.I0 = static_cast<float>(rf.I0);
-        out.re = static_cast<float>(rf.re);
-        out.n = static_cast<float>(rf.n);
-        out.chi2 = rf.chi2;
+        // two refinement passes: the second evaluates chi^2 exactly at the
+        // first one's point, and its own step is much smaller than the first
+#pragma unroll 1
+        for (int r = 0; r < 2; ++r) {
+            const Refined rf = fit_refine<IVAR>(s, L, sq, w, npix, lane, out.I0, out.re, out.n, lq,
+                                                st, r == 1);
+            out.I0 = static_cast<float>(rf.I0);
+            out.re = static_cast<float>(rf.re);
+            out.n = static_cast<float>(rf.n);
+            out.chi2 = rf.chi2;
+        }
     }
     if (out.re <= re_min || out.re >= re_max || out.n <= n_min || out.n >= n_max)
         status |= FSE_ST_FIT_BOUND;
