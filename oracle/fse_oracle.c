@@ -488,6 +488,29 @@ static double profiled_eval(const fit_data *d, double re, double n, double *I0_o
     return chi2;
 }
 
+/* Keep (r_e, n) inside the fit's box. */
+static void clamp_theta(double q[2], const orc_opts *o, double re_max)
+{
+    if (q[0] < o->re_min) q[0] = o->re_min;
+    if (q[0] > re_max) q[0] = re_max;
+    if (q[1] < o->n_min) q[1] = o->n_min;
+    if (q[1] > o->n_max) q[1] = o->n_max;
+}
+
+/* Relative size max_i |s_i| / theta_i of the undamped Gauss-Newton step
+ * s = -H^-1 g, clipped to the box (0 when the box stops it entirely); +inf
+ * when H is not positive definite. */
+static double gn_step(double H[2][2], const double g[2], const double th[2], const orc_opts *o,
+                      double re_max)
+{
+    double det = H[0][0] * H[1][1] - H[0][1] * H[1][0];
+    if (!(det > 0.0) || !(H[0][0] > 0.0) || !isfinite(det)) return INFINITY;
+    double q[2] = { th[0] + (-H[1][1] * g[0] + H[0][1] * g[1]) / det,
+                    th[1] + (H[1][0] * g[0] - H[0][0] * g[1]) / det };
+    clamp_theta(q, o, re_max);
+    return fmax(fabs(q[0] - th[0]) / th[0], fabs(q[1] - th[1]) / th[1]);
+}
+
 static void fit_stamp(const double *I, const double *ivar, int h, int w, const orc_opts *o,
                       double xc, double yc, double g1, double g2, double sw,
                       orc_result *res)
@@ -522,6 +545,10 @@ static void fit_stamp(const double *I, const double *ivar, int h, int w, const o
     double lambda = o->lm_lambda0, nu = 2.0;
     int it, converged = 0;
     for (it = 1; it <= o->max_iter_fit; ++it) {
+        /* Stop test on the undamped Gauss-Newton step, the estimate of the
+         * distance to the minimum that MIGRAD also stops on: a damped step can
+         * be small far from the minimum of a flat valley when lambda is large. */
+        if (gn_step(H, g, th, o, re_max) <= o->tol_fit) { converged = 1; break; }
         double M[2][2] = { { H[0][0] * (1.0 + lambda), H[0][1] },
                            { H[1][0], H[1][1] * (1.0 + lambda) } };
         double det = M[0][0] * M[1][1] - M[0][1] * M[1][0];
@@ -529,13 +556,8 @@ static void fit_stamp(const double *I, const double *ivar, int h, int w, const o
         double dt[2] = { (-M[1][1] * g[0] + M[0][1] * g[1]) / det,
                          (M[1][0] * g[0] - M[0][0] * g[1]) / det };
         double q[2] = { th[0] + dt[0], th[1] + dt[1] };
-        if (q[0] < o->re_min) q[0] = o->re_min;
-        if (q[0] > re_max) q[0] = re_max;
-        if (q[1] < o->n_min) q[1] = o->n_min;
-        if (q[1] > o->n_max) q[1] = o->n_max;
+        clamp_theta(q, o, re_max);
         double s[2] = { q[0] - th[0], q[1] - th[1] };
-        double step = fmax(fabs(s[0]) / th[0], fabs(s[1]) / th[1]);
-        if (step <= o->tol_fit) { converged = 1; break; }
         double Hq[2][2], gq[2], I0q;
         double chi2q = profiled_eval(&d, q[0], q[1], &I0q, Hq, gq);
         ++evals;

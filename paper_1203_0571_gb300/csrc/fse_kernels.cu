@@ -12,6 +12,7 @@
 // reduced with xor shuffles, which give every lane the same total, so all
 // lanes run the scalar update redundantly and stay in lock-step.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -48,6 +49,8 @@ __device__ __forceinline__ float exp2_acc(float x) {
     if (x > 127.f) return INFINITY;
     const float k = rintf(x);
     const float f = x - k;
+    // Horner's scheme (about 1.2 ulp; shorter-chain schemes round the leading
+    // terms earlier and lose accuracy)
     float p = 1.5252733804059841e-05f;
     p = fmaf(p, f, 1.540353039338161e-04f);
     p = fmaf(p, f, 1.3333558146428443e-03f);
@@ -240,6 +243,15 @@ __device__ __forceinline__ void bn_eval_f(float n, float* b, float* db) {
            (3.f * t2 - 2.f * t) * h * p1.y) * static_cast<float>(1.0 / kBnStep);
 }
 
+// b''(n) as the slope of b' across the table interval (first-order accurate;
+// it only enters the curvature term of the final Newton steps).
+__device__ __forceinline__ float bn_d2_f(float n) {
+    const float x = (n - static_cast<float>(kBnLo)) * static_cast<float>(1.0 / kBnStep);
+    int k = static_cast<int>(floorf(x));
+    k = k < 0 ? 0 : (k > kBnNodes - 2 ? kBnNodes - 2 : k);
+    return (g_bnf[k + 1].y - g_bnf[k].y) * static_cast<float>(1.0 / kBnStep);
+}
+
 __global__ void eval_bn_kernel(const double* n, double* b, double* db, int64_t count) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= count) return;
@@ -358,13 +370,28 @@ struct MomState {
     float xf, yf;    // fractional part, |.| <= 0.5 after renormalisation
     float g1, g2;    // weight ellipticity g_w
     float sw;        // weight size sigma_w
+    int xr, yr;      // reference pixel of the stored per-pixel offsets
 };
+
+// Offsets (column - xr, row - yr) of every pixel as half2 (integers below
+// 2048 are exact in fp16), stored in the auxiliary buffer for the moment
+// passes.
+__device__ __forceinline__ void store_offsets(__half2* C, int w, int npix, int lane, int xr,
+                                              int yr) {
+    PixelWalk pw(lane, w);
+    for (int p = lane; p < npix; p += 32) {
+        C[p] = __floats2half2_rn(static_cast<float>(pw.col - xr), static_cast<float>(pw.row - yr));
+        pw.next();
+    }
+    __syncwarp();
+}
 
 // One weighted pass: S0 = sum f W, S1 = sum f W theta, the three second and
 // five fourth moments of f W (f = pixel value).  Everything the centroid step
 // (Eqs. 5-6) and the ellipticity step (Eqs. 8-9 with A5-A6, B7-B14) needs is a
 // linear combination of these eleven sums.
-__device__ __forceinline__ void moment_pass(const float* __restrict__ s, int w, int npix, int lane,
+__device__ __forceinline__ void moment_pass(const float* __restrict__ s,
+                                            const __half2* __restrict__ C, int npix, int lane,
                                             const MomState& st, float (&acc)[11]) {
     const float gg = st.g1 * st.g1 + st.g2 * st.g2;
     const float A = 1.f + gg - 2.f * st.g1;
@@ -373,11 +400,16 @@ __device__ __forceinline__ void moment_pass(const float* __restrict__ s, int w, 
     const float cw = -kLog2e / (2.f * st.sw * st.sw);
 #pragma unroll
     for (int i = 0; i < 11; ++i) acc[i] = 0.f;
-    PixelWalk pw(lane, w);
-    const float fxf = st.xf, fyf = st.yf;
+    // centre relative to the reference pixel; rounding it to fp32 here costs
+    // at most 2.4e-7 px, below the noise of these sums (the refinement passes
+    // use exact offsets)
+    const float cx = static_cast<float>(st.xi - st.xr) + st.xf;
+    const float cy = static_cast<float>(st.yi - st.yr) + st.yf;
+#pragma unroll 2
     for (int p = lane; p < npix; p += 32) {
-        const float t1 = static_cast<float>(pw.col - st.xi) - fxf;
-        const float t2 = static_cast<float>(pw.row - st.yi) - fyf;
+        const float2 X = __half22float2(C[p]);
+        const float t1 = X.x - cx;
+        const float t2 = X.y - cy;
         const float t11 = t1 * t1, t22 = t2 * t2, t12 = t1 * t2;
         const float R2 = fmaf(A, t11, fmaf(B, t22, -G4 * t12));
         const float f = s[p] * ex2(R2 * cw);
@@ -393,7 +425,6 @@ __device__ __forceinline__ void moment_pass(const float* __restrict__ s, int w, 
         acc[8] = fmaf(f11, t22, acc[8]);    // theta1^2 theta2^2
         acc[9] = fmaf(f22, t12, acc[9]);    // theta1 theta2^3
         acc[10] = fmaf(f22, t22, acc[10]);  // theta2^4
-        pw.next();
     }
     warp_allsum(acc);
 }
@@ -614,14 +645,17 @@ __device__ void moment_refine(const float* __restrict__ s, int w, int npix, int 
 }
 
 // Iterate to the stop rule.  Returns the number of passes; sets status bits.
-__device__ int moment_iterate(const float* s, int h, int w, int npix, int lane, const DevOpts& o,
-                              bool ellip, MomState& st, uint32_t& status) {
+__device__ int moment_iterate(const float* s, __half2* C, int h, int w, int npix, int lane,
+                              const DevOpts& o, bool ellip, MomState& st, uint32_t& status) {
+    st.xr = st.xi;
+    st.yr = st.yi;
+    store_offsets(C, w, npix, lane, st.xr, st.yr);
     const float sw_max = 0.5f * static_cast<float>(h < w ? h : w);
     float prev = 0.f;   // size of the previous step, for the contraction estimate
     int it;
     for (it = 1; it <= o.max_iter_mom; ++it) {
         float m[11];
-        moment_pass(s, w, npix, lane, st, m);
+        moment_pass(s, C, npix, lane, st, m);
         const MomStep d = moment_step(m, st, o.k_gain, ellip);
         if (!d.ok) {
             status |= FSE_ST_MOM_FAILED;
@@ -829,6 +863,7 @@ __device__ FitEval fit_eval(const float* __restrict__ s, const float* __restrict
     float acc[10];
 #pragma unroll
     for (int i = 0; i < 10; ++i) acc[i] = 0.f;
+#pragma unroll 2
     for (int p = lane; p < npix; p += 32) {
         const float a = L[p] - c0;
         const float u = ex2(a * inv_n);
@@ -939,6 +974,19 @@ struct Refined {
 // evaluates chi^2 for those pixels in fp64.
 constexpr float kBrightSigma = 512.f;
 
+// fp64 squared residual of one bright pixel (kept out of line: rarely taken).
+struct BrightModel {
+    double b, lnre, ln1g, A, B, G4, inv_n, I0;
+};
+
+__device__ __noinline__ double bright_r2(const BrightModel& bm, double t1, double t2, float pix,
+                                         float q) {
+    const double R2 = bm.A * t1 * t1 + bm.B * t2 * t2 - bm.G4 * t1 * t2;
+    const double u = exp((0.5 * log(R2) - bm.ln1g - bm.lnre) * bm.inv_n);
+    const double r = (bm.I0 * exp(-bm.b * u) - pix) * q;
+    return r * r;
+}
+
 template <bool IVAR>
 __device__ Refined fit_refine(const float* __restrict__ s, const float* __restrict__ L,
                               const float* __restrict__ sq, int w, int npix, int lane, float I0g,
@@ -948,20 +996,27 @@ __device__ Refined fit_refine(const float* __restrict__ s, const float* __restri
     const float inv_n = 1.f / n;
     const float nbl = -bf * kLog2e;
     const float c0 = log2f(re) + lq;
-    // fp64 model constants for the bright pixels of the final pass
-    double bd = 0.0, dbd, lnre = 0.0, ln1g = 0.0, Ad = 0.0, Bd = 0.0, G4d = 0.0;
-    if (final_pass) {
-        bn_eval(static_cast<double>(n), &bd, &dbd);
-        lnre = log(static_cast<double>(re));
+    // fp64 model constants for the bright pixels of the final pass; a model
+    // value exceeds the threshold only if |I0| does (E <= 1)
+    const bool check_bright = final_pass && (IVAR || fabsf(I0g) > kBrightSigma);
+    BrightModel bm;
+    if (check_bright) {
+        double dbd;
+        bn_eval(static_cast<double>(n), &bm.b, &dbd);
+        bm.lnre = log(static_cast<double>(re));
         const double g1 = st.g1, g2 = st.g2, gg = g1 * g1 + g2 * g2;
-        ln1g = log(1.0 - sqrt(gg));
-        Ad = 1.0 + gg - 2.0 * g1;
-        Bd = 1.0 + gg + 2.0 * g1;
-        G4d = 4.0 * g2;
+        bm.ln1g = log(1.0 - sqrt(gg));
+        bm.A = 1.0 + gg - 2.0 * g1;
+        bm.B = 1.0 + gg + 2.0 * g1;
+        bm.G4 = 4.0 * g2;
+        bm.inv_n = 1.0 / static_cast<double>(n);
+        bm.I0 = I0g;
     }
-    float rh[10], rl[10];
+    float rh[10], rl[10], T[4];
 #pragma unroll
     for (int i = 0; i < 10; ++i) rh[i] = rl[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) T[i] = 0.f;
     PixelWalk pw(lane, w);
     for (int p = lane; p < npix; p += 32) {
         const float a = L[p] - c0;
@@ -970,15 +1025,11 @@ __device__ Refined fit_refine(const float* __restrict__ s, const float* __restri
         float r = fmaf(I0g, E, -s[p]);
         float rr_hi = 0.f, rr_lo = 0.f;
         bool bright = false;
-        if (final_pass) {
+        if (check_bright) {
             const float q = IVAR ? sq[p] : 1.f;
             if (fabsf(I0g * E) * q > kBrightSigma) {
-                const double t1 = static_cast<double>(pw.col - st.xi) - st.xf;
-                const double t2 = static_cast<double>(pw.row - st.yi) - st.yf;
-                const double R2 = Ad * t1 * t1 + Bd * t2 * t2 - G4d * t1 * t2;
-                const double ud = exp((0.5 * log(R2) - ln1g - lnre) / static_cast<double>(n));
-                const double rd = (static_cast<double>(I0g) * exp(-bd * ud) - s[p]) * q;
-                const double rrd = rd * rd;
+                const double rrd = bright_r2(bm, static_cast<double>(pw.col - st.xi) - st.xf,
+                                             static_cast<double>(pw.row - st.yi) - st.yf, s[p], q);
                 rr_hi = static_cast<float>(rrd);
                 rr_lo = static_cast<float>(rrd - rr_hi);
                 bright = true;
@@ -991,6 +1042,7 @@ __device__ Refined fit_refine(const float* __restrict__ s, const float* __restri
             r *= q;
         }
         const float v = E * u, va = v * a;
+        const float vr = v * r, var = va * r;
         df_add(rh[0], rl[0], E * E);
         df_add(rh[1], rl[1], E * v);
         df_add(rh[2], rl[2], E * va);
@@ -998,8 +1050,13 @@ __device__ Refined fit_refine(const float* __restrict__ s, const float* __restri
         df_add(rh[4], rl[4], v * va);
         df_add(rh[5], rl[5], va * va);
         df_add(rh[6], rl[6], E * r);
-        df_add(rh[7], rl[7], v * r);
-        df_add(rh[8], rl[8], va * r);
+        df_add(rh[7], rl[7], vr);
+        df_add(rh[8], rl[8], var);
+        // residual-weighted second-derivative sums of the model (Newton term)
+        T[0] = fmaf(var, a, T[0]);       // r E u a^2
+        T[1] = fmaf(vr, u, T[1]);        // r E u^2
+        T[2] = fmaf(var, u, T[2]);       // r E u^2 a
+        T[3] = fmaf(var * u, a, T[3]);   // r E u^2 a^2
         if (bright) {
             df_add(rh[9], rl[9], rr_hi);
             rl[9] += rr_lo;
@@ -1008,6 +1065,7 @@ __device__ Refined fit_refine(const float* __restrict__ s, const float* __restri
         }
     }
     warp_allsum_df(rh, rl);
+    warp_allsum(T);
     // The sums are exact to about 1e-14 relative; the quantities that vanish at
     // the optimum (the gradient) are formed from them in fp32 only after the
     // cancellation has happened inside the double-float sums.
@@ -1028,9 +1086,45 @@ __device__ Refined fit_refine(const float* __restrict__ s, const float* __restri
     const float Cvv = svv - sEv * sEv / sEE;
     const float Cvva = svva - sEv * sEva / sEE;
     const float Cvaa = svaa - sEva * sEva / sEE;
+    // gradient of chi^2/2 over (r_e, n) at I0*
     const float g0 = k2 * svr_s, g1 = kA * svar_s - kB * svr_s;
-    const float H00 = k2 * k2 * Cvv, H01 = k2 * (kA * Cvva - kB * Cvv);
-    const float H11 = kA * kA * Cvaa - 2.f * kA * kB * Cvva + kB * kB * Cvv;
+    // Gauss-Newton part of the reduced Hessian (J^T J with I0 profiled out)
+    float H00 = k2 * k2 * Cvv, H01 = k2 * (kA * Cvva - kB * Cvv);
+    float H11 = kA * kA * Cvaa - 2.f * kA * kB * Cvva + kB * kB * Cvv;
+    // J^T J couplings of I0 with r_e and n
+    float JI0 = k2 * sEv, JI1 = kA * sEva - kB * sEv;
+    {
+        // Newton: add sum r d^2 m.  With phi = b u and E = exp(-phi),
+        // d^2 E = E (dphi_i dphi_j - d^2 phi_ij); the derivatives of u = (r/r_e)^(1/n)
+        // give the six residual sums r E u {1, a, a^2} and r E u^2 {1, a, a^2}
+        // (a = log2(r/r_e)).  Where the residuals are large, dropping this term
+        // leaves a Gauss-Newton iteration that converges slowly or not at all.
+        const float d2b = bn_d2_f(n);
+        const float ln2 = static_cast<float>(kLn2);
+        const float c = inv_n / re;
+        const float in2 = inv_n * inv_n;
+        const float T1 = svr, T2 = svar;
+        const float Srr = bf * c * c * (bf * T[1] - (1.f + n) * T1);
+        const float Srn = c * (-bf * dbf * T[1] + bf * bf * ln2 * in2 * T[2] + dbf * T1 -
+                               bf * ln2 * in2 * T2 - bf * inv_n * T1);
+        const float Snn = dbf * dbf * T[1] - 2.f * bf * dbf * ln2 * in2 * T[2] +
+                          bf * bf * ln2 * ln2 * in2 * in2 * T[3] - d2b * T1 +
+                          2.f * dbf * ln2 * in2 * T2 - bf * ln2 * ln2 * in2 * in2 * T[0] -
+                          2.f * bf * ln2 * in2 * inv_n * T2;
+        // the I0 rows gain g/I0 (sum r dE), which also enters the Schur complement
+        const float q0 = g0 / I0, q1 = g1 / I0;
+        const float N00 = H00 + I0 * Srr - (2.f * JI0 * q0 + q0 * q0) / sEE;
+        const float N01 = H01 + I0 * Srn - (JI0 * q1 + JI1 * q0 + q0 * q1) / sEE;
+        const float N11 = H11 + I0 * Snn - (2.f * JI1 * q1 + q1 * q1) / sEE;
+        // keep Gauss-Newton where the full Hessian is not positive definite
+        if (N00 > 0.f && N00 * N11 - N01 * N01 > 0.f && isfinite(N00 * N11)) {
+            H00 = N00;
+            H01 = N01;
+            H11 = N11;
+            JI0 += q0;
+            JI1 += q1;
+        }
+    }
     const float det = H00 * H11 - H01 * H01;
     o.I0 = I0;
     o.re = re;
@@ -1042,7 +1136,7 @@ __device__ Refined fit_refine(const float* __restrict__ s, const float* __restri
         const float d1 = (H01 * g0 - H00 * g1) / det;
         if (fabsf(d0) <= 1e-2f * re && fabsf(d1) <= 1e-2f * n) {
             // I0 follows Eq. 13 to first order along the step
-            const float dI0 = -(k2 * sEv * d0 + (kA * sEva - kB * sEv) * d1) / sEE;
+            const float dI0 = -(JI0 * d0 + JI1 * d1) / sEE;
             o.re = static_cast<double>(re) + d0;
             o.n = static_cast<double>(n) + d1;
             o.I0 = static_cast<double>(I0) + dI0;
@@ -1320,7 +1414,8 @@ __global__ void __launch_bounds__(256, 1) estimator_kernel(LaunchArgs a) {
         }
         if (!skip && STAGE != kStageFit) {
             const bool ellip = STAGE != kStageCentroid;
-            res.it_mom = moment_iterate(s, h, w, npix, lane, o, ellip, st, status);
+            res.it_mom = moment_iterate(s, reinterpret_cast<__half2*>(aux), h, w, npix, lane, o,
+                                        ellip, st, status);
             res.x0 = static_cast<float>(st.xi) + st.xf;
             res.y0 = static_cast<float>(st.yi) + st.yf;
             res.sigma_w = st.sw;
