@@ -199,6 +199,29 @@ int fse_sersic_b(fse_ctx *ctx, const double *n, double *b, double *db, int64_t c
  * earlier call of this context (FSE_ETIMEOUT), or FSE_OK.  Clears the flag. */
 int fse_sync_check(fse_ctx *ctx, void *stream);
 
+/* fse_fit_batch without a context and without allocating device memory (the
+ * paper has no counterpart: it concerns the library, not the method).  For
+ * callers that cannot allocate at the point of the call, e.g. a service whose
+ * device footprint is fixed after start-up, or code under a caching allocator
+ * that owns all device memory.  Same arguments, layout and results as
+ * fse_fit_batch, on the CURRENT CUDA device; all pointers but opts and err are
+ * device pointers owned by the caller.
+ *  - Scratch: a file-scope device array of two 32-bit words (the work counter
+ *    and the error word), cleared by a cudaMemsetAsync on `stream` before each
+ *    launch.  count is limited to 2^31 - 1 stamps, the range the counter
+ *    indexes; a larger count returns FSE_EINVAL with a message.
+ *  - First call on a device: builds the b(n) table (a kernel and a device
+ *    synchronise) and looks up the scratch address; make it before any stream
+ *    capture.  Later calls only clear the scratch and launch.
+ *  - Calls that can overlap on the GPU (different streams or host threads)
+ *    share the scratch and race: issue them in order on one stream.
+ *  - A bounded device wait that expires marks the stamp FSE_ST_TIMEOUT.
+ *  - err (may be NULL): on failure, a NUL-terminated message of at most
+ *    err_len bytes; empty on success. */
+int fse_fit_batch_static(const void *pix, int dtype, const float *scale, const fse_stamp *idx,
+                         int64_t count, const float *inv_var, const fse_opts *opts,
+                         fse_result *out, void *stream, char *err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,7 +32,7 @@ ST = dict(MOM_CONVERGED=1 << 0, FIT_CONVERGED=1 << 1, MOM_MAXITER=1 << 2, FIT_MA
 # exported symbols, in the order include/fse.h declares them
 EXPORTS = ["fse_create", "fse_destroy", "fse_last_error", "fse_opts_default", "fse_centroid",
            "fse_ellipticity", "fse_sersic_fit", "fse_fit_batch", "fse_fit_batch_plain",
-           "fse_fit_batch_host", "fse_sersic_b", "fse_sync_check"]
+           "fse_fit_batch_host", "fse_sersic_b", "fse_sync_check", "fse_fit_batch_static"]
 
 
 class Opts(ctypes.Structure):
@@ -92,6 +92,10 @@ def load(build: bool = True, path: str | None = None) -> ctypes.CDLL:
     L.fse_sersic_b.restype = ctypes.c_int
     L.fse_sync_check.argtypes = [_vp, _vp]
     L.fse_sync_check.restype = ctypes.c_int
+    L.fse_fit_batch_static.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int64, _vp,
+                                       ctypes.POINTER(Opts), _vp, _vp, ctypes.c_char_p,
+                                       ctypes.c_size_t]
+    L.fse_fit_batch_static.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -279,3 +283,21 @@ def fse_sersic_b(ctx: Context, *a, **k):
 
 def fse_sync_check(ctx: Context, *a, **k):
     return ctx.sync_check(*a, **k)
+
+
+def fit_batch_static(pix, index, *, scale=None, inv_var=None, opts=None, out=None, stream=None):
+    """fse_fit_batch_static: the whole chain on the current device with no context
+    and no device allocation inside the call (scratch in static device memory)."""
+    n = int(index.shape[0])
+    if out is None:
+        out = torch.zeros((n, 64), dtype=torch.uint8, device=pix.device)
+    err = ctypes.create_string_buffer(512)
+    rc = load().fse_fit_batch_static(_ptr(pix), _dtype_of(pix), _ptr(scale), _ptr(index), n,
+                                     _ptr(inv_var), ctypes.byref(opts or default_opts()), _ptr(out),
+                                     _stream(stream), err, len(err))
+    if rc != FSE_OK:
+        raise FseError(rc, err.value.decode())
+    return out
+
+
+fse_fit_batch_static = fit_batch_static

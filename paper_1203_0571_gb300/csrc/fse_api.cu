@@ -195,6 +195,18 @@ int grow(fse_ctx* ctx, T** p, size_t* cap, size_t n) {
     return FSE_OK;
 }
 
+// Allocation-free form of fse_fit_batch (fse_fit_batch_static).  Some callers
+// cannot allocate device memory at the point of the call: a service that must
+// keep its footprint fixed after start-up, code running under a caching
+// allocator that owns all of the device memory, or a caller that holds no
+// fse_ctx.  The estimator's only per-call scratch is the work counter of the
+// persistent launch and the error word of its bounded waits; for those callers
+// both live in this file-scope array instead of in a context's device memory.
+constexpr int kStaticWords = 2;                      // [0] work counter, [1] error word
+constexpr int64_t kStaticMaxCount = 0x7fffffffLL;    // the 32-bit counter indexes at most this
+static __device__ __align__(256) unsigned int g_static_scratch[kStaticWords];
+unsigned int* g_static_addr[256];                    // its address on each device
+
 }  // namespace
 
 extern "C" {
@@ -465,6 +477,61 @@ int fse_sync_check(fse_ctx* ctx, void* stream) {
         cudaMemset(ctx->d_err, 0, sizeof(unsigned int));
         return set_error(ctx, FSE_ETIMEOUT, "a bounded device wait expired");
     }
+    return FSE_OK;
+}
+
+int fse_fit_batch_static(const void* pix, int dtype, const float* scale, const fse_stamp* idx,
+                         int64_t count, const float* inv_var, const fse_opts* opts,
+                         fse_result* out, void* stream, char* err, size_t err_len) {
+    fse_ctx sink;   // on the stack: only the error text of the shared checks
+    if (err && err_len) err[0] = 0;
+    auto fail = [&](int rc) {
+        if (err && err_len) snprintf(err, err_len, "%s", sink.err);
+        return rc;
+    };
+    if (count > kStaticMaxCount)
+        return fail(set_error(&sink, FSE_EINVAL,
+                              "count %lld exceeds %lld, the largest batch the static work counter "
+                              "can index", static_cast<long long>(count),
+                              static_cast<long long>(kStaticMaxCount)));
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 256) {
+        cudaGetLastError();
+        return fail(set_error(&sink, FSE_ECUDA, "no usable current CUDA device"));
+    }
+    sink.device = dev;
+    fse::LaunchArgs a;
+    int rc = prepare(&sink, pix, dtype, scale, idx, count, inv_var, opts, out, fse::kStageAll, &a);
+    if (rc) return fail(rc);
+    if (count == 0) return FSE_OK;
+    unsigned int* scratch = nullptr;
+    {
+        // first call on this device: the b(n) table (static device storage,
+        // built by a kernel, then a device synchronise) and the scratch address
+        std::lock_guard<std::mutex> lk(g_table_mutex);
+        if (!g_table_built[dev]) {
+            e = fse::build_bn_table(nullptr);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return fail(cuda_fail(&sink, e, "b(n) table"));
+            g_table_built[dev] = true;
+        }
+        if (!g_static_addr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_static_scratch);
+            if (e != cudaSuccess) return fail(cuda_fail(&sink, e, "static scratch address"));
+            g_static_addr[dev] = static_cast<unsigned int*>(p);
+        }
+        scratch = g_static_addr[dev];
+    }
+    a.queue = scratch;
+    a.err = scratch + 1;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // both words must start at zero: one stream-ordered clear before the launch
+    e = cudaMemsetAsync(scratch, 0, kStaticWords * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return fail(cuda_fail(&sink, e, "static scratch clear"));
+    e = fse::launch_estimator(a, s);
+    if (e != cudaSuccess) return fail(cuda_fail(&sink, e, "estimator launch"));
     return FSE_OK;
 }
 

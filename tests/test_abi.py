@@ -81,3 +81,12 @@ def test_index_packing():
     arr = idx.numpy().view(binding.STAMP_DTYPE).reshape(-1)
     assert arr["offset"].tolist() == [0, 1024, 5]
     assert arr["h"].tolist() == [32, 16, 3] and arr["w"].tolist() == [32, 64, 7]
+
+
+def test_static_entry_rejects_oversized_batch(lib):
+    """The batch limit of the static-scratch entry is checked before any CUDA call."""
+    err = ctypes.create_string_buffer(256)
+    rc = lib.fse_fit_batch_static(None, binding.FSE_F32, None, None, 1 << 31, None,
+                                  ctypes.byref(binding.default_opts()), None, None, err, len(err))
+    assert rc == binding.FSE_EINVAL
+    assert b"static work counter" in err.value

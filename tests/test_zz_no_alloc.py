@@ -1,0 +1,44 @@
+"""fse_fit_batch_static (scratch in static device memory, no allocation in the
+call) against fse_fit_batch, through the C ABI.  The file sorts last so that it
+also runs after the other GPU tests; it passes alone in a fresh process too,
+where its first call does the per-device setup itself."""
+import numpy as np
+import pytest
+import torch
+
+import parity as PR
+from paper_1203_0571_gb300 import binding as B
+from paper_1203_0571_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def within_tolerance(g, r):
+    assert np.array_equal(g["status"], r["status"])
+    for k, tol in PR.TOL.items():
+        a, b = g[k].astype(np.float64), r[k].astype(np.float64)
+        same = (a == b) | (np.isnan(a) & np.isnan(b))     # includes equal infinities
+        with np.errstate(invalid="ignore"):
+            err = np.abs(a - b) if k in PR.ABS else np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
+        assert np.all(same | (err <= tol)), (k, float(np.nanmax(np.where(same, 0.0, err))))
+
+
+def test_static_entry_matches_fit_batch():
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    batch = synth.make_workload(1, count=4000, device="cuda")
+    idx = B.make_index(batch.offset, batch.h, batch.w)
+    opts = B.default_opts(max_pix=48 * 48)
+    # two calls in a row: the second must find its scratch cleared again
+    first = B.results(B.fit_batch_static(batch.pix, idx, opts=opts))
+    out = torch.zeros((batch.count, 64), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    B.fit_batch_static(batch.pix, idx, opts=opts, out=out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free_before    # nothing allocated by the call
+    second = B.results(out)
+    ref = B.results(B.Context(0).fit_batch(batch.pix, idx, opts=opts))
+    assert ((ref["status"] & 3) == 3).mean() > 0.9
+    within_tolerance(first, ref)
+    within_tolerance(second, ref)
+
