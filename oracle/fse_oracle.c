@@ -688,6 +688,67 @@ void orc_fit_eval(const double *I, const double *ivar, int h, int w, double xc, 
     free(r);
 }
 
+/* Gradient of chi^2 (Eq. 11) for the elliptical Sérsic model of Eq. 10 with
+ * respect to all seven parameters p = (x0, y0, g1, g2, I0, r_e, n) and to the
+ * pixels.  With r_i = m_i - I_i and weights w_i (1/sigma_i^2, default 1):
+ *   chi^2 = sum w r^2,   dchi^2/dp = 2 sum w r dm/dp,   dchi^2/dI_i = -2 w_i r_i.
+ * The model depends on the centre and the ellipticity only through the
+ * Sérsic radius r = sqrt(R^2(theta; g)) / (1 - |g|) (R^2 from Eq. A1), so
+ *   dm/dq = dm/dr * dr/dq,   dm/dr = -m b u / (n r),   u = (r / r_e)^(1/n),
+ *   dr/dR^2 = r / (2 R^2),   dr/d|g| = r / (1 - |g|),   d|g|/dg_k = g_k / |g|.
+ * The pixel at R^2 = 0 adds no centre or shape derivative (the profile has a
+ * cusp there for n > 1), and d|g|/dg is taken as 0 at g = 0 (the kink).
+ * Writes chi^2, grad[7] and, if dpix != NULL, the h*w pixel gradient. */
+void orc_chi2_grad(const double *I, const double *ivar, int h, int w, const double p[7],
+                   double *chi2_out, double grad[7], double *dpix)
+{
+    const double x0 = p[0], y0 = p[1], g1 = p[2], g2 = p[3], I0 = p[4], re = p[5], n = p[6];
+    const double gabs = sqrt(g1 * g1 + g2 * g2);
+    const double b = orc_sersic_b(n), db = orc_sersic_db(n);
+    /* R^2 = A t1^2 + B t2^2 - 4 g2 t1 t2 and the derivatives of its coefficients */
+    const double A = (1.0 - g1) * (1.0 - g1) + g2 * g2;
+    const double B = (1.0 + g1) * (1.0 + g1) + g2 * g2;
+    const double dA_g1 = -2.0 * (1.0 - g1), dB_g1 = 2.0 * (1.0 + g1);
+    const double dA_g2 = 2.0 * g2, dB_g2 = 2.0 * g2;
+    const double dabs1 = gabs > 0.0 ? g1 / gabs : 0.0, dabs2 = gabs > 0.0 ? g2 / gabs : 0.0;
+    double chi2 = 0.0;
+    for (int a = 0; a < 7; ++a) grad[a] = 0.0;
+    for (int i = 0; i < h; ++i)
+        for (int j = 0; j < w; ++j) {
+            const int k = i * w + j;
+            const double t1 = j - x0, t2 = i - y0;
+            const double R2 = ellip_R2(t1, t2, g1, g2);
+            const double r = sqrt(R2 > 0.0 ? R2 : 0.0) / (1.0 - gabs);
+            const double x = r / re;
+            const double u = x > 0.0 ? pow(x, 1.0 / n) : 0.0;
+            const double E = exp(-b * u);
+            const double m = I0 * E;
+            const double wgt = ivar ? ivar[k] : 1.0;
+            const double res = m - I[k];
+            const double c = 2.0 * wgt * res;
+            chi2 += wgt * res * res;
+            grad[4] += c * E;                                        /* dm/dI0 = E */
+            grad[5] += c * m * b * u / (n * re);                     /* dm/dr_e */
+            if (x > 0.0) grad[6] += c * m * u * (b * log(x) / (n * n) - db);   /* dm/dn */
+            if (R2 > 0.0) {
+                const double dm_dr = -m * b * u / (n * r);
+                const double dr_dR2 = r / (2.0 * R2);
+                const double dR2_x0 = -(2.0 * A * t1 - 4.0 * g2 * t2);
+                const double dR2_y0 = -(2.0 * B * t2 - 4.0 * g2 * t1);
+                const double dR2_g1 = dA_g1 * t1 * t1 + dB_g1 * t2 * t2;
+                const double dR2_g2 = dA_g2 * t1 * t1 + dB_g2 * t2 * t2 - 4.0 * t1 * t2;
+                const double dr_g1 = dr_dR2 * dR2_g1 + r / (1.0 - gabs) * dabs1;
+                const double dr_g2 = dr_dR2 * dR2_g2 + r / (1.0 - gabs) * dabs2;
+                grad[0] += c * dm_dr * dr_dR2 * dR2_x0;
+                grad[1] += c * dm_dr * dr_dR2 * dR2_y0;
+                grad[2] += c * dm_dr * dr_g1;
+                grad[3] += c * dm_dr * dr_g2;
+            }
+            if (dpix) dpix[k] = -c;
+        }
+    *chi2_out = chi2;
+}
+
 /* Batch over a flat fp32 buffer (stamp s at pix + offset[s], h[s] x w[s]),
  * parallel over stamps with OpenMP.  stage: 0 = whole chain (orc_measure),
  * 1 = centroid, 2 = ellipticity (uses res[s] x0, y0, sigma_w), 3 = fit (uses

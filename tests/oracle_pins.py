@@ -270,6 +270,66 @@ def pin_fit_chi2_distribution(O):
     assert abs(m - 1.0) <= 4 * math.sqrt(2.0 / (N - 3)) / math.sqrt(len(vals)), m
 
 
+def pin_r50_gaussian(O):
+    """Start-up (Sec. 4.1): the growth-curve half-light radius of a circular
+    Gaussian of size s centred on a pixel is s sqrt(2 ln 2) (half the flux of a
+    2-D Gaussian lies inside that radius), up to pixelisation (< 3 %)."""
+    for s_ in (2.0, 3.0, 4.0, 6.0, 8.0):
+        img = _gauss(64, 64, 32.0, 32.0, 0.0, 0.0, s_)
+        r = O.centroid(img)
+        assert abs(r["r50"] / (math.sqrt(2 * math.log(2)) * s_) - 1) <= 0.03, (s_, r["r50"])
+
+
+def _grad_case(k):
+    rng = np.random.default_rng(40 + k)
+    h, w = int(rng.integers(14, 30)), int(rng.integers(14, 30))
+    n, re = rng.uniform(0.6, 6.0), rng.uniform(1.5, 4.0)
+    g1, g2 = rng.uniform(-0.35, 0.35, 2)
+    xc, yc = (w - 1) / 2 + rng.uniform(-1, 1), (h - 1) / 2 + rng.uniform(-1, 1)
+    img = synth.single_stamp(h, w, n=n, re=re, g1=g1, g2=g2, xc=xc, yc=yc, I0=400.0,
+                             noise_sigma=1.0, seed=60 + k)
+    # evaluate away from the generating point so that the residuals are not pure noise
+    p = np.array([xc + 0.07, yc - 0.05, g1 + 0.02, g2 - 0.015, 380.0, re * 1.05, n * 0.96])
+    return img, p
+
+
+def pin_chi2_grad_fd(O):
+    """The analytic gradient of chi^2 (Eq. 11) with respect to (x0, y0, g1, g2, I0,
+    r_e, n) and to a pixel equals Richardson-extrapolated central differences of
+    chi^2; chi^2 itself equals the fit's evaluation of Eq. 11."""
+    for k in range(4):
+        img, p = _grad_case(k)
+        iv = None if k % 2 == 0 else 0.5 + np.random.default_rng(k).random(img.shape)
+        chi2, g, dpix = O.chi2_grad(img, p, ivar=iv, pixels=True)
+        assert abs(chi2 / O.fit_eval(img, p[0], p[1], p[2], p[3], p[4:], ivar=iv)[0] - 1) <= 1e-12
+        scale = np.array([1.0, 1.0, 0.1, 0.1, abs(p[4]), p[5], p[6]])
+        for a in range(7):
+            def f(hh):
+                q = p.copy()
+                q[a] += hh
+                return O.chi2_grad(img, q, ivar=iv)[0]
+            hs = 1e-3 * scale[a]
+            d1 = (f(hs) - f(-hs)) / (2 * hs)
+            d2 = (f(hs / 2) - f(-hs / 2)) / hs
+            fd = (4 * d2 - d1) / 3
+            assert abs(g[a] - fd) <= 1e-7 * max(abs(fd), 1e-3 * np.abs(g).max()), (k, a, g[a], fd)
+        i, j = img.shape[0] // 2, img.shape[1] // 3
+        def fp(hh):
+            im = img.copy()
+            im[i, j] += hh
+            return O.chi2_grad(im, p, ivar=iv)[0]
+        fd = (fp(1e-3) - fp(-1e-3)) / 2e-3           # chi^2 is quadratic in a pixel: exact
+        assert abs(dpix[i, j] - fd) <= 1e-6 * max(1.0, abs(fd)), (dpix[i, j], fd)
+
+
+def pin_chi2_grad_noiseless(O):
+    """A noiseless Eq. 10 stamp rendered independently (scipy's b(n)) has chi^2 = 0
+    and a zero gradient at its generating parameters."""
+    img = synth.single_stamp(26, 22, n=3.3, re=2.7, g1=-0.2, g2=0.3, xc=10.4, yc=12.9, I0=250.0)
+    chi2, g = O.chi2_grad(img, [10.4, 12.9, -0.2, 0.3, 250.0, 2.7, 3.3])
+    assert chi2 <= 1e-18 and np.abs(g).max() <= 1e-7, (chi2, g)
+
+
 def pin_edge_cases(O):
     """Status codes: non-finite pixels, empty flux, out-of-range sizes."""
     img = np.ones((8, 8))
@@ -285,4 +345,5 @@ def pin_edge_cases(O):
 ALL_PINS = [pin_gamma_p_library, pin_sersic_b, pin_sersic_db, pin_flux_closed_form,
             pin_flux_pixel_sum, pin_centroid_symmetric, pin_centroid_gain, pin_ellipticity_exact,
             pin_ellipticity_step_newton, pin_matched_sigma_w, pin_stages_chain, pin_fit_noiseless,
-            pin_fit_gradient_fd, pin_fit_minimum, pin_fit_chi2_distribution, pin_edge_cases]
+            pin_fit_gradient_fd, pin_fit_minimum, pin_fit_chi2_distribution, pin_r50_gaussian,
+            pin_chi2_grad_fd, pin_chi2_grad_noiseless, pin_edge_cases]

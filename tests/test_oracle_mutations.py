@@ -48,6 +48,16 @@ MUTATIONS = {
                        "double I0 = sIf / sqrt(sff);                             /* Eq. 13 */"),
     # start-up: ties / argmax replaced by argmin
     "brightest_pixel": ("if (I[p] > I[best]) best = p;", "if (I[p] < I[best]) best = p;"),
+    # start-up: r50 at a quarter of the total instead of half
+    "r50_fraction": ("double half = 0.5 * total, prev = 0.0;", "double half = 0.25 * total, prev = 0.0;"),
+    # adjoint: the (1 - |g|) part of dr/dg dropped
+    "grad_abs_g_term": ("const double dr_g1 = dr_dR2 * dR2_g1 + r / (1.0 - gabs) * dabs1;",
+                        "const double dr_g1 = dr_dR2 * dR2_g1;"),
+    # adjoint: sign of the cross term in dR^2/dx0
+    "grad_x0_cross_sign": ("const double dR2_x0 = -(2.0 * A * t1 - 4.0 * g2 * t2);",
+                           "const double dR2_x0 = -(2.0 * A * t1 + 4.0 * g2 * t2);"),
+    # adjoint: sign of the pixel gradient
+    "grad_dpix_sign": ("if (dpix) dpix[k] = -c;", "if (dpix) dpix[k] = c;"),
     # non-finite input no longer flagged
     "nonfinite_check": ("if (!isfinite(I[p])) { *status |= ORC_NONFINITE; return 0; }", ""),
 }
