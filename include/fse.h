@@ -195,6 +195,29 @@ int fse_fit_batch_host(fse_ctx *ctx, const void *pix, int64_t npix_total, int dt
 int fse_sersic_b(fse_ctx *ctx, const double *n, double *b, double *db, int64_t count,
                  void *stream);
 
+/* chi^2 (Eq. 11) of the elliptical Sérsic model (Eq. 10) at given parameters,
+ * and its gradient (the adjoint) with respect to the parameters and to the
+ * pixels.  params[s*7 + k] holds (x0, y0, e1, e2, I0, r_e, n) for stamp s, in
+ * the conventions above (centre in stamp pixels, g of Eq. A1, r_e along the
+ * major axis).  With residuals r_i = m_i - I_i and weights w_i (inv_var, or 1):
+ *   chi2[s]            = sum_i w_i r_i^2                       (fp64)
+ *   dparams[s*7 + k]   = gout[s] * 2 sum_i w_i r_i dm_i/dp_k    (fp32)
+ *   dpix[offset_s + i] = gout[s] * (-2 w_i r_i)                 (fp32)
+ * gout (count doubles, or NULL = 1 for every stamp) makes the call a
+ * vector-Jacobian product.  dpix has the element layout of pix (each stamp at
+ * its own offset) and is the derivative with respect to the decoded pixel
+ * value; it is always fp32.  chi2, dparams and dpix may each be NULL (not
+ * computed), but not all three.  The pixel at R^2 = 0 adds no derivative with
+ * respect to the centre or the ellipticity, and d|g|/dg is taken as 0 at
+ * g = 0.  A stamp whose size is outside [1, FSE_MAX_PIX], or whose parameters
+ * are not finite or lie outside r_e > 0, |g| < 1, n in [0.129, 10.27] (the
+ * b(n) table), gets NaN in chi2, dparams and (for a valid size) dpix.  All
+ * arrays are device pointers; asynchronous on `stream`. */
+int fse_sersic_chi2_grad(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
+                         const fse_stamp *idx, int64_t count, const float *inv_var,
+                         const float *params, const double *gout, double *chi2,
+                         float *dparams, float *dpix, void *stream);
+
 /* Wait for `stream` and report a bounded device wait that expired during any
  * earlier call of this context (FSE_ETIMEOUT), or FSE_OK.  Clears the flag. */
 int fse_sync_check(fse_ctx *ctx, void *stream);

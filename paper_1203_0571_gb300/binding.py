@@ -32,7 +32,8 @@ ST = dict(MOM_CONVERGED=1 << 0, FIT_CONVERGED=1 << 1, MOM_MAXITER=1 << 2, FIT_MA
 # exported symbols, in the order include/fse.h declares them
 EXPORTS = ["fse_create", "fse_destroy", "fse_last_error", "fse_opts_default", "fse_centroid",
            "fse_ellipticity", "fse_sersic_fit", "fse_fit_batch", "fse_fit_batch_plain",
-           "fse_fit_batch_host", "fse_sersic_b", "fse_sync_check", "fse_fit_batch_static"]
+           "fse_fit_batch_host", "fse_sersic_b", "fse_sersic_chi2_grad", "fse_sync_check",
+           "fse_fit_batch_static"]
 
 
 class Opts(ctypes.Structure):
@@ -90,6 +91,9 @@ def load(build: bool = True, path: str | None = None) -> ctypes.CDLL:
     L.fse_fit_batch_host.restype = ctypes.c_int
     L.fse_sersic_b.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, _vp]
     L.fse_sersic_b.restype = ctypes.c_int
+    L.fse_sersic_chi2_grad.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int64, _vp, _vp,
+                                       _vp, _vp, _vp, _vp, _vp]
+    L.fse_sersic_chi2_grad.restype = ctypes.c_int
     L.fse_sync_check.argtypes = [_vp, _vp]
     L.fse_sync_check.restype = ctypes.c_int
     L.fse_fit_batch_static.argtypes = [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int64, _vp,
@@ -247,6 +251,28 @@ class Context:
                                         _stream(stream)))
         return b, db
 
+    def chi2_grad(self, pix, index, params, *, scale=None, inv_var=None, gout=None,
+                  want_chi2=True, want_dparams=True, want_dpix=False, stream=None):
+        """fse_sersic_chi2_grad: chi^2 and its gradient at params (float32 [N, 7]).
+
+        Returns (chi2 float64 [N] or None, dparams float32 [N, 7] or None,
+        dpix float32 like pix or None)."""
+        n = int(index.shape[0])
+        dev = pix.device
+        chi2 = torch.empty(n, dtype=torch.float64, device=dev) if want_chi2 else None
+        dpar = torch.empty((n, 7), dtype=torch.float32, device=dev) if want_dparams else None
+        dpix = torch.zeros(pix.numel(), dtype=torch.float32, device=dev) if want_dpix else None
+        params = params.contiguous()
+        if params.dtype != torch.float32 or params.shape != (n, 7):
+            raise TypeError("params must be float32 [N, 7]")
+        if gout is not None:
+            gout = gout.to(torch.float64).contiguous()
+        rc = load().fse_sersic_chi2_grad(self._h, _ptr(pix), _dtype_of(pix), _ptr(scale), _ptr(index),
+                                         n, _ptr(inv_var), _ptr(params), _ptr(gout), _ptr(chi2),
+                                         _ptr(dpar), _ptr(dpix), _stream(stream))
+        self._check(rc)
+        return chi2, dpar, dpix
+
     def sync_check(self, stream=None):
         """fse_sync_check: wait for the stream and raise if a bounded device wait expired."""
         self._check(load().fse_sync_check(self._h, _stream(stream)))
@@ -279,6 +305,10 @@ def fse_fit_batch_host(ctx: Context, *a, **k):
 
 def fse_sersic_b(ctx: Context, *a, **k):
     return ctx.sersic_b(*a, **k)
+
+
+def fse_sersic_chi2_grad(ctx: Context, *a, **k):
+    return ctx.chi2_grad(*a, **k)
 
 
 def fse_sync_check(ctx: Context, *a, **k):

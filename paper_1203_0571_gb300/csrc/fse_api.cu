@@ -465,6 +465,44 @@ int fse_sersic_b(fse_ctx* ctx, const double* n, double* b, double* db, int64_t c
     return FSE_OK;
 }
 
+int fse_sersic_chi2_grad(fse_ctx* ctx, const void* pix, int dtype, const float* scale,
+                         const fse_stamp* idx, int64_t count, const float* inv_var,
+                         const float* params, const double* gout, double* chi2, float* dparams,
+                         float* dpix, void* stream) {
+    if (!ctx) return FSE_EINVAL;
+    if (count < 0 || count > 0x7fffffffLL) return set_error(ctx, FSE_EINVAL, "count out of range");
+    if (dtype != FSE_F32 && dtype != FSE_BF16) return set_error(ctx, FSE_EINVAL, "unknown dtype %d", dtype);
+    if (count == 0) return FSE_OK;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return set_error(ctx, FSE_ECUDA, "cannot select device %d", ctx->device);
+    if (!pix || !idx || !params) return set_error(ctx, FSE_EINVAL, "pix, idx and params must not be NULL");
+    if (!chi2 && !dparams && !dpix) return set_error(ctx, FSE_EINVAL, "no output requested");
+    const void* dev_ptrs[] = {pix, idx, params, scale, inv_var, gout, chi2, dparams, dpix};
+    for (const void* q : dev_ptrs)
+        if (q && !is_device_ptr(q))
+            return set_error(ctx, FSE_EINVAL, "all array arguments must be device pointers");
+    fse::GradArgs a;
+    memset(&a, 0, sizeof a);
+    a.pix = pix;
+    a.dtype = dtype;
+    a.scale = scale;
+    a.idx = idx;
+    a.count = count;
+    a.inv_var = inv_var;
+    a.params = params;
+    a.gout = gout;
+    a.chi2 = chi2;
+    a.dparams = dparams;
+    a.dpix = dpix;
+    a.queue = ctx->d_queue + (ctx->next_queue++ % kQueues);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "work counter reset");
+    e = fse::launch_chi2_grad(a, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "chi2/adjoint launch");
+    return FSE_OK;
+}
+
 int fse_sync_check(fse_ctx* ctx, void* stream) {
     if (!ctx) return FSE_EINVAL;
     DeviceGuard g(ctx->device);

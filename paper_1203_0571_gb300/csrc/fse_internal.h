@@ -45,6 +45,22 @@ struct LaunchArgs {
     int static_assign;       // 1: warp w of the grid takes stamp w only (no counter)
 };
 
+// Arguments of the chi^2 / adjoint kernel (fse_sersic_chi2_grad).
+struct GradArgs {
+    const void* pix;
+    int dtype;
+    const float* scale;
+    const fse_stamp* idx;
+    int64_t count;
+    const float* inv_var;
+    const float* params;     // count x 7: x0, y0, e1, e2, I0, r_e, n
+    const double* gout;      // count upstream gradients, or NULL (= 1)
+    double* chi2;            // count, or NULL
+    float* dparams;          // count x 7, or NULL
+    float* dpix;             // laid out like pix (fp32), or NULL
+    unsigned int* queue;     // work counter (zeroed before launch)
+};
+
 // Number of nodes of the b(n) table and its range.
 constexpr double kBnLo = 0.125;
 constexpr double kBnStep = 1.0 / 512.0;
@@ -56,6 +72,8 @@ cudaError_t build_bn_table(cudaStream_t stream);
 cudaError_t eval_bn(const double* n, double* b, double* db, int64_t count, cudaStream_t stream);
 // Launches the estimator kernel; returns the launch error.
 cudaError_t launch_estimator(const LaunchArgs& a, cudaStream_t stream);
+// Launches the chi^2 / adjoint kernel; returns the launch error.
+cudaError_t launch_chi2_grad(const GradArgs& a, cudaStream_t stream);
 // Shared memory a warp needs for stamps of up to max_pix pixels.
 size_t smem_per_warp(int max_pix);
 // Largest warps-per-CTA / CTAs-per-SM choice for a tile size.
