@@ -83,7 +83,7 @@ class Oracle:
                                      [ctypes.c_int, _dp]
         L.orc_fit_eval.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + \
                                   [_dp, _dp]
-        L.orc_chi2_grad.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
+        L.orc_chi2_grad.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
         L.orc_chi2_grad.restype = None
         L.orc_batch.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(Opts), ctypes.c_int,
@@ -162,18 +162,26 @@ class Oracle:
                             xc, yc, g1, g2, _as_dp(pp), _as_dp(out))
         return out[0], out[1:4].copy(), out[4:].reshape(3, 3).copy()
 
-    def chi2_grad(self, I, p, ivar=None, pixels: bool = False):
+    def chi2_grad(self, I, p, ivar=None, pixels: bool = False, scales: bool = False):
         """chi^2 and its gradient with respect to p = (x0, y0, g1, g2, I0, r_e, n)
-        (and, with pixels=True, to every pixel) for one stamp."""
+        for one stamp; with pixels=True also the pixel gradient, with scales=True
+        also the first-order error scales (8 values: 7 parameters, chi^2)."""
         I = _img(I)
         iv = None if ivar is None else _img(ivar)
         pp = np.ascontiguousarray(p, dtype=np.float64)
         chi2 = np.zeros(1)
         g = np.zeros(7)
         dp = np.zeros(I.shape) if pixels else None
+        sc = np.zeros(8) if scales else None
         self.L.orc_chi2_grad(_as_dp(I), None if iv is None else _as_dp(iv), I.shape[0], I.shape[1],
-                             _as_dp(pp), _as_dp(chi2), _as_dp(g), None if dp is None else _as_dp(dp))
-        return (float(chi2[0]), g, dp) if pixels else (float(chi2[0]), g)
+                             _as_dp(pp), _as_dp(chi2), _as_dp(g), None if dp is None else _as_dp(dp),
+                             None if sc is None else _as_dp(sc))
+        out = (float(chi2[0]), g)
+        if pixels:
+            out += (dp,)
+        if scales:
+            out += (sc,)
+        return out
 
     def batch(self, pix, offset, h, w, stage: str = "measure", ivar=None,
               opts: Opts | None = None, init=None, threads: int = 0):

@@ -698,9 +698,14 @@ void orc_fit_eval(const double *I, const double *ivar, int h, int w, double xc, 
  *   dr/dR^2 = r / (2 R^2),   dr/d|g| = r / (1 - |g|),   d|g|/dg_k = g_k / |g|.
  * The pixel at R^2 = 0 adds no centre or shape derivative (the profile has a
  * cusp there for n > 1), and d|g|/dg is taken as 0 at g = 0 (the kink).
- * Writes chi^2, grad[7] and, if dpix != NULL, the h*w pixel gradient. */
+ * Writes chi^2, grad[7] and, if dpix != NULL, the h*w pixel gradient.
+ * If scale != NULL it also writes the first-order error scales of a
+ * lower-precision evaluation: scale[k] = sum_i 2 w_i |dm_i/dp_k| (|m_i| + |r_i|)
+ * for k < 7 and scale[7] = sum_i 2 w_i |r_i| (|m_i| + |r_i|).  An
+ * implementation whose per-pixel m and r carry relative errors up to eps
+ * differs from grad[k] and chi^2 by at most about eps * scale[k]. */
 void orc_chi2_grad(const double *I, const double *ivar, int h, int w, const double p[7],
-                   double *chi2_out, double grad[7], double *dpix)
+                   double *chi2_out, double grad[7], double *dpix, double scale[8])
 {
     const double x0 = p[0], y0 = p[1], g1 = p[2], g2 = p[3], I0 = p[4], re = p[5], n = p[6];
     const double gabs = sqrt(g1 * g1 + g2 * g2);
@@ -713,9 +718,11 @@ void orc_chi2_grad(const double *I, const double *ivar, int h, int w, const doub
     const double dabs1 = gabs > 0.0 ? g1 / gabs : 0.0, dabs2 = gabs > 0.0 ? g2 / gabs : 0.0;
     double chi2 = 0.0;
     for (int a = 0; a < 7; ++a) grad[a] = 0.0;
+    if (scale) for (int a = 0; a < 8; ++a) scale[a] = 0.0;
     for (int i = 0; i < h; ++i)
         for (int j = 0; j < w; ++j) {
             const int k = i * w + j;
+            double dm[7] = { 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0 };   /* dm/dp, for scale */
             const double t1 = j - x0, t2 = i - y0;
             const double R2 = ellip_R2(t1, t2, g1, g2);
             const double r = sqrt(R2 > 0.0 ? R2 : 0.0) / (1.0 - gabs);
@@ -727,9 +734,9 @@ void orc_chi2_grad(const double *I, const double *ivar, int h, int w, const doub
             const double res = m - I[k];
             const double c = 2.0 * wgt * res;
             chi2 += wgt * res * res;
-            grad[4] += c * E;                                        /* dm/dI0 = E */
-            grad[5] += c * m * b * u / (n * re);                     /* dm/dr_e */
-            if (x > 0.0) grad[6] += c * m * u * (b * log(x) / (n * n) - db);   /* dm/dn */
+            dm[4] = E;                                               /* dm/dI0 */
+            dm[5] = m * b * u / (n * re);                            /* dm/dr_e */
+            if (x > 0.0) dm[6] = m * u * (b * log(x) / (n * n) - db);   /* dm/dn */
             if (R2 > 0.0) {
                 const double dm_dr = -m * b * u / (n * r);
                 const double dr_dR2 = r / (2.0 * R2);
@@ -739,10 +746,16 @@ void orc_chi2_grad(const double *I, const double *ivar, int h, int w, const doub
                 const double dR2_g2 = dA_g2 * t1 * t1 + dB_g2 * t2 * t2 - 4.0 * t1 * t2;
                 const double dr_g1 = dr_dR2 * dR2_g1 + r / (1.0 - gabs) * dabs1;
                 const double dr_g2 = dr_dR2 * dR2_g2 + r / (1.0 - gabs) * dabs2;
-                grad[0] += c * dm_dr * dr_dR2 * dR2_x0;
-                grad[1] += c * dm_dr * dr_dR2 * dR2_y0;
-                grad[2] += c * dm_dr * dr_g1;
-                grad[3] += c * dm_dr * dr_g2;
+                dm[0] = dm_dr * dr_dR2 * dR2_x0;
+                dm[1] = dm_dr * dr_dR2 * dR2_y0;
+                dm[2] = dm_dr * dr_g1;
+                dm[3] = dm_dr * dr_g2;
+            }
+            for (int a = 0; a < 7; ++a) grad[a] += c * dm[a];
+            if (scale) {
+                const double mag = 2.0 * wgt * (fabs(m) + fabs(res));
+                for (int a = 0; a < 7; ++a) scale[a] += mag * fabs(dm[a]);
+                scale[7] += mag * fabs(res);
             }
             if (dpix) dpix[k] = -c;
         }
