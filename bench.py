@@ -38,10 +38,10 @@ WORKLOAD = 1
 # pass of the method as formulated here; see the design notes for the derivation.
 OPS_INIT = 12          # brightest pixel, total, growth-curve ring histogram
 OPS_MOMENT = 24        # one weighted pass (11 moments, 1 ex2)
-OPS_MOM_REFINE = 88    # one moment refinement pass (exact offsets, ~1-ulp exp2, double-float sums); two run
+OPS_MOM_REFINE = 88    # one moment refinement pass (exact offsets, ~1-ulp exp2, double-float sums)
 OPS_FIT_SETUP = 8 + 26  # 0.5 log2 R^2 per pixel + the four-candidate start pass (8 ex2)
 OPS_FIT = 18           # one profile pass (10 sums, 2 ex2)
-OPS_REFINE = 68        # one fit refinement pass (two ~1-ulp exp2, double-float sums); two run
+OPS_REFINE = 76        # one fit refinement pass (two ~1-ulp exp2, double-float and curvature sums)
 SMS = 152
 LANES_PER_SM = 128
 
@@ -66,9 +66,10 @@ def algorithmic_ops(res) -> float:
     ok = (st & (32 | 16)) == 0
     fit = ((st & 1) != 0) & ok
     ops = npix * (OPS_INIT + OPS_MOMENT * res["it_mom"]) * ok
-    ops += npix * 2 * OPS_MOM_REFINE * fit
+    # one refinement pass of each kind, and a second where the status says it ran
+    ops += npix * OPS_MOM_REFINE * (1 + ((st & (1 << 13)) != 0)) * fit
     ops += npix * (OPS_FIT_SETUP + OPS_FIT * res["it_fit"]) * fit
-    ops += npix * 2 * OPS_REFINE * (((st & 2) != 0) & ((st & 128) == 0) & fit)
+    ops += npix * OPS_REFINE * (1 + ((st & (1 << 14)) != 0)) * (((st & 2) != 0) & ((st & 128) == 0) & fit)
     return float(ops.sum())
 
 

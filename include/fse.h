@@ -75,6 +75,8 @@ extern "C" {
 #define FSE_ST_SIGW_CLAMPED   (1u << 10) /* sigma_w clamped to [0.5, min(h,w)/2]            */
 #define FSE_ST_INIT_FALLBACK  (1u << 11) /* stamp total <= 0: sigma_w from r50 = 1.1774 px  */
 #define FSE_ST_TIMEOUT        (1u << 12) /* a bounded device wait expired for this stamp    */
+#define FSE_ST_MOM_REFINE2    (1u << 13) /* informational: a second moment refinement ran    */
+#define FSE_ST_FIT_REFINE2    (1u << 14) /* informational: a second fit refinement ran       */
 
 typedef struct fse_ctx fse_ctx;
 

@@ -27,7 +27,7 @@ FSE_MAX_PIX = 128 * 128
 ST = dict(MOM_CONVERGED=1 << 0, FIT_CONVERGED=1 << 1, MOM_MAXITER=1 << 2, FIT_MAXITER=1 << 3,
           NONFINITE=1 << 4, BAD_SIZE=1 << 5, MOM_FAILED=1 << 6, FIT_BOUND=1 << 7,
           FIT_SINGULAR=1 << 8, NONPOS_FLUX=1 << 9, SIGW_CLAMPED=1 << 10, INIT_FALLBACK=1 << 11,
-          TIMEOUT=1 << 12)
+          TIMEOUT=1 << 12, MOM_REFINE2=1 << 13, FIT_REFINE2=1 << 14)
 
 # exported symbols, in the order include/fse.h declares them
 EXPORTS = ["fse_create", "fse_destroy", "fse_last_error", "fse_opts_default", "fse_centroid",

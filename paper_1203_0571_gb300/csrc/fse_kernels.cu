@@ -552,8 +552,8 @@ __device__ __forceinline__ void shear_polarizability(const float (&m)[11], const
 // the weighted first moments, i.e. k taken from the moments) and the step of
 // Eq. 9 for g.  The fp32 iteration stops within the noise of its own sums
 // (~1e-6 px); this pass removes most of that noise.
-__device__ void moment_refine(const float* __restrict__ s, int w, int npix, int lane, bool ellip,
-                              MomState& st) {
+__device__ float moment_refine(const float* __restrict__ s, int w, int npix, int lane, bool ellip,
+                               MomState& st) {
     const float gg = st.g1 * st.g1 + st.g2 * st.g2;
     const float A = 1.f + gg - 2.f * st.g1;
     const float B = 1.f + gg + 2.f * st.g1;
@@ -603,7 +603,7 @@ __device__ void moment_refine(const float* __restrict__ s, int w, int npix, int 
     const float Q11 = dh[3] + (dl[3] + cx[2]);
     const float Q12 = dh[4] + (dl[4] + cx[3]);
     const float Q22 = dh[5] + (dl[5] + cx[4]);
-    if (!(M0 > 0.f) || !(Q11 + Q22 > 0.f)) return;
+    if (!(M0 > 0.f) || !(Q11 + Q22 > 0.f)) return 1.f;
     const float c = 1.f / (2.f * st.sw * st.sw);
     const float g1 = st.g1, g2 = st.g2;
     const float J11 = 2.f * c * (A * Q11 - 2.f * g2 * Q12) - M0;
@@ -611,7 +611,7 @@ __device__ void moment_refine(const float* __restrict__ s, int w, int npix, int 
     const float J21 = 2.f * c * (A * Q12 - 2.f * g2 * Q22);
     const float J22 = 2.f * c * (B * Q22 - 2.f * g2 * Q12) - M0;
     const float dj = J11 * J22 - J12 * J21;
-    if (!(dj > 0.f)) return;
+    if (!(dj > 0.f)) return 1.f;
     const float dx = -(J22 * M1x - J12 * M1y) / dj;
     const float dy = -(-J21 * M1x + J11 * M1y) / dj;
     float dg1 = 0.f, dg2 = 0.f;
@@ -633,19 +633,22 @@ __device__ void moment_refine(const float* __restrict__ s, int w, int npix, int 
         float P11, P12, P21, P22;
         shear_polarizability(m, st, (Q11 - Q22) / T, 2.f * Q12 / T, &P11, &P12, &P21, &P22);
         const float det = P11 * P22 - P12 * P21;
-        if (!(fabsf(det) > 0.f) || !isfinite(det)) return;
+        if (!(fabsf(det) > 0.f) || !isfinite(det)) return 1.f;
         const float sc = (1.f - gg) / det;
         dg1 = sc * (P22 * r1 - P12 * r2);
         dg2 = sc * (-P21 * r1 + P11 * r2);
     }
     // a refinement moves the point by at most the iteration's own noise
     if (!(fabsf(dx) <= 1e-3f && fabsf(dy) <= 1e-3f && fabsf(dg1) <= 1e-3f && fabsf(dg2) <= 1e-3f))
-        return;
+        return 1.f;
     st.xf += dx;
     st.yf += dy;
     st.g1 += dg1;
     st.g2 += dg2;
+    return fmaxf(fmaxf(fabsf(dx), fabsf(dy)), fmaxf(fabsf(dg1), fabsf(dg2)));
 }
+
+constexpr float kMomRefineSkip = 1e-7f;
 
 // Iterate to the stop rule.  Returns the number of passes; sets status bits.
 __device__ int moment_iterate(const float* s, __half2* C, int h, int w, int npix, int lane,
@@ -721,11 +724,14 @@ __device__ int moment_iterate(const float* s, __half2* C, int h, int w, int npix
         status |= FSE_ST_MOM_MAXITER;
         it = o.max_iter_mom;
     }
-    // two refinement steps: the first leaves ~1e-7 (the centre and g steps are
-    // taken separately), the second ~1e-8
+    // refinement steps: the first leaves about a tenth of its own step (the
+    // centre and g steps are taken separately); a second runs unless the first
+    // moved the point by less than 1e-7
     if (status & FSE_ST_MOM_CONVERGED) {
-#pragma unroll 1
-        for (int r = 0; r < 2; ++r) moment_refine(s, w, npix, lane, ellip, st);
+        if (moment_refine(s, w, npix, lane, ellip, st) > kMomRefineSkip) {
+            moment_refine(s, w, npix, lane, ellip, st);
+            status |= FSE_ST_MOM_REFINE2;
+        }
     }
     return it;
 }
@@ -1151,6 +1157,8 @@ __device__ Refined fit_refine(const float* __restrict__ s, const float* __restri
     return o;
 }
 
+constexpr float kFitRefineSkip = 1e-5f;
+
 struct FitOut {
     float I0, re, n, flux;
     double chi2;
@@ -1274,16 +1282,22 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
     out.n = n;
     out.chi2 = cur.chi2;
     if (converged && isfinite(cur.chi2) && re > re_min && re < re_max && n > n_min && n < n_max) {
-        // two refinement passes: the second evaluates chi^2 exactly at the
-        // first one's point, and its own step is much smaller than the first
+        // Newton refinement passes.  The error left after one is about the
+        // square of its step, and its chi^2 (exact at the start point plus the
+        // quadratic model of the step) is then exact to third order in the
+        // step; a second pass runs unless the first step was below 1e-5.
 #pragma unroll 1
         for (int r = 0; r < 2; ++r) {
             const Refined rf = fit_refine<IVAR>(s, L, sq, w, npix, lane, out.I0, out.re, out.n, lq,
-                                                st, r == 1);
+                                                st, true);
+            const float step = fmaxf(fabsf(static_cast<float>(rf.re) / out.re - 1.f),
+                                     fabsf(static_cast<float>(rf.n) / out.n - 1.f));
             out.I0 = static_cast<float>(rf.I0);
             out.re = static_cast<float>(rf.re);
             out.n = static_cast<float>(rf.n);
             out.chi2 = rf.chi2;
+            if (r == 1) status |= FSE_ST_FIT_REFINE2;
+            if (!rf.applied || step <= kFitRefineSkip) break;
         }
     }
     if (out.re <= re_min || out.re >= re_max || out.n <= n_min || out.n >= n_max)
