@@ -78,6 +78,10 @@ extern "C" {
 #define FSE_ST_MOM_REFINE2    (1u << 13) /* informational: a second moment refinement ran    */
 #define FSE_ST_FIT_REFINE2    (1u << 14) /* informational: a second fit refinement ran       */
 
+/* fse_opts.flags: fse_fit_batch_ragged captures its launch sequence into a
+ * CUDA graph on first use and replays it while its arguments are unchanged. */
+#define FSE_FLAG_GRAPH        (1u << 0)
+
 typedef struct fse_ctx fse_ctx;
 
 /* Stamp index entry (16 bytes).  offset counts elements (not bytes). */
@@ -108,7 +112,7 @@ typedef struct {
     double  re_min;         /* lower bound on r_e, px                         (0.2)     */
     double  re_max_frac;    /* upper bound on r_e = re_max_frac * max(h, w)   (2)       */
     double  lm_lambda0;     /* initial Levenberg-Marquardt damping            (1e-3)    */
-    uint32_t flags;         /* reserved, 0                                              */
+    uint32_t flags;         /* FSE_FLAG_* bits                                 (0)       */
     int32_t warps_per_cta;  /* launch shape: 0 (library choice), 1, 2, 4 or 8                      */
 } fse_opts;
 
@@ -191,6 +195,39 @@ int fse_fit_batch_host(fse_ctx *ctx, const void *pix, int64_t npix_total, int dt
                        const float *scale, const fse_stamp *idx, int64_t count,
                        const float *inv_var, const fse_opts *opts, fse_result *out,
                        void *stream);
+
+/* fse_fit_batch for a RAGGED batch (stamps of different sizes, 1 to
+ * FSE_MAX_PIX pixels, in any order).  The stamps are bucketed on the device
+ * into seven size classes (h*w up to 16^2, 24^2, 32^2, 48^2, 64^2, 96^2,
+ * 128^2), and each class runs in its own persistent launch whose shared-memory
+ * tile fits that class, largest class first.  Results are those of
+ * fse_fit_batch, stamp by stamp.  opts->max_pix is not used (each class sets
+ * its own); opts->warps_per_cta, if non-zero, applies to every class, else
+ * the class uses the choice of fse_autotune or the library default.  With
+ * FSE_FLAG_GRAPH in opts->flags the classification and the class launches are
+ * captured into a CUDA graph on a context stream the first time, and later
+ * calls with the same pointers, count, options and tuning replay it on
+ * `stream`.  Device workspace: 4 bytes per stamp, grown as needed (a grown
+ * buffer is a new pointer, so the next call captures again).  One ragged call
+ * may be in flight per context. */
+int fse_fit_batch_ragged(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
+                         const fse_stamp *idx, int64_t count, const float *inv_var,
+                         const fse_opts *opts, fse_result *out, void *stream);
+
+/* Choose warps per CTA (1, 2, 4 or 8, as far as shared memory allows) for
+ * each size class of fse_fit_batch_ragged by timing the class launches on
+ * this batch (each candidate twice, the faster counts).  The choice is kept
+ * in the context for this dtype and inverse-variance setting and used by
+ * later ragged calls.  out receives the batch's results.  Synchronises
+ * `stream`.  No counterpart in the paper: a launch-shape search. */
+int fse_autotune(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
+                 const fse_stamp *idx, int64_t count, const float *inv_var,
+                 const fse_opts *opts, fse_result *out, void *stream);
+
+/* The warps per CTA the ragged path uses for each of the seven size classes
+ * (tuned or default), for a dtype and with (1) or without (0) inverse
+ * variance.  warps is a host array of 7. */
+int fse_tuned_warps(const fse_ctx *ctx, int dtype, int has_inv_var, int32_t *warps);
 
 /* Evaluate the device b(n) table (Eq. 10: P(2n, b) = 1/2) and its derivative
  * at count values n[i] in [0.2, 10] (device pointers, doubles).  For tests. */

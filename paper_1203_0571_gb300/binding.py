@@ -32,8 +32,8 @@ ST = dict(MOM_CONVERGED=1 << 0, FIT_CONVERGED=1 << 1, MOM_MAXITER=1 << 2, FIT_MA
 # exported symbols, in the order include/fse.h declares them
 EXPORTS = ["fse_create", "fse_destroy", "fse_last_error", "fse_opts_default", "fse_centroid",
            "fse_ellipticity", "fse_sersic_fit", "fse_fit_batch", "fse_fit_batch_plain",
-           "fse_fit_batch_host", "fse_sersic_b", "fse_sersic_chi2_grad", "fse_sync_check",
-           "fse_fit_batch_static"]
+           "fse_fit_batch_host", "fse_fit_batch_ragged", "fse_autotune", "fse_tuned_warps",
+           "fse_sersic_b", "fse_sersic_chi2_grad", "fse_sync_check", "fse_fit_batch_static"]
 
 
 class Opts(ctypes.Structure):
@@ -83,7 +83,7 @@ def load(build: bool = True, path: str | None = None) -> ctypes.CDLL:
     L.fse_opts_default.restype = None
     dev_sig = [_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int64, _vp, ctypes.POINTER(Opts), _vp, _vp]
     for f in ("fse_centroid", "fse_ellipticity", "fse_sersic_fit", "fse_fit_batch",
-              "fse_fit_batch_plain"):
+              "fse_fit_batch_plain", "fse_fit_batch_ragged", "fse_autotune"):
         getattr(L, f).argtypes = dev_sig
         getattr(L, f).restype = ctypes.c_int
     L.fse_fit_batch_host.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int, _vp, _vp,
@@ -91,6 +91,8 @@ def load(build: bool = True, path: str | None = None) -> ctypes.CDLL:
     L.fse_fit_batch_host.restype = ctypes.c_int
     L.fse_sersic_b.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, _vp]
     L.fse_sersic_b.restype = ctypes.c_int
+    L.fse_tuned_warps.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]
+    L.fse_tuned_warps.restype = ctypes.c_int
     L.fse_sersic_chi2_grad.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int64, _vp, _vp,
                                        _vp, _vp, _vp, _vp, _vp]
     L.fse_sersic_chi2_grad.restype = ctypes.c_int
@@ -217,6 +219,21 @@ class Context:
         """fse_fit_batch_plain: the same chain, one launch per stamp."""
         return self._dev_call("fse_fit_batch_plain", pix, index, out, scale, inv_var, opts, stream)
 
+    def fit_batch_ragged(self, pix, index, *, scale=None, inv_var=None, opts=None, out=None,
+                         stream=None):
+        """fse_fit_batch_ragged: size-class launches (opts.flags |= 1 replays a CUDA graph)."""
+        return self._dev_call("fse_fit_batch_ragged", pix, index, out, scale, inv_var, opts, stream)
+
+    def autotune(self, pix, index, *, scale=None, inv_var=None, opts=None, out=None, stream=None):
+        """fse_autotune: time the launch shapes of each size class on this batch."""
+        return self._dev_call("fse_autotune", pix, index, out, scale, inv_var, opts, stream)
+
+    def tuned_warps(self, dtype: int = FSE_F32, inv_var: bool = False) -> list:
+        """fse_tuned_warps: warps per CTA of the seven size classes."""
+        w = (ctypes.c_int32 * 7)()
+        self._check(load().fse_tuned_warps(self._h, dtype, int(inv_var), w))
+        return list(w)
+
     def fit_batch_host(self, pix: np.ndarray | torch.Tensor, index: np.ndarray | torch.Tensor, *,
                        scale=None, inv_var=None, opts=None, out=None, stream=None) -> np.ndarray:
         """fse_fit_batch_host: host buffers in, host results out (synchronous)."""
@@ -301,6 +318,18 @@ def fse_fit_batch_plain(ctx: Context, *a, **k):
 
 def fse_fit_batch_host(ctx: Context, *a, **k):
     return ctx.fit_batch_host(*a, **k)
+
+
+def fse_fit_batch_ragged(ctx: Context, *a, **k):
+    return ctx.fit_batch_ragged(*a, **k)
+
+
+def fse_autotune(ctx: Context, *a, **k):
+    return ctx.autotune(*a, **k)
+
+
+def fse_tuned_warps(ctx: Context, *a, **k):
+    return ctx.tuned_warps(*a, **k)
 
 
 def fse_sersic_b(ctx: Context, *a, **k):

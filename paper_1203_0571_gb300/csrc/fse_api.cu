@@ -32,6 +32,19 @@ struct fse_ctx {
     size_t scale_cap = 0;
     float* d_ivar = nullptr;
     size_t ivar_cap = 0;
+    // ragged path: stamps grouped by size class, and the class bookkeeping
+    // (counts[K] | range[2K] | cursor[K] | work counters[K])
+    int32_t* d_perm = nullptr;
+    size_t perm_cap = 0;
+    unsigned int* d_cls = nullptr;
+    // warps per CTA chosen by fse_autotune, by dtype, inverse variance and size
+    // class (0 = library default)
+    int tuned[2][2][fse::kClasses] = {};
+    unsigned tune_version = 0;
+    // the CUDA graph of the last ragged call made with FSE_FLAG_GRAPH
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    unsigned char gkey[256] = {0};
 };
 
 namespace {
@@ -96,6 +109,8 @@ int check_opts(fse_ctx* ctx, const fse_opts* o) {
     const int w = o->warps_per_cta;
     if (!(w == 0 || w == 1 || w == 2 || w == 4 || w == 8))
         return set_error(ctx, FSE_EINVAL, "warps_per_cta must be 0, 1, 2, 4 or 8");
+    if (o->flags & ~static_cast<uint32_t>(FSE_FLAG_GRAPH))
+        return set_error(ctx, FSE_EINVAL, "unknown bits in flags");
     return FSE_OK;
 }
 
@@ -195,6 +210,82 @@ int grow(fse_ctx* ctx, T** p, size_t* cap, size_t n) {
     return FSE_OK;
 }
 
+// ---------------------------------------------------------------- ragged path
+constexpr int kK = fse::kClasses;
+
+int ragged_workspace(fse_ctx* ctx, int64_t count) {
+    int rc = grow(ctx, &ctx->d_perm, &ctx->perm_cap, static_cast<size_t>(count));
+    if (rc) return rc;
+    if (!ctx->d_cls) {
+        cudaError_t e = cudaMalloc(&ctx->d_cls, 5 * kK * sizeof(unsigned int));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(ctx, FSE_ENOMEM, "ragged workspace: %s", cudaGetErrorString(e));
+        }
+    }
+    return FSE_OK;
+}
+
+int class_warps(const fse_ctx* ctx, const fse::LaunchArgs& a, int user_wpc, int k) {
+    if (user_wpc > 0) return user_wpc;
+    const int t = ctx->tuned[a.dtype == FSE_BF16][a.inv_var != nullptr][k];
+    return t > 0 ? t : default_warps(fse::kClassPix[k]);
+}
+
+// Classification, then one persistent launch per size class (largest first),
+// each with a shared-memory tile for its class.  Everything is stream-ordered
+// on `s` with no host synchronisation, so the sequence can be captured.
+int enqueue_ragged(fse_ctx* ctx, const fse::LaunchArgs& a, int user_wpc, cudaStream_t s) {
+    unsigned int* counts = ctx->d_cls;
+    unsigned int* range = counts + kK;
+    unsigned int* cursor = range + 2 * kK;
+    unsigned int* queues = cursor + kK;
+    cudaError_t e = cudaMemsetAsync(counts, 0, kK * sizeof(unsigned int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(queues, 0, kK * sizeof(unsigned int), s);
+    if (e == cudaSuccess) e = fse::classify_stamps(a.idx, a.count, counts, range, cursor, ctx->d_perm, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "size classification");
+    for (int k = kK - 1; k >= 0; --k) {
+        fse::LaunchArgs b = a;
+        b.opts.max_pix = fse::kClassPix[k];
+        b.perm = ctx->d_perm;
+        b.range = range + 2 * k;
+        b.queue = queues + k;
+        b.warps_per_cta = class_warps(ctx, a, user_wpc, k);
+        e = fse::launch_estimator(b, s);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "size-class launch");
+    }
+    return FSE_OK;
+}
+
+// Identity of a ragged call for the graph cache.
+struct RaggedKey {
+    const void* pix;
+    const float* scale;
+    const fse_stamp* idx;
+    const float* inv_var;
+    fse_result* out;
+    const int32_t* perm;
+    int64_t count;
+    int dtype;
+    unsigned tune_version;
+    fse_opts opts;
+};
+static_assert(sizeof(RaggedKey) <= 256, "graph key");
+
+void make_key(const fse_ctx* ctx, const fse::LaunchArgs& a, const fse_opts& o, RaggedKey* k) {
+    memset(k, 0, sizeof *k);
+    k->pix = a.pix;
+    k->scale = a.scale;
+    k->idx = a.idx;
+    k->inv_var = a.inv_var;
+    k->out = a.out;
+    k->perm = ctx->d_perm;
+    k->count = a.count;
+    k->dtype = a.dtype;
+    k->tune_version = ctx->tune_version;
+    k->opts = o;
+}
+
 // Allocation-free form of fse_fit_batch (fse_fit_batch_static).  Some callers
 // cannot allocate device memory at the point of the call: a service that must
 // keep its footprint fixed after start-up, code running under a caching
@@ -252,7 +343,8 @@ int fse_create(fse_ctx** out, int device) {
         return FSE_ENOMEM;
     }
     if (cudaMemset(ctx->d_err, 0, sizeof(unsigned int)) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         fse_destroy(ctx);
         return FSE_ECUDA;
@@ -286,7 +378,11 @@ void fse_destroy(fse_ctx* ctx) {
         cudaFree(ctx->d_out);
         cudaFree(ctx->d_scale);
         cudaFree(ctx->d_ivar);
+        cudaFree(ctx->d_perm);
+        cudaFree(ctx->d_cls);
+        if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
         if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+        if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
         cudaGetLastError();
     }
     delete ctx;
@@ -448,6 +544,122 @@ int fse_fit_batch_host(fse_ctx* ctx, const void* pix, int64_t npix_total, int dt
     if (flag) {
         cudaMemset(ctx->d_err, 0, sizeof(unsigned int));
         return set_error(ctx, FSE_ETIMEOUT, "a bounded device wait expired");
+    }
+    return FSE_OK;
+}
+
+int fse_fit_batch_ragged(fse_ctx* ctx, const void* pix, int dtype, const float* scale,
+                         const fse_stamp* idx, int64_t count, const float* inv_var,
+                         const fse_opts* opts, fse_result* out, void* stream) {
+    if (!ctx) return FSE_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return set_error(ctx, FSE_ECUDA, "cannot select device %d", ctx->device);
+    fse_opts o;
+    if (opts) o = *opts; else fse_opts_default(&o);
+    fse::LaunchArgs a;
+    int rc = prepare(ctx, pix, dtype, scale, idx, count, inv_var, &o, out, fse::kStageAll, &a);
+    if (rc || count == 0) return rc;
+    if ((rc = ragged_workspace(ctx, count))) return rc;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!(o.flags & FSE_FLAG_GRAPH)) return enqueue_ragged(ctx, a, o.warps_per_cta, s);
+    RaggedKey key;
+    make_key(ctx, a, o, &key);
+    if (!ctx->gexec || memcmp(&key, ctx->gkey, sizeof key) != 0) {
+        if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture");
+        rc = enqueue_ragged(ctx, a, o.warps_per_cta, ctx->cap_stream);
+        e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture");
+        e = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            ctx->gexec = nullptr;
+            return cuda_fail(ctx, e, "graph instantiation");
+        }
+        memcpy(ctx->gkey, &key, sizeof key);
+    }
+    cudaError_t e = cudaGraphLaunch(ctx->gexec, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "graph launch");
+    return FSE_OK;
+}
+
+int fse_autotune(fse_ctx* ctx, const void* pix, int dtype, const float* scale,
+                 const fse_stamp* idx, int64_t count, const float* inv_var, const fse_opts* opts,
+                 fse_result* out, void* stream) {
+    if (!ctx) return FSE_EINVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return set_error(ctx, FSE_ECUDA, "cannot select device %d", ctx->device);
+    fse_opts o;
+    if (opts) o = *opts; else fse_opts_default(&o);
+    fse::LaunchArgs a;
+    int rc = prepare(ctx, pix, dtype, scale, idx, count, inv_var, &o, out, fse::kStageAll, &a);
+    if (rc || count == 0) return rc;
+    if ((rc = ragged_workspace(ctx, count))) return rc;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned int* counts = ctx->d_cls;
+    unsigned int* range = counts + kK;
+    unsigned int* cursor = range + 2 * kK;
+    unsigned int* queues = cursor + kK;
+    cudaError_t e = cudaMemsetAsync(counts, 0, kK * sizeof(unsigned int), s);
+    if (e == cudaSuccess) e = fse::classify_stamps(a.idx, a.count, counts, range, cursor, ctx->d_perm, s);
+    unsigned int hc[kK] = {0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc, counts, sizeof hc, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "size classification");
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    const int dt = dtype == FSE_BF16, iv = inv_var != nullptr;
+    for (int k = 0; k < kK && e == cudaSuccess; ++k) {
+        if (hc[k] == 0) continue;
+        const size_t spw = fse::smem_per_warp_iv(fse::kClassPix[k], iv != 0);
+        float best = 1e30f;
+        int best_w = 0;
+        for (int wpc = 1; wpc <= 8 && e == cudaSuccess; wpc *= 2) {
+            if (spw * wpc > 227 * 1024) break;
+            float t_min = 1e30f;
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+                fse::LaunchArgs b = a;
+                b.opts.max_pix = fse::kClassPix[k];
+                b.perm = ctx->d_perm;
+                b.range = range + 2 * k;
+                b.queue = queues + k;
+                b.warps_per_cta = wpc;
+                e = cudaMemsetAsync(queues + k, 0, sizeof(unsigned int), s);
+                if (e == cudaSuccess) e = cudaEventRecord(ev0, s);
+                if (e == cudaSuccess) e = fse::launch_estimator(b, s);
+                if (e == cudaSuccess) e = cudaEventRecord(ev1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
+                if (e == cudaSuccess && ms < t_min) t_min = ms;
+            }
+            if (t_min < best) {
+                best = t_min;
+                best_w = wpc;
+            }
+        }
+        if (best_w > 0) ctx->tuned[dt][iv][k] = best_w;
+    }
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune launch");
+    ++ctx->tune_version;
+    return FSE_OK;
+}
+
+int fse_tuned_warps(const fse_ctx* ctx, int dtype, int has_inv_var, int32_t* warps) {
+    if (!ctx || !warps || (dtype != FSE_F32 && dtype != FSE_BF16)) return FSE_EINVAL;
+    for (int k = 0; k < kK; ++k) {
+        const int t = ctx->tuned[dtype == FSE_BF16][has_inv_var != 0][k];
+        warps[k] = t > 0 ? t : default_warps(fse::kClassPix[k]);
     }
     return FSE_OK;
 }

@@ -43,7 +43,25 @@ struct LaunchArgs {
     int warps_per_cta;
     int num_ctas;            // 0 = library choice
     int static_assign;       // 1: warp w of the grid takes stamp w only (no counter)
+    // Size-class launches of the ragged path: the launch takes the stamps
+    // perm[range[0] .. range[0] + range[1]) (range in device memory, written by
+    // the classification kernels earlier on the stream).  NULL: stamps 0..count.
+    const int32_t* perm;
+    const unsigned int* range;
 };
+
+// Size classes of the ragged path: class k holds the stamps with
+// kClassPix[k-1] < h*w <= kClassPix[k] (stamps of invalid size go to class 0,
+// where the kernel flags them without reading pixels).
+constexpr int kClasses = 7;
+constexpr int kClassPix[kClasses] = {16 * 16, 24 * 24, 32 * 32, 48 * 48, 64 * 64, 96 * 96, 128 * 128};
+
+// Buckets count stamps into the size classes: counts/range/cursor are device
+// arrays of kClasses, kClasses x 2 and kClasses unsigned ints; perm gets count
+// stamp ids grouped by class.  counts must be zero on entry.
+cudaError_t classify_stamps(const fse_stamp* idx, int64_t count, unsigned int* counts,
+                            unsigned int* range, unsigned int* cursor, int32_t* perm,
+                            cudaStream_t stream);
 
 // Arguments of the chi^2 / adjoint kernel (fse_sersic_chi2_grad).
 struct GradArgs {
@@ -76,6 +94,8 @@ cudaError_t launch_estimator(const LaunchArgs& a, cudaStream_t stream);
 cudaError_t launch_chi2_grad(const GradArgs& a, cudaStream_t stream);
 // Shared memory a warp needs for stamps of up to max_pix pixels.
 size_t smem_per_warp(int max_pix);
+// The same with the per-pixel inverse-variance tile when ivar is set.
+size_t smem_per_warp_iv(int max_pix, bool ivar);
 // Largest warps-per-CTA / CTAs-per-SM choice for a tile size.
 void choose_launch(int max_pix, int* warps_per_cta, int* ctas_per_sm);
 

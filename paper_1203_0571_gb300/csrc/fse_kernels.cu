@@ -1331,6 +1331,9 @@ __global__ void __launch_bounds__(256, 1) estimator_kernel(LaunchArgs a) {
     __syncwarp();
     uint32_t phase = 0;
     const DevOpts& o = a.opts;
+    // this launch's stamps: all of them, or one size class through perm
+    const unsigned long long count = a.range ? a.range[1] : static_cast<unsigned long long>(a.count);
+    const unsigned base = a.range ? a.range[0] : 0u;
 
     for (int round = 0;; ++round) {
         unsigned sidx = 0;
@@ -1342,8 +1345,8 @@ __global__ void __launch_bounds__(256, 1) estimator_kernel(LaunchArgs a) {
             if (lane == 0) sidx = atomicAdd(a.queue, 1u);
             sidx = __shfl_sync(kFull, sidx, 0);
         }
-        if (sidx >= static_cast<unsigned long long>(a.count)) break;
-        const int64_t si = static_cast<int64_t>(sidx);
+        if (sidx >= count) break;
+        const int64_t si = a.perm ? static_cast<int64_t>(a.perm[base + sidx]) : static_cast<int64_t>(sidx);
         const fse_stamp ix = a.idx[si];
         const int h = ix.h, w = ix.w;
         const long long npl = static_cast<long long>(h) * w;
@@ -1679,6 +1682,7 @@ cudaError_t launch_stage(const LaunchArgs& a, cudaStream_t stream) {
 
 // ------------------------------------------------------------------ host wrappers
 size_t smem_per_warp(int max_pix) { return warp_bytes(max_pix, false); }
+size_t smem_per_warp_iv(int max_pix, bool ivar) { return warp_bytes(max_pix, ivar); }
 
 void choose_launch(int max_pix, int* warps_per_cta, int* ctas_per_sm) {
     const size_t spw = warp_bytes(max_pix, false);
