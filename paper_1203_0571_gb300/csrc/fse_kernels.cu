@@ -973,9 +973,16 @@ __device__ void fit_start(const float* __restrict__ s, const float* __restrict__
 // sum r^2 accumulated in double-float, then one Gauss-Newton step of the
 // reduced problem and chi^2 from its quadratic model.  The fp32 LM stops
 // within the noise of its own sums; this pass removes most of that noise.
-struct Refined {
-    double I0, re, n, chi2;
-    bool applied;
+// A precise evaluation of the profiled problem at (r_e, n): chi^2 at I0*, the
+// Newton step for (r_e, n) (Gauss-Newton where the full Hessian is not
+// positive definite), and what a step predicts.
+struct Precise {
+    double chi2;      // exact chi^2 at (I0*, r_e, n)
+    double chi2_step; // chi^2 the quadratic model predicts after the full step
+    float I0;         // I0* (Eq. 13 at this point)
+    float d0, d1;     // Newton step for r_e, n (valid when ok)
+    float c0, c1;     // dI0 = c0 d0 + c1 d1 along a step (Eq. 13 to first order)
+    bool ok;
 };
 
 // Model values above this many noise sigmas carry an fp32 rounding (6e-8 of the
@@ -996,10 +1003,87 @@ __device__ __noinline__ double bright_r2(const BrightModel& bm, double t1, doubl
     return r * r;
 }
 
+// The scalar part of a refinement pass in precision R, from the
+// double-float sums of the pass: I0* and chi^2 at I0*, then the Newton system
+// over (r_e, n) with I0 profiled out (Schur complement).
+template <typename R>
+__device__ Precise refine_tail(const float (&rh)[10], const float (&rl)[10], const float (&T)[4],
+                               double chi2_rr, float I0g, float re_f, float n_f, float bf, float dbf,
+                               float d2bf) {
+    R S[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) S[i] = static_cast<R>(rh[i]) + static_cast<R>(rl[i]);
+    const R sEE = S[0], sEv = S[1], sEva = S[2], svv = S[3], svva = S[4], svaa = S[5];
+    const R sEr = S[6], svr = S[7], svar = S[8];
+    const R re = re_f, n = n_f, b = bf, db = dbf, d2b = d2bf;
+    const R inv_n = R(1) / n;
+    const R ln2 = static_cast<R>(kLn2);
+    Precise o;
+    const R d = -sEr / sEE;
+    const R I0 = static_cast<R>(I0g) + d;
+    // chi^2 at I0*: sum r^2 + d sum E r, with sum r^2 kept as a float pair
+    o.chi2 = chi2_rr + static_cast<double>(d) * static_cast<double>(sEr);
+    o.I0 = static_cast<float>(I0);
+    const R k2 = I0 * b / (n * re);
+    const R kA = I0 * b * ln2 * inv_n * inv_n;
+    const R kB = I0 * db;
+    const R svr_s = svr + d * sEv, svar_s = svar + d * sEva;
+    const R Cvv = svv - sEv * sEv / sEE;
+    const R Cvva = svva - sEv * sEva / sEE;
+    const R Cvaa = svaa - sEva * sEva / sEE;
+    // gradient of chi^2/2 over (r_e, n) at I0*
+    const R g0 = k2 * svr_s, g1 = kA * svar_s - kB * svr_s;
+    // Gauss-Newton part of the reduced Hessian (J^T J with I0 profiled out)
+    R H00 = k2 * k2 * Cvv, H01 = k2 * (kA * Cvva - kB * Cvv);
+    R H11 = kA * kA * Cvaa - R(2) * kA * kB * Cvva + kB * kB * Cvv;
+    // J^T J couplings of I0 with r_e and n
+    R JI0 = k2 * sEv, JI1 = kA * sEva - kB * sEv;
+    {
+        // Newton: add sum r d^2 m.  With phi = b u and E = exp(-phi),
+        // d^2 E = E (dphi_i dphi_j - d^2 phi_ij); the derivatives of u = (r/r_e)^(1/n)
+        // give the six residual sums r E u {1, a, a^2} and r E u^2 {1, a, a^2}
+        // (a = log2(r/r_e)).  Where the residuals are large, dropping this term
+        // leaves a Gauss-Newton iteration that converges slowly or not at all.
+        const R c = inv_n / re;
+        const R in2 = inv_n * inv_n;
+        const R T0 = T[0], T1r = T[1], T2r = T[2], T3 = T[3];
+        const R Srr = b * c * c * (b * T1r - (R(1) + n) * svr);
+        const R Srn = c * (-b * db * T1r + b * b * ln2 * in2 * T2r + db * svr - b * ln2 * in2 * svar -
+                           b * inv_n * svr);
+        const R Snn = db * db * T1r - R(2) * b * db * ln2 * in2 * T2r + b * b * ln2 * ln2 * in2 * in2 * T3 -
+                      d2b * svr + R(2) * db * ln2 * in2 * svar - b * ln2 * ln2 * in2 * in2 * T0 -
+                      R(2) * b * ln2 * in2 * inv_n * svar;
+        // the I0 rows gain g/I0 (sum r dE), which also enters the Schur complement
+        const R q0 = g0 / I0, q1 = g1 / I0;
+        const R N00 = H00 + I0 * Srr - (R(2) * JI0 * q0 + q0 * q0) / sEE;
+        const R N01 = H01 + I0 * Srn - (JI0 * q1 + JI1 * q0 + q0 * q1) / sEE;
+        const R N11 = H11 + I0 * Snn - (R(2) * JI1 * q1 + q1 * q1) / sEE;
+        // keep Gauss-Newton where the full Hessian is not positive definite
+        if (N00 > R(0) && N00 * N11 - N01 * N01 > R(0) && isfinite(N00 * N11)) {
+            H00 = N00;
+            H01 = N01;
+            H11 = N11;
+            JI0 += q0;
+            JI1 += q1;
+        }
+    }
+    const R det = H00 * H11 - H01 * H01;
+    const R d0 = (-H11 * g0 + H01 * g1) / det;
+    const R d1 = (H01 * g0 - H00 * g1) / det;
+    o.ok = det > R(0) && isfinite(det) && isfinite(o.chi2) && isfinite(d0) && isfinite(d1);
+    o.d0 = static_cast<float>(d0);
+    o.d1 = static_cast<float>(d1);
+    o.c0 = static_cast<float>(-JI0 / sEE);
+    o.c1 = static_cast<float>(-JI1 / sEE);
+    o.chi2_step = o.chi2 + static_cast<double>(R(2) * (g0 * d0 + g1 * d1) + d0 * (H00 * d0 + H01 * d1) +
+                                               d1 * (H01 * d0 + H11 * d1));
+    return o;
+}
+
 template <bool IVAR>
-__device__ Refined fit_refine(const float* __restrict__ s, const float* __restrict__ L,
+__device__ Precise fit_refine(const float* __restrict__ s, const float* __restrict__ L,
                               const float* __restrict__ sq, int w, int npix, int lane, float I0g,
-                              float re, float n, float lq, const MomState& st, bool final_pass) {
+                              float re, float n, float lq, const MomState& st) {
     float bf, dbf;
     bn_eval_f(n, &bf, &dbf);
     const float inv_n = 1.f / n;
@@ -1007,7 +1091,7 @@ __device__ Refined fit_refine(const float* __restrict__ s, const float* __restri
     const float c0 = log2f(re) + lq;
     // fp64 model constants for the bright pixels of the final pass; a model
     // value exceeds the threshold only if |I0| does (E <= 1)
-    const bool check_bright = final_pass && (IVAR || fabsf(I0g) > kBrightSigma);
+    const bool check_bright = IVAR || fabsf(I0g) > kBrightSigma;
     BrightModel bm;
     if (check_bright) {
         double dbd;
@@ -1076,88 +1160,16 @@ __device__ Refined fit_refine(const float* __restrict__ s, const float* __restri
     warp_allsum_df(rh, rl);
     warp_allsum(T);
     // The sums are exact to about 1e-14 relative; the quantities that vanish at
-    // the optimum (the gradient) are formed from them in fp32 only after the
+    // the optimum (the gradient) are formed from them only after the
     // cancellation has happened inside the double-float sums.
-    float S[10];
-#pragma unroll
-    for (int i = 0; i < 10; ++i) S[i] = rh[i] + rl[i];
-    const float sEE = S[0], sEv = S[1], sEva = S[2], svv = S[3], svva = S[4], svaa = S[5];
-    const float sEr = S[6], svr = S[7], svar = S[8];
-    Refined o;
-    const float d = -sEr / sEE;
-    const float I0 = I0g + d;
-    // chi^2 at I0*: sum r^2 + d sum E r, with sum r^2 kept as a float pair
-    const double chi2 = (static_cast<double>(rh[9]) + rl[9]) + static_cast<double>(d) * sEr;
-    const float k2 = I0 * bf / (n * re);
-    const float kA = I0 * bf * static_cast<float>(kLn2) * inv_n * inv_n;
-    const float kB = I0 * dbf;
-    const float svr_s = fmaf(d, sEv, svr), svar_s = fmaf(d, sEva, svar);
-    const float Cvv = svv - sEv * sEv / sEE;
-    const float Cvva = svva - sEv * sEva / sEE;
-    const float Cvaa = svaa - sEva * sEva / sEE;
-    // gradient of chi^2/2 over (r_e, n) at I0*
-    const float g0 = k2 * svr_s, g1 = kA * svar_s - kB * svr_s;
-    // Gauss-Newton part of the reduced Hessian (J^T J with I0 profiled out)
-    float H00 = k2 * k2 * Cvv, H01 = k2 * (kA * Cvva - kB * Cvv);
-    float H11 = kA * kA * Cvaa - 2.f * kA * kB * Cvva + kB * kB * Cvv;
-    // J^T J couplings of I0 with r_e and n
-    float JI0 = k2 * sEv, JI1 = kA * sEva - kB * sEv;
-    {
-        // Newton: add sum r d^2 m.  With phi = b u and E = exp(-phi),
-        // d^2 E = E (dphi_i dphi_j - d^2 phi_ij); the derivatives of u = (r/r_e)^(1/n)
-        // give the six residual sums r E u {1, a, a^2} and r E u^2 {1, a, a^2}
-        // (a = log2(r/r_e)).  Where the residuals are large, dropping this term
-        // leaves a Gauss-Newton iteration that converges slowly or not at all.
-        const float d2b = bn_d2_f(n);
-        const float ln2 = static_cast<float>(kLn2);
-        const float c = inv_n / re;
-        const float in2 = inv_n * inv_n;
-        const float T1 = svr, T2 = svar;
-        const float Srr = bf * c * c * (bf * T[1] - (1.f + n) * T1);
-        const float Srn = c * (-bf * dbf * T[1] + bf * bf * ln2 * in2 * T[2] + dbf * T1 -
-                               bf * ln2 * in2 * T2 - bf * inv_n * T1);
-        const float Snn = dbf * dbf * T[1] - 2.f * bf * dbf * ln2 * in2 * T[2] +
-                          bf * bf * ln2 * ln2 * in2 * in2 * T[3] - d2b * T1 +
-                          2.f * dbf * ln2 * in2 * T2 - bf * ln2 * ln2 * in2 * in2 * T[0] -
-                          2.f * bf * ln2 * in2 * inv_n * T2;
-        // the I0 rows gain g/I0 (sum r dE), which also enters the Schur complement
-        const float q0 = g0 / I0, q1 = g1 / I0;
-        const float N00 = H00 + I0 * Srr - (2.f * JI0 * q0 + q0 * q0) / sEE;
-        const float N01 = H01 + I0 * Srn - (JI0 * q1 + JI1 * q0 + q0 * q1) / sEE;
-        const float N11 = H11 + I0 * Snn - (2.f * JI1 * q1 + q1 * q1) / sEE;
-        // keep Gauss-Newton where the full Hessian is not positive definite
-        if (N00 > 0.f && N00 * N11 - N01 * N01 > 0.f && isfinite(N00 * N11)) {
-            H00 = N00;
-            H01 = N01;
-            H11 = N11;
-            JI0 += q0;
-            JI1 += q1;
-        }
-    }
-    const float det = H00 * H11 - H01 * H01;
-    o.I0 = I0;
-    o.re = re;
-    o.n = n;
-    o.chi2 = chi2;
-    o.applied = false;
-    if (det > 0.f && isfinite(det) && isfinite(chi2)) {
-        const float d0 = (-H11 * g0 + H01 * g1) / det;
-        const float d1 = (H01 * g0 - H00 * g1) / det;
-        if (fabsf(d0) <= 1e-2f * re && fabsf(d1) <= 1e-2f * n) {
-            // I0 follows Eq. 13 to first order along the step
-            const float dI0 = -(JI0 * d0 + JI1 * d1) / sEE;
-            o.re = static_cast<double>(re) + d0;
-            o.n = static_cast<double>(n) + d1;
-            o.I0 = static_cast<double>(I0) + dI0;
-            o.chi2 = chi2 + static_cast<double>(2.f * (g0 * d0 + g1 * d1) + d0 * (H00 * d0 + H01 * d1) +
-                                                d1 * (H01 * d0 + H11 * d1));
-            o.applied = true;
-        }
-    }
-    return o;
+    const double chi2_rr = static_cast<double>(rh[9]) + rl[9];
+    return refine_tail<float>(rh, rl, T, chi2_rr, I0g, re, n, bf, dbf, bn_d2_f(n));
 }
 
-constexpr float kFitRefineSkip = 1e-5f;
+constexpr float kFitRefineSkip = 1e-5f;   // a Newton step below this ends the refinement
+constexpr float kFitRefineCap = 0.2f;     // largest relative step of one refinement pass
+constexpr float kFitRefineTrusted = 1e-2f; // steps up to this are taken without a chi^2 test
+constexpr int kFitRefineMax = 16;         // refinement passes at most
 
 struct FitOut {
     float I0, re, n, flux;
@@ -1274,32 +1286,77 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
         ret = qre;
         nt = qn;
     }
-    if (converged && isfinite(cur.chi2)) status |= FSE_ST_FIT_CONVERGED;
-    else if (finite0 && it > o.max_iter_fit) status |= FSE_ST_FIT_MAXITER;
     FitOut out;
     out.I0 = cur.I0;
     out.re = re;
     out.n = n;
     out.chi2 = cur.chi2;
-    if (converged && isfinite(cur.chi2) && re > re_min && re < re_max && n > n_min && n < n_max) {
-        // Newton refinement passes.  The error left after one is about the
-        // square of its step, and its chi^2 (exact at the start point plus the
-        // quadratic model of the step) is then exact to third order in the
-        // step; a second pass runs unless the first step was below 1e-5.
+    bool refined = false;
+    if (isfinite(cur.chi2) && re > re_min && re < re_max && n > n_min && n < n_max) {
+        // Newton refinement on exact chi^2 (double-float sums): the error left
+        // after a step is about the square of the step, so a step below 1e-5
+        // ends it, applied with chi^2 from the quadratic model (exact to third
+        // order in the step).  Steps up to 1e-2 are taken as they are; larger
+        // ones are capped at 20 % of each parameter and taken only if the
+        // exact chi^2 does not rise, else retried at a quarter of the length.  This also finishes fits that the
+        // fp32 iteration left early in a flat valley, where chi^2 changes below
+        // its fp32 resolution.
+        // one call site (the pixel pass is large): each round evaluates the
+        // next point, then accepts or rejects it against the best so far
+        Precise P;
+        P.ok = false;
+        float te = re, tn = n, tI0 = cur.I0;   // the point to evaluate next
+        float step_last = 0.f;                  // relative length of the step to it
+        float shrink = 1.f;
+        int passes = 0;
 #pragma unroll 1
-        for (int r = 0; r < 2; ++r) {
-            const Refined rf = fit_refine<IVAR>(s, L, sq, w, npix, lane, out.I0, out.re, out.n, lq,
-                                                st, true);
-            const float step = fmaxf(fabsf(static_cast<float>(rf.re) / out.re - 1.f),
-                                     fabsf(static_cast<float>(rf.n) / out.n - 1.f));
-            out.I0 = static_cast<float>(rf.I0);
-            out.re = static_cast<float>(rf.re);
-            out.n = static_cast<float>(rf.n);
-            out.chi2 = rf.chi2;
-            if (r == 1) status |= FSE_ST_FIT_REFINE2;
-            if (!rf.applied || step <= kFitRefineSkip) break;
+        for (;;) {
+            const Precise E = fit_refine<IVAR>(s, L, sq, w, npix, lane, tI0, te, tn, lq, st);
+            ++passes;
+            // a step within 1e-2 is taken on the Newton model alone: its chi^2
+            // decrease can be below the rounding of the fp32 model values
+            const bool accept = passes == 1 || (E.ok && (step_last <= kFitRefineTrusted || E.chi2 <= P.chi2));
+            if (accept) {
+                P = E;
+                re = te;
+                n = tn;
+                shrink = 1.f;
+            } else {
+                shrink *= 0.25f;
+                if (shrink < 1e-3f) break;
+            }
+            if (!P.ok) break;
+            const float rel = fmaxf(fabsf(P.d0) / re, fabsf(P.d1) / n);
+            if (rel <= kFitRefineSkip) {
+                out.re = re + P.d0;
+                out.n = n + P.d1;
+                out.I0 = P.I0 + P.c0 * P.d0 + P.c1 * P.d1;
+                out.chi2 = P.chi2_step;
+                refined = true;
+                break;
+            }
+            if (passes >= kFitRefineMax) break;
+            const float f = fminf(1.f, kFitRefineCap / rel) * shrink;
+            te = re + f * P.d0;
+            tn = n + f * P.d1;
+            te = te < re_min ? re_min : (te > re_max ? re_max : te);
+            tn = tn < n_min ? n_min : (tn > n_max ? n_max : tn);
+            tI0 = P.I0 + P.c0 * (te - re) + P.c1 * (tn - n);
+            step_last = f * rel;
         }
+        if (!refined) {
+            // no step small enough to end on: keep the best point evaluated
+            out.re = re;
+            out.n = n;
+            if (isfinite(P.chi2)) {
+                out.I0 = P.I0;
+                out.chi2 = P.chi2;
+            }
+        }
+        if (passes > 1) status |= FSE_ST_FIT_REFINE2;
     }
+    if ((converged || refined) && isfinite(out.chi2)) status |= FSE_ST_FIT_CONVERGED;
+    else if (finite0 && it > o.max_iter_fit) status |= FSE_ST_FIT_MAXITER;
     if (out.re <= re_min || out.re >= re_max || out.n <= n_min || out.n >= n_max)
         status |= FSE_ST_FIT_BOUND;
     if (!(out.I0 > 0.f)) status |= FSE_ST_NONPOS_FLUX;
@@ -1314,7 +1371,9 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
 
 // ------------------------------------------------------------------ kernel
 template <int STAGE, int DT, bool IVAR>
-__global__ void __launch_bounds__(256, 1) estimator_kernel(LaunchArgs a) {
+// 168 registers per thread let three CTAs of four warps share an SM (the
+// launch shape of 48x48 and smaller tiles); more would leave two.
+__global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
