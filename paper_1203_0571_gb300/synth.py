@@ -278,6 +278,24 @@ def encode_bf16(batch: StampBatch) -> StampBatch:
     dev = batch.pix.device
     scale = torch.empty(N, dtype=torch.float32, device=dev)
     out = torch.empty(batch.pix.numel(), dtype=torch.bfloat16, device=dev)
+    offs = batch.offset.to("cpu").numpy()
+    area = (batch.h.to(torch.int64) * batch.w.to(torch.int64)).to("cpu").numpy()
+    if N and np.array_equal(offs[1:], offs[:-1] + area[:-1]):
+        # stamps back to back: per-stamp maxima over chunks of about 2^24 pixels
+        i0 = 0
+        while i0 < N:
+            i1 = int(np.searchsorted(offs, offs[i0] + (1 << 24), side="left"))
+            i1 = max(i1, i0 + 1)
+            a = torch.as_tensor(area[i0:i1], device=dev)
+            o0, o1 = int(offs[i0]), int(offs[i1 - 1] + area[i1 - 1])
+            seg = batch.pix[o0:o1]
+            sid = torch.repeat_interleave(torch.arange(i1 - i0, device=dev), a)
+            mx = torch.zeros(i1 - i0, dtype=torch.float32, device=dev)
+            mx = mx.scatter_reduce(0, sid, seg.abs(), reduce="amax", include_self=True).clamp(min=1e-30)
+            scale[i0:i1] = mx
+            out[o0:o1] = (seg / mx[sid]).to(torch.bfloat16)
+            i0 = i1
+        return dataclasses.replace(batch, pix=out, scale=scale)
     for i in range(N):
         o, a = int(batch.offset[i]), int(batch.h[i]) * int(batch.w[i])
         seg = batch.pix[o:o + a]
