@@ -208,7 +208,7 @@ def _render(side: int, p: dict, sel: np.ndarray, ids: np.ndarray, seed: int,
     g1, g2 = gabs * torch.cos(2 * phi), gabs * torch.sin(2 * phi)
     c = (side - 1) / 2.0
     xc, yc = c + t(p["dx"]), c + t(p["dy"])
-    b = t(sersic_b(p["n"]))
+    b = torch.as_tensor(sersic_b(p["n"][sel]), **f64).view(k, 1, 1)
     yy, xx = torch.meshgrid(torch.arange(side, **f64), torch.arange(side, **f64), indexing="ij")
     d1, d2 = xx - xc, yy - yc
     R2 = ((1 - g1) ** 2 + g2 ** 2) * d1 * d1 + ((1 + g1) ** 2 + g2 ** 2) * d2 * d2 - 4 * g2 * d1 * d2
