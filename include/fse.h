@@ -102,8 +102,10 @@ typedef struct {
     double  tol_fit;        /* fit stops when max relative (r_e, n) step <= tol_fit (1e-6) */
     int32_t max_iter_mom;   /* moment iterations                              (60)      */
     int32_t max_iter_fit;   /* fit iterations                                 (60)      */
-    double  k_gain;         /* centroid gain k of Sec. 2 (0.75); 0 = k determined from
-                               the current moments at every step (Newton step)       */
+    double  k_gain;         /* centroid gain k of Sec. 2.  0 (default): k determined
+                               from the current moments (a Newton step) near the fixed
+                               point, 0.75 elsewhere; > 0: that fixed gain (the paper's
+                               0.75).  The fixed point does not depend on k.    (0)     */
     int32_t sigw_mode;      /* 1: sigma_w = r50/sqrt(2 ln 2) fixed; 0: matched-weight
                                rule sigma_w^2 = sum I W R^2 / sum I W (Sec. 4.2.1)  (1)  */
     int32_t max_pix;        /* upper bound of h*w over the batch; sets the shared-memory

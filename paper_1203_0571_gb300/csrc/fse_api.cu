@@ -312,7 +312,7 @@ void fse_opts_default(fse_opts* o) {
     o->tol_fit = 1e-6;
     o->max_iter_mom = 60;
     o->max_iter_fit = 60;
-    o->k_gain = 0.75;
+    o->k_gain = 0.0;
     o->sigw_mode = 1;
     o->max_pix = 0;
     o->n_min = 0.2;

@@ -458,22 +458,37 @@ __device__ __forceinline__ MomStep moment_step(const float (&m)[11], const MomSt
     const float A = 1.f + gg - 2.f * g1, B = 1.f + gg + 2.f * g1;
     if (!(S0 > 0.f)) return r;
     const float c = 1.f / (2.f * st.sw * st.sw);
-    if (k_gain > 0.f) {
-        // Eqs. 5-6 with the fixed gain k
-        r.dx = m[1] / (k_gain * S0);
-        r.dy = m[2] / (k_gain * S0);
-    } else {
+    // Eqs. 5-6 with the fixed gain k (k_gain, or 0.75 where the determined
+    // gain below is not usable)
+    const float kf = k_gain > 0.f ? k_gain : 0.75f;
+    r.dx = m[1] / (kf * S0);
+    r.dy = m[2] / (kf * S0);
+    if (k_gain <= 0.f) {
         // k determined from the current moments: the derivative of
         // (sum I W theta_1, sum I W theta_2) with respect to the centre, which
-        // for a Gaussian profile is k = s_w^2 / (s^2 + s_w^2) (Sec. 2)
+        // for a Gaussian profile is k = s_w^2 / (s^2 + s_w^2) (Sec. 2).  It is
+        // used near the fixed point only (fixed-gain step below 0.25 px, where
+        // the linearisation holds), when the Jacobian is positive definite and
+        // the gain it implies, |M1| / (S0 |step|), lies in [0.15, 1.5], and
+        // the weight is wider than 0.6 px: far from the fixed point a noisy
+        // first moment with a small gain jumps out of the stamp, and a weight
+        // about as narrow as a pixel (sigma_w clamped at 0.5) makes the
+        // moments pixelated and the derivative meaningless.
         const float J11 = 2.f * c * (A * Q11 - 2.f * g2 * Q12) - S0;
         const float J12 = 2.f * c * (B * Q12 - 2.f * g2 * Q11);
         const float J21 = 2.f * c * (A * Q12 - 2.f * g2 * Q22);
         const float J22 = 2.f * c * (B * Q22 - 2.f * g2 * Q12) - S0;
         const float dj = J11 * J22 - J12 * J21;
-        if (!(dj > 0.f)) return r;
-        r.dx = -(J22 * m[1] - J12 * m[2]) / dj;
-        r.dy = -(-J21 * m[1] + J11 * m[2]) / dj;
+        const float nx = -(J22 * m[1] - J12 * m[2]) / dj;
+        const float ny = -(-J21 * m[1] + J11 * m[2]) / dj;
+        const float num = sqrtf(m[1] * m[1] + m[2] * m[2]);
+        const float den = S0 * sqrtf(nx * nx + ny * ny);
+        const bool near = fmaxf(fabsf(r.dx), fabsf(r.dy)) < 0.25f && st.sw > 0.6f;
+        if (near && dj > 0.f && isfinite(nx) && isfinite(ny) &&
+            (den == 0.f || (num >= 0.15f * den && num <= 1.5f * den))) {
+            r.dx = nx;
+            r.dy = ny;
+        }
     }
     const float SR2 = A * Q11 + B * Q22 - 4.f * g2 * Q12;      // sum f W R^2
     r.sw_new = SR2 > 0.f ? sqrtf(SR2 / S0) : 0.f;
@@ -658,11 +673,19 @@ __device__ int moment_iterate(const float* s, __half2* C, int h, int w, int npix
     store_offsets(C, w, npix, lane, st.xr, st.yr);
     const float sw_max = 0.5f * static_cast<float>(h < w ? h : w);
     float prev = 0.f;   // size of the previous step, for the contraction estimate
+    // with the determined gain (k_gain = 0): a centre step that does not shrink
+    // switches the rest of the iteration to the fixed gain
+    float k_use = o.k_gain, prev_c = 0.f;
     int it;
     for (it = 1; it <= o.max_iter_mom; ++it) {
         float m[11];
         moment_pass(s, C, npix, lane, st, m);
-        const MomStep d = moment_step(m, st, o.k_gain, ellip);
+        const MomStep d = moment_step(m, st, k_use, ellip);
+        if (k_use <= 0.f) {
+            const float dc = fmaxf(fabsf(d.dx), fabsf(d.dy));
+            if (it > 2 && dc >= prev_c) k_use = 0.75f;
+            prev_c = dc;
+        }
         if (!d.ok) {
             status |= FSE_ST_MOM_FAILED;
             break;

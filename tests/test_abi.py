@@ -62,7 +62,7 @@ def test_struct_layout_matches_c(tmp_path):
 def test_opts_defaults(lib):
     o = binding.default_opts()
     assert o.size == ctypes.sizeof(binding.Opts)
-    assert o.k_gain == 0.75 and o.sigw_mode == 1 and o.max_pix == 0
+    assert o.k_gain == 0.0 and o.sigw_mode == 1 and o.max_pix == 0
     assert o.n_min == 0.2 and o.n_max == 10.0
 
 

@@ -227,3 +227,18 @@ def test_host_buffers_equal_device(ctx):
     ctx.fit_batch_host(host_pix, host_idx, out=out)
     host = out.numpy().view(B.RESULT_DTYPE).reshape(-1)
     assert host.tobytes() == dev.tobytes()
+
+
+def test_fixed_gain_reaches_the_same_fixed_point(ctx, O):
+    """k = 0.75 (the fixed gain of Sec. 2) and the default determined gain both
+    reach the oracle's fixed point; only the number of passes differs."""
+    batch = synth.make_workload(0)
+    ids = np.arange(batch.count)
+    o = PR.oracle_results(O, batch, ids)
+    g75 = gpu_run(ctx, batch, opts=opts_for(batch, k_gain=0.75))
+    g0 = gpu_run(ctx, batch)
+    for g in (g75, g0):
+        rep = PR.compare(g, o, O=O, batch=batch, ids=ids)
+        assert_gate(rep)
+    both = ((g75["status"] & 1) & (g0["status"] & 1)).astype(bool)
+    assert g0["it_mom"][both].mean() < g75["it_mom"][both].mean()
