@@ -116,6 +116,9 @@ typedef struct {
     double  lm_lambda0;     /* initial Levenberg-Marquardt damping            (1e-3)    */
     uint32_t flags;         /* FSE_FLAG_* bits                                 (0)       */
     int32_t warps_per_cta;  /* launch shape: 0 (library choice), 1, 2, 4 or 8                      */
+    int32_t warps_per_stamp;/* warps sharing one stamp (whole chain only): 0 (library
+                               choice: 1 up to 48x48 tiles, then 2, 4, 8 up to 128x128),
+                               1, 2, 4 or 8; warps_per_cta must be a multiple     (0)  */
 } fse_opts;
 
 /* Per-stamp result (64 bytes). */
@@ -216,9 +219,10 @@ int fse_fit_batch_ragged(fse_ctx *ctx, const void *pix, int dtype, const float *
                          const fse_stamp *idx, int64_t count, const float *inv_var,
                          const fse_opts *opts, fse_result *out, void *stream);
 
-/* Choose warps per CTA (1, 2, 4 or 8, as far as shared memory allows) for
- * each size class of fse_fit_batch_ragged by timing the class launches on
- * this batch (each candidate twice, the faster counts).  The choice is kept
+/* Choose the launch shape of each size class of fse_fit_batch_ragged -- warps
+ * per stamp (1, 2, 4, 8) and stamp groups per CTA, at most 8 warps per CTA and
+ * as far as shared memory allows -- by timing the class launches on this
+ * batch (each candidate twice, the faster counts).  The choice is kept
  * in the context for this dtype and inverse-variance setting and used by
  * later ragged calls.  out receives the batch's results.  Synchronises
  * `stream`.  No counterpart in the paper: a launch-shape search. */
@@ -226,10 +230,12 @@ int fse_autotune(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
                  const fse_stamp *idx, int64_t count, const float *inv_var,
                  const fse_opts *opts, fse_result *out, void *stream);
 
-/* The warps per CTA the ragged path uses for each of the seven size classes
+/* The launch shape the ragged path uses for each of the seven size classes
  * (tuned or default), for a dtype and with (1) or without (0) inverse
- * variance.  warps is a host array of 7. */
-int fse_tuned_warps(const fse_ctx *ctx, int dtype, int has_inv_var, int32_t *warps);
+ * variance: warps per CTA and warps per stamp (host arrays of 7; the second
+ * may be NULL). */
+int fse_tuned_warps(const fse_ctx *ctx, int dtype, int has_inv_var, int32_t *warps_per_cta,
+                    int32_t *warps_per_stamp);
 
 /* Evaluate the device b(n) table (Eq. 10: P(2n, b) = 1/2) and its derivative
  * at count values n[i] in [0.2, 10] (device pointers, doubles).  For tests. */

@@ -44,7 +44,7 @@ class Opts(ctypes.Structure):
                 ("max_pix", ctypes.c_int32), ("n_min", ctypes.c_double), ("n_max", ctypes.c_double),
                 ("re_min", ctypes.c_double), ("re_max_frac", ctypes.c_double),
                 ("lm_lambda0", ctypes.c_double), ("flags", ctypes.c_uint32),
-                ("warps_per_cta", ctypes.c_int32)]
+                ("warps_per_cta", ctypes.c_int32), ("warps_per_stamp", ctypes.c_int32)]
 
 
 RESULT_DTYPE = np.dtype([("x0", "<f4"), ("y0", "<f4"), ("e1", "<f4"), ("e2", "<f4"), ("I0", "<f4"),
@@ -91,7 +91,8 @@ def load(build: bool = True, path: str | None = None) -> ctypes.CDLL:
     L.fse_fit_batch_host.restype = ctypes.c_int
     L.fse_sersic_b.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, _vp]
     L.fse_sersic_b.restype = ctypes.c_int
-    L.fse_tuned_warps.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]
+    L.fse_tuned_warps.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_int32)]
     L.fse_tuned_warps.restype = ctypes.c_int
     L.fse_sersic_chi2_grad.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int64, _vp, _vp,
                                        _vp, _vp, _vp, _vp, _vp]
@@ -229,10 +230,11 @@ class Context:
         return self._dev_call("fse_autotune", pix, index, out, scale, inv_var, opts, stream)
 
     def tuned_warps(self, dtype: int = FSE_F32, inv_var: bool = False) -> list:
-        """fse_tuned_warps: warps per CTA of the seven size classes."""
+        """fse_tuned_warps: (warps per CTA, warps per stamp) of the seven size classes."""
         w = (ctypes.c_int32 * 7)()
-        self._check(load().fse_tuned_warps(self._h, dtype, int(inv_var), w))
-        return list(w)
+        n = (ctypes.c_int32 * 7)()
+        self._check(load().fse_tuned_warps(self._h, dtype, int(inv_var), w, n))
+        return list(zip(w, n))
 
     def fit_batch_host(self, pix: np.ndarray | torch.Tensor, index: np.ndarray | torch.Tensor, *,
                        scale=None, inv_var=None, opts=None, out=None, stream=None) -> np.ndarray:

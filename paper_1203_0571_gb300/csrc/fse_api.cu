@@ -40,6 +40,7 @@ struct fse_ctx {
     // warps per CTA chosen by fse_autotune, by dtype, inverse variance and size
     // class (0 = library default)
     int tuned[2][2][fse::kClasses] = {};
+    int tuned_nw[2][2][fse::kClasses] = {};   // warps per stamp of the tuned shape
     unsigned tune_version = 0;
     // the CUDA graph of the last ragged call made with FSE_FLAG_GRAPH
     cudaStream_t cap_stream = nullptr;
@@ -106,9 +107,13 @@ int check_opts(fse_ctx* ctx, const fse_opts* o) {
         return set_error(ctx, FSE_EINVAL, "n bounds must satisfy %.4f <= n_min < n_max <= %.4f", tab_lo, tab_hi);
     if (!(o->re_min > 0 && o->re_max_frac > 0)) return set_error(ctx, FSE_EINVAL, "r_e bounds must be positive");
     if (!(o->lm_lambda0 > 0)) return set_error(ctx, FSE_EINVAL, "lm_lambda0 must be positive");
-    const int w = o->warps_per_cta;
+    const int w = o->warps_per_cta, ws = o->warps_per_stamp;
     if (!(w == 0 || w == 1 || w == 2 || w == 4 || w == 8))
         return set_error(ctx, FSE_EINVAL, "warps_per_cta must be 0, 1, 2, 4 or 8");
+    if (!(ws == 0 || ws == 1 || ws == 2 || ws == 4 || ws == 8))
+        return set_error(ctx, FSE_EINVAL, "warps_per_stamp must be 0, 1, 2, 4 or 8");
+    if (w > 0 && ws > 0 && w % ws != 0)
+        return set_error(ctx, FSE_EINVAL, "warps_per_cta must be a multiple of warps_per_stamp");
     if (o->flags & ~static_cast<uint32_t>(FSE_FLAG_GRAPH))
         return set_error(ctx, FSE_EINVAL, "unknown bits in flags");
     return FSE_OK;
@@ -133,10 +138,23 @@ fse::DevOpts dev_opts(const fse_opts& o) {
     return d;
 }
 
-int default_warps(int max_pix) {
-    int wpc = 0, per_sm = 0;
-    fse::choose_launch(max_pix, &wpc, &per_sm);
-    return wpc;
+// Launch shape for a tile: the options' warps per CTA and per stamp where
+// given, the library choice otherwise.  Only the whole chain puts several
+// warps on a stamp; a warps_per_cta given alone means one warp per stamp.
+void launch_shape(const fse_opts& o, int max_pix, int stage, int* wpc, int* nw) {
+    int dw = 0, dn = 0;
+    fse::choose_launch(max_pix, &dw, &dn);
+    int n = o.warps_per_stamp > 0 ? o.warps_per_stamp : (o.warps_per_cta > 0 ? 1 : dn);
+    if (stage != fse::kStageAll) n = 1;
+    int w = o.warps_per_cta > 0 ? o.warps_per_cta : (n == dn ? dw : n);
+    if (n == 1 && o.warps_per_cta <= 0 && dn != 1) {
+        // one warp per stamp on a large tile: as many as fit, up to four
+        const size_t spw = fse::smem_per_group(max_pix, false, 1);
+        w = 4;
+        while (w > 1 && spw * w > 227 * 1024) w >>= 1;
+    }
+    *wpc = w;
+    *nw = n;
 }
 
 // Common checks of the device entry points; fills `a` on success.
@@ -168,7 +186,11 @@ int prepare(fse_ctx* ctx, const void* pix, int dtype, const float* scale, const 
     a->err = ctx->d_err;
     a->opts = dev_opts(o);
     a->stage = stage;
-    a->warps_per_cta = o.warps_per_cta > 0 ? o.warps_per_cta : default_warps(a->opts.max_pix);
+    if (stage != fse::kStageAll && o.warps_per_stamp > 1)
+        return set_error(ctx, FSE_EINVAL, "warps_per_stamp > 1 applies to the whole chain only");
+    launch_shape(o, a->opts.max_pix, stage, &a->warps_per_cta, &a->warps_per_stamp);
+    if (a->warps_per_cta % a->warps_per_stamp != 0)
+        return set_error(ctx, FSE_EINVAL, "warps_per_cta must be a multiple of warps_per_stamp");
     return FSE_OK;
 }
 
@@ -226,16 +248,27 @@ int ragged_workspace(fse_ctx* ctx, int64_t count) {
     return FSE_OK;
 }
 
-int class_warps(const fse_ctx* ctx, const fse::LaunchArgs& a, int user_wpc, int k) {
-    if (user_wpc > 0) return user_wpc;
-    const int t = ctx->tuned[a.dtype == FSE_BF16][a.inv_var != nullptr][k];
-    return t > 0 ? t : default_warps(fse::kClassPix[k]);
+// Launch shape of size class k: the options' where given, else the
+// autotuner's choice, else the library default for the class's tile.
+void class_shape(const fse_ctx* ctx, const fse::LaunchArgs& a, const fse_opts& o, int k, int* wpc,
+                 int* nw) {
+    if (o.warps_per_cta > 0 || o.warps_per_stamp > 0) {
+        launch_shape(o, fse::kClassPix[k], fse::kStageAll, wpc, nw);
+        return;
+    }
+    const int dt = a.dtype == FSE_BF16, iv = a.inv_var != nullptr;
+    if (ctx->tuned[dt][iv][k] > 0) {
+        *wpc = ctx->tuned[dt][iv][k];
+        *nw = ctx->tuned_nw[dt][iv][k];
+        return;
+    }
+    launch_shape(o, fse::kClassPix[k], fse::kStageAll, wpc, nw);
 }
 
 // Classification, then one persistent launch per size class (largest first),
 // each with a shared-memory tile for its class.  Everything is stream-ordered
 // on `s` with no host synchronisation, so the sequence can be captured.
-int enqueue_ragged(fse_ctx* ctx, const fse::LaunchArgs& a, int user_wpc, cudaStream_t s) {
+int enqueue_ragged(fse_ctx* ctx, const fse::LaunchArgs& a, const fse_opts& o, cudaStream_t s) {
     unsigned int* counts = ctx->d_cls;
     unsigned int* range = counts + kK;
     unsigned int* cursor = range + 2 * kK;
@@ -250,7 +283,7 @@ int enqueue_ragged(fse_ctx* ctx, const fse::LaunchArgs& a, int user_wpc, cudaStr
         b.perm = ctx->d_perm;
         b.range = range + 2 * k;
         b.queue = queues + k;
-        b.warps_per_cta = class_warps(ctx, a, user_wpc, k);
+        class_shape(ctx, a, o, k, &b.warps_per_cta, &b.warps_per_stamp);
         e = fse::launch_estimator(b, s);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "size-class launch");
     }
@@ -322,6 +355,7 @@ void fse_opts_default(fse_opts* o) {
     o->lm_lambda0 = 1e-3;
     o->flags = 0;
     o->warps_per_cta = 0;
+    o->warps_per_stamp = 0;
 }
 
 int fse_create(fse_ctx** out, int device) {
@@ -428,6 +462,7 @@ int fse_fit_batch_plain(fse_ctx* ctx, const void* pix, int dtype, const float* s
     int rc = prepare(ctx, pix, dtype, scale, idx, count, inv_var, opts, out, fse::kStageAll, &a);
     if (rc) return rc;
     a.warps_per_cta = 1;
+    a.warps_per_stamp = 1;
     a.num_ctas = 1;
     a.static_assign = 1;
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -522,7 +557,7 @@ int fse_fit_batch_host(fse_ctx* ctx, const void* pix, int64_t npix_total, int dt
         a.err = ctx->d_err;
         a.opts = dev_opts(o);
         a.stage = fse::kStageAll;
-        a.warps_per_cta = o.warps_per_cta > 0 ? o.warps_per_cta : default_warps(a.opts.max_pix);
+        launch_shape(o, a.opts.max_pix, fse::kStageAll, &a.warps_per_cta, &a.warps_per_stamp);
         rc = run(ctx, a, st);
         if (rc) {
             cudaEventDestroy(ev0);
@@ -561,7 +596,7 @@ int fse_fit_batch_ragged(fse_ctx* ctx, const void* pix, int dtype, const float* 
     if (rc || count == 0) return rc;
     if ((rc = ragged_workspace(ctx, count))) return rc;
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (!(o.flags & FSE_FLAG_GRAPH)) return enqueue_ragged(ctx, a, o.warps_per_cta, s);
+    if (!(o.flags & FSE_FLAG_GRAPH)) return enqueue_ragged(ctx, a, o, s);
     RaggedKey key;
     make_key(ctx, a, o, &key);
     if (!ctx->gexec || memcmp(&key, ctx->gkey, sizeof key) != 0) {
@@ -570,7 +605,7 @@ int fse_fit_batch_ragged(fse_ctx* ctx, const void* pix, int dtype, const float* 
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "graph capture");
-        rc = enqueue_ragged(ctx, a, o.warps_per_cta, ctx->cap_stream);
+        rc = enqueue_ragged(ctx, a, o, ctx->cap_stream);
         e = cudaStreamEndCapture(ctx->cap_stream, &graph);
         if (rc) {
             if (graph) cudaGraphDestroy(graph);
@@ -619,11 +654,16 @@ int fse_autotune(fse_ctx* ctx, const void* pix, int dtype, const float* scale,
     const int dt = dtype == FSE_BF16, iv = inv_var != nullptr;
     for (int k = 0; k < kK && e == cudaSuccess; ++k) {
         if (hc[k] == 0) continue;
-        const size_t spw = fse::smem_per_warp_iv(fse::kClassPix[k], iv != 0);
         float best = 1e30f;
-        int best_w = 0;
-        for (int wpc = 1; wpc <= 8 && e == cudaSuccess; wpc *= 2) {
-            if (spw * wpc > 227 * 1024) break;
+        int best_w = 0, best_n = 1;
+        // (warps per stamp, stamp groups per CTA) with at most 8 warps per CTA
+        // and the groups' tiles within the shared memory of a CTA
+        for (int cand = 0; cand < 10 && e == cudaSuccess; ++cand) {
+            static const int kNw[10] = {1, 1, 1, 1, 2, 2, 2, 4, 4, 8};
+            static const int kGr[10] = {1, 2, 4, 8, 1, 2, 4, 1, 2, 1};
+            const int nw = kNw[cand], groups = kGr[cand];
+            if (fse::smem_per_group(fse::kClassPix[k], iv != 0, nw) * groups > 227 * 1024) continue;
+            const int wpc = nw * groups;
             float t_min = 1e30f;
             for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
                 fse::LaunchArgs b = a;
@@ -632,6 +672,7 @@ int fse_autotune(fse_ctx* ctx, const void* pix, int dtype, const float* scale,
                 b.range = range + 2 * k;
                 b.queue = queues + k;
                 b.warps_per_cta = wpc;
+                b.warps_per_stamp = nw;
                 e = cudaMemsetAsync(queues + k, 0, sizeof(unsigned int), s);
                 if (e == cudaSuccess) e = cudaEventRecord(ev0, s);
                 if (e == cudaSuccess) e = fse::launch_estimator(b, s);
@@ -644,9 +685,13 @@ int fse_autotune(fse_ctx* ctx, const void* pix, int dtype, const float* scale,
             if (t_min < best) {
                 best = t_min;
                 best_w = wpc;
+                best_n = nw;
             }
         }
-        if (best_w > 0) ctx->tuned[dt][iv][k] = best_w;
+        if (best_w > 0) {
+            ctx->tuned[dt][iv][k] = best_w;
+            ctx->tuned_nw[dt][iv][k] = best_n;
+        }
     }
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
@@ -655,11 +700,17 @@ int fse_autotune(fse_ctx* ctx, const void* pix, int dtype, const float* scale,
     return FSE_OK;
 }
 
-int fse_tuned_warps(const fse_ctx* ctx, int dtype, int has_inv_var, int32_t* warps) {
-    if (!ctx || !warps || (dtype != FSE_F32 && dtype != FSE_BF16)) return FSE_EINVAL;
+int fse_tuned_warps(const fse_ctx* ctx, int dtype, int has_inv_var, int32_t* warps_per_cta,
+                    int32_t* warps_per_stamp) {
+    if (!ctx || !warps_per_cta || (dtype != FSE_F32 && dtype != FSE_BF16)) return FSE_EINVAL;
+    fse_opts o;
+    fse_opts_default(&o);
     for (int k = 0; k < kK; ++k) {
-        const int t = ctx->tuned[dtype == FSE_BF16][has_inv_var != 0][k];
-        warps[k] = t > 0 ? t : default_warps(fse::kClassPix[k]);
+        const int dt = dtype == FSE_BF16, iv = has_inv_var != 0;
+        int w = ctx->tuned[dt][iv][k], n = ctx->tuned_nw[dt][iv][k];
+        if (w <= 0) launch_shape(o, fse::kClassPix[k], fse::kStageAll, &w, &n);
+        warps_per_cta[k] = w;
+        if (warps_per_stamp) warps_per_stamp[k] = n;
     }
     return FSE_OK;
 }

@@ -40,7 +40,8 @@ struct LaunchArgs {
     unsigned int* err;       // sticky error word (bounded waits that expired)
     DevOpts opts;
     int stage;
-    int warps_per_cta;
+    int warps_per_cta;       // a multiple of warps_per_stamp
+    int warps_per_stamp;     // 1, 2, 4 or 8 warps share a stamp (whole chain only)
     int num_ctas;            // 0 = library choice
     int static_assign;       // 1: warp w of the grid takes stamp w only (no counter)
     // Size-class launches of the ragged path: the launch takes the stamps
@@ -92,11 +93,11 @@ cudaError_t eval_bn(const double* n, double* b, double* db, int64_t count, cudaS
 cudaError_t launch_estimator(const LaunchArgs& a, cudaStream_t stream);
 // Launches the chi^2 / adjoint kernel; returns the launch error.
 cudaError_t launch_chi2_grad(const GradArgs& a, cudaStream_t stream);
-// Shared memory a warp needs for stamps of up to max_pix pixels.
-size_t smem_per_warp(int max_pix);
-// The same with the per-pixel inverse-variance tile when ivar is set.
-size_t smem_per_warp_iv(int max_pix, bool ivar);
-// Largest warps-per-CTA / CTAs-per-SM choice for a tile size.
-void choose_launch(int max_pix, int* warps_per_cta, int* ctas_per_sm);
+// Shared memory of one stamp group (warps_per_stamp warps) for stamps of up
+// to max_pix pixels, with the per-pixel inverse-variance tile when ivar is set.
+size_t smem_per_group(int max_pix, bool ivar, int warps_per_stamp);
+// Library launch shape for a tile size: warps per stamp, and warps per CTA
+// (a multiple of it) as large as shared memory allows, up to four groups.
+void choose_launch(int max_pix, int* warps_per_cta, int* warps_per_stamp);
 
 }  // namespace fse

@@ -147,6 +147,112 @@ __device__ __forceinline__ void warp_allsum_df(float (&hi)[N], float (&lo)[N]) {
     }
 }
 
+// ------------------------------------------------------------------ stamp groups
+// NW warps may share one stamp (large stamps, whose shared-memory tile leaves
+// room for few of them per SM).  Thread t = 32 (warp in group) + lane strides
+// the pixels by 32 NW; reductions finish through the group's shared scratch in
+// a fixed order, so every thread of the group ends with the same bits, and the
+// scalar steps run redundantly in all of them, as in a single warp.  With
+// NW = 1 every operation below is the single-warp one (shuffles, __syncwarp).
+template <int NW>
+struct Grp {
+    static constexpr int NT = 32 * NW;
+    int t;        // thread index in the group
+    int lane;
+    int wi;       // warp index in the group
+    float* red;   // NW x 32 words of reduction scratch (NW > 1), 8-byte aligned
+    int bar;      // named barrier of the group (NW > 1)
+
+    __device__ __forceinline__ void sync() const {
+        if (NW == 1)
+            __syncwarp();
+        else
+            asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(NT) : "memory");
+    }
+
+    template <int N>
+    __device__ __forceinline__ void allsum(float (&v)[N]) const {
+        static_assert(N <= 32, "reduction width");
+        warp_allsum(v);
+        if (NW > 1) {
+            sync();   // the previous reduction's readers are done with red
+            if (lane == 0) {
+#pragma unroll
+                for (int i = 0; i < N; ++i) red[wi * 32 + i] = v[i];
+            }
+            sync();
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                float acc = red[i];
+#pragma unroll
+                for (int k = 1; k < NW; ++k) acc += red[k * 32 + i];
+                v[i] = acc;
+            }
+        }
+    }
+
+    template <int N>
+    __device__ __forceinline__ void allsum_df(float (&hi)[N], float (&lo)[N]) const {
+        static_assert(2 * N <= 32, "reduction width");
+        warp_allsum_df(hi, lo);
+        if (NW > 1) {
+            sync();
+            if (lane == 0) {
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    red[wi * 32 + i] = hi[i];
+                    red[wi * 32 + N + i] = lo[i];
+                }
+            }
+            sync();
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                float h = red[i], l = red[N + i];
+#pragma unroll
+                for (int k = 1; k < NW; ++k) {
+                    const float oh = red[k * 32 + i], ol = red[k * 32 + N + i];
+                    const float sum = h + oh;
+                    const float bb = sum - h;
+                    const float e = (h - (sum - bb)) + (oh - bb);
+                    l = (l + ol) + e;
+                    h = sum;
+                }
+                hi[i] = h;
+                lo[i] = l;
+            }
+        }
+    }
+
+    __device__ __forceinline__ long long allsum_ll(long long v) const {
+        v = warp_allsum_ll(v);
+        if (NW > 1) {
+            long long* r = reinterpret_cast<long long*>(red);
+            sync();
+            if (lane == 0) r[wi * 16] = v;
+            sync();
+            long long acc = r[0];
+#pragma unroll
+            for (int k = 1; k < NW; ++k) acc += r[k * 16];
+            v = acc;
+        }
+        return v;
+    }
+
+    __device__ __forceinline__ bool all(bool b) const {
+        b = __all_sync(kFull, b);
+        if (NW > 1) {
+            sync();
+            if (lane == 0) red[wi * 32] = b ? 1.f : 0.f;
+            sync();
+            bool acc = true;
+#pragma unroll
+            for (int k = 0; k < NW; ++k) acc = acc && red[k * 32] != 0.f;
+            b = acc;
+        }
+        return b;
+    }
+};
+
 // ------------------------------------------------------------------ b(n)
 // Digamma for z > 0: recurrence up to z >= 10, then the asymptotic series
 // psi(z) ~ ln z - 1/(2z) - sum B_2k / (2k z^2k) (Abramowitz & Stegun 6.3.18).
@@ -274,15 +380,20 @@ __host__ __device__ inline size_t aux_bytes(int max_pix) {
 __host__ __device__ inline size_t warp_bytes(int max_pix, bool ivar) {
     return pix_bytes(max_pix) + aux_bytes(max_pix) + (ivar ? pix_bytes(max_pix) : 0) + 16;
 }
+// Shared memory of a stamp group: the tile above plus, for nw > 1 warps per
+// stamp, the reduction scratch (nw x 32 words) and the work-counter word.
+__host__ __device__ inline size_t group_bytes(int max_pix, bool ivar, int nw) {
+    return warp_bytes(max_pix, ivar) + (nw > 1 ? static_cast<size_t>(nw) * 128 + 16 : 0);
+}
 
-// Pixel iterator: lane handles p = lane, lane + 32, ... of a w-wide stamp.
+// Pixel iterator: thread t handles p = t, t + nt, ... of a w-wide stamp.
 struct PixelWalk {
     int row, col, dr, dc, w;
-    __device__ PixelWalk(int lane, int w_) : w(w_) {
-        row = lane / w;
-        col = lane - row * w;
-        dr = 32 / w;
-        dc = 32 - dr * w;
+    __device__ PixelWalk(int t, int w_, int nt = 32) : w(w_) {
+        row = t / w;
+        col = t - row * w;
+        dr = nt / w;
+        dc = nt - dr * w;
     }
     __device__ __forceinline__ void next() {
         col += dc;
@@ -300,9 +411,10 @@ struct PixelWalk {
 // Floats: the stamp starts at buf + pad with pad chosen so that the body's
 // shared address is 16-byte aligned too.  BF16: the raw 2-byte values are
 // staged in `raw` first and decoded (times scale) into the float buffer.
-template <int DT>
+template <int DT, int NW>
 __device__ bool stage_stamp(float* buf, float** stamp, float* raw, const void* gsrc, int npix,
-                            float scale, uint64_t* bar, uint32_t* phase, int lane) {
+                            float scale, uint64_t* bar, uint32_t* phase, const Grp<NW>& g) {
+    constexpr int NT = Grp<NW>::NT;
     constexpr int esz = DT == FSE_BF16 ? 2 : 4;
     const uintptr_t ga = reinterpret_cast<uintptr_t>(gsrc);
     int head = static_cast<int>(((16 - (ga & 15)) & 15) / esz);
@@ -323,13 +435,13 @@ __device__ bool stage_stamp(float* buf, float** stamp, float* raw, const void* g
         dst_base = reinterpret_cast<char*>(buf);
         *stamp = buf + pad;
     }
-    // order this warp's earlier generic-proxy accesses to the buffer before
+    // order the group's earlier generic-proxy accesses to the buffer before
     // the async-proxy (TMA) write into it
     fence_proxy_async();
-    __syncwarp();
+    g.sync();
     bool ok = true;
     if (body > 0) {
-        if (lane == 0) {
+        if (g.t == 0) {
             mbar_expect_tx(bar, static_cast<uint32_t>(body * esz));
             tma_bulk_load(dst_base + (size_t)(pad + head) * esz,
                           static_cast<const char*>(gsrc) + (size_t)head * esz,
@@ -337,15 +449,15 @@ __device__ bool stage_stamp(float* buf, float** stamp, float* raw, const void* g
         }
     }
     if (DT == FSE_BF16) {
-        const __nv_bfloat16* g = static_cast<const __nv_bfloat16*>(gsrc);
+        const __nv_bfloat16* gb = static_cast<const __nv_bfloat16*>(gsrc);
         __nv_bfloat16* r = reinterpret_cast<__nv_bfloat16*>(dst_base) + pad;
-        for (int i = lane; i < head; i += 32) r[i] = g[i];
-        for (int i = tail + lane; i < npix; i += 32) r[i] = g[i];
+        for (int i = g.t; i < head; i += NT) r[i] = gb[i];
+        for (int i = tail + g.t; i < npix; i += NT) r[i] = gb[i];
     } else {
-        const float* g = static_cast<const float*>(gsrc);
+        const float* gf = static_cast<const float*>(gsrc);
         float* s = *stamp;
-        for (int i = lane; i < head; i += 32) s[i] = __ldg(g + i);
-        for (int i = tail + lane; i < npix; i += 32) s[i] = __ldg(g + i);
+        for (int i = g.t; i < head; i += NT) s[i] = __ldg(gf + i);
+        for (int i = tail + g.t; i < npix; i += NT) s[i] = __ldg(gf + i);
     }
     if (body > 0) {
         ok = false;
@@ -357,14 +469,17 @@ __device__ bool stage_stamp(float* buf, float** stamp, float* raw, const void* g
         }
         ++*phase;
     }
-    __syncwarp();
-    if (DT == FSE_BF16) {
+    g.sync();   // the head and tail loads of the other threads are visible
+    // every thread of the group waited on the same barrier; they act on one
+    // verdict
+    ok = g.all(ok);
+    if (DT == FSE_BF16 && ok) {
         const __nv_bfloat16* r = reinterpret_cast<const __nv_bfloat16*>(dst_base) + pad;
         float* s = *stamp;
-        for (int i = lane; i < npix; i += 32) s[i] = __bfloat162float(r[i]) * scale;
-        __syncwarp();
+        for (int i = g.t; i < npix; i += NT) s[i] = __bfloat162float(r[i]) * scale;
     }
-    return __all_sync(kFull, ok);
+    g.sync();
+    return ok;
 }
 
 // ------------------------------------------------------------------ moments
@@ -379,23 +494,26 @@ struct MomState {
 // Offsets (column - xr, row - yr) of every pixel as half2 (integers below
 // 2048 are exact in fp16), stored in the auxiliary buffer for the moment
 // passes.
-__device__ __forceinline__ void store_offsets(__half2* C, int w, int npix, int lane, int xr,
-                                              int yr) {
-    PixelWalk pw(lane, w);
-    for (int p = lane; p < npix; p += 32) {
+template <int NW>
+__device__ __forceinline__ void store_offsets(__half2* C, int w, int npix, const Grp<NW>& g,
+                                              int xr, int yr) {
+    PixelWalk pw(g.t, w, Grp<NW>::NT);
+    for (int p = g.t; p < npix; p += Grp<NW>::NT) {
         C[p] = __floats2half2_rn(static_cast<float>(pw.col - xr), static_cast<float>(pw.row - yr));
         pw.next();
     }
-    __syncwarp();
+    g.sync();
 }
 
 // One weighted pass: S0 = sum f W, S1 = sum f W theta, the three second and
 // five fourth moments of f W (f = pixel value).  Everything the centroid step
 // (Eqs. 5-6) and the ellipticity step (Eqs. 8-9 with A5-A6, B7-B14) needs is a
 // linear combination of these eleven sums.
+template <int NW>
 __device__ __forceinline__ void moment_pass(const float* __restrict__ s,
-                                            const __half2* __restrict__ C, int npix, int lane,
-                                            const MomState& st, float (&acc)[11]) {
+                                            const __half2* __restrict__ C, int npix,
+                                            const Grp<NW>& g, const MomState& st,
+                                            float (&acc)[11]) {
     const float gg = st.g1 * st.g1 + st.g2 * st.g2;
     const float A = 1.f + gg - 2.f * st.g1;
     const float B = 1.f + gg + 2.f * st.g1;
@@ -409,7 +527,7 @@ __device__ __forceinline__ void moment_pass(const float* __restrict__ s,
     const float cx = static_cast<float>(st.xi - st.xr) + st.xf;
     const float cy = static_cast<float>(st.yi - st.yr) + st.yf;
 #pragma unroll 2
-    for (int p = lane; p < npix; p += 32) {
+    for (int p = g.t; p < npix; p += Grp<NW>::NT) {
         const float2 X = __half22float2(C[p]);
         const float t1 = X.x - cx;
         const float t2 = X.y - cy;
@@ -429,7 +547,7 @@ __device__ __forceinline__ void moment_pass(const float* __restrict__ s,
         acc[9] = fmaf(f22, t12, acc[9]);    // theta1 theta2^3
         acc[10] = fmaf(f22, t22, acc[10]);  // theta2^4
     }
-    warp_allsum(acc);
+    g.allsum(acc);
 }
 
 struct MomStep {
@@ -567,8 +685,9 @@ __device__ __forceinline__ void shear_polarizability(const float (&m)[11], const
 // the weighted first moments, i.e. k taken from the moments) and the step of
 // Eq. 9 for g.  The fp32 iteration stops within the noise of its own sums
 // (~1e-6 px); this pass removes most of that noise.
-__device__ float moment_refine(const float* __restrict__ s, int w, int npix, int lane, bool ellip,
-                               MomState& st) {
+template <int NW>
+__device__ float moment_refine(const float* __restrict__ s, int w, int npix, const Grp<NW>& g,
+                               bool ellip, MomState& st) {
     const float gg = st.g1 * st.g1 + st.g2 * st.g2;
     const float A = 1.f + gg - 2.f * st.g1;
     const float B = 1.f + gg + 2.f * st.g1;
@@ -579,8 +698,8 @@ __device__ float moment_refine(const float* __restrict__ s, int w, int npix, int
     for (int i = 0; i < 6; ++i) dh[i] = dl[i] = 0.f;
 #pragma unroll
     for (int i = 0; i < 5; ++i) cx[i] = F[i] = 0.f;
-    PixelWalk pw(lane, w);
-    for (int p = lane; p < npix; p += 32) {
+    PixelWalk pw(g.t, w, Grp<NW>::NT);
+    for (int p = g.t; p < npix; p += Grp<NW>::NT) {
         const float k1 = static_cast<float>(pw.col - st.xi), k2 = static_cast<float>(pw.row - st.yi);
         // theta = k - x_f exactly as hi + lo (|k| >= |x_f| unless k = 0, where lo = 0)
         const float t1 = k1 - st.xf, t1l = -st.xf - (t1 - k1);
@@ -607,9 +726,9 @@ __device__ float moment_refine(const float* __restrict__ s, int w, int npix, int
         F[4] = fmaf(f22, t22, F[4]);
         pw.next();
     }
-    warp_allsum_df(dh, dl);
-    warp_allsum(cx);
-    warp_allsum(F);
+    g.allsum_df(dh, dl);
+    g.allsum(cx);
+    g.allsum(F);
     // The first moments vanish at the fixed point; once accumulated exactly
     // they are small numbers that fp32 carries to full relative precision.
     const float M0 = dh[0] + dl[0];
@@ -666,11 +785,12 @@ __device__ float moment_refine(const float* __restrict__ s, int w, int npix, int
 constexpr float kMomRefineSkip = 1e-7f;
 
 // Iterate to the stop rule.  Returns the number of passes; sets status bits.
-__device__ int moment_iterate(const float* s, __half2* C, int h, int w, int npix, int lane,
+template <int NW>
+__device__ int moment_iterate(const float* s, __half2* C, int h, int w, int npix, const Grp<NW>& g,
                               const DevOpts& o, bool ellip, MomState& st, uint32_t& status) {
     st.xr = st.xi;
     st.yr = st.yi;
-    store_offsets(C, w, npix, lane, st.xr, st.yr);
+    store_offsets(C, w, npix, g, st.xr, st.yr);
     const float sw_max = 0.5f * static_cast<float>(h < w ? h : w);
     float prev = 0.f;   // size of the previous step, for the contraction estimate
     // with the determined gain (k_gain = 0): a centre step that does not shrink
@@ -679,7 +799,7 @@ __device__ int moment_iterate(const float* s, __half2* C, int h, int w, int npix
     int it;
     for (it = 1; it <= o.max_iter_mom; ++it) {
         float m[11];
-        moment_pass(s, C, npix, lane, st, m);
+        moment_pass(s, C, npix, g, st, m);
         const MomStep d = moment_step(m, st, k_use, ellip);
         if (k_use <= 0.f) {
             const float dc = fmaxf(fabsf(d.dx), fabsf(d.dy));
@@ -751,8 +871,8 @@ __device__ int moment_iterate(const float* s, __half2* C, int h, int w, int npix
     // centre and g steps are taken separately); a second runs unless the first
     // moved the point by less than 1e-7
     if (status & FSE_ST_MOM_CONVERGED) {
-        if (moment_refine(s, w, npix, lane, ellip, st) > kMomRefineSkip) {
-            moment_refine(s, w, npix, lane, ellip, st);
+        if (moment_refine(s, w, npix, g, ellip, st) > kMomRefineSkip) {
+            moment_refine(s, w, npix, g, ellip, st);
             status |= FSE_ST_MOM_REFINE2;
         }
     }
@@ -773,25 +893,47 @@ struct InitOut {
 // interpolates linearly in the ring that crosses.  Sums are exact 64-bit
 // fixed point (pixel * 2^S), so the crossing ring does not depend on the
 // summation order.
-__device__ InitOut stamp_init(const float* s, int h, int w, int npix, int lane,
+template <int NW>
+__device__ InitOut stamp_init(const float* s, int h, int w, int npix, const Grp<NW>& g,
                               unsigned long long* hist) {
+    constexpr int NT = Grp<NW>::NT;
+    const int lane = g.lane;
     InitOut o;
     float vmax = -INFINITY, amax = 0.f;
     int imax = 0x7fffffff;
     bool fin = true;
-    for (int p = lane; p < npix; p += 32) {
+    for (int p = g.t; p < npix; p += NT) {
         const float v = s[p];
         fin = fin && isfinite(v);
         if (v > vmax) { vmax = v; imax = p; }
         amax = fmaxf(amax, fabsf(v));
     }
-    o.finite = __all_sync(kFull, fin);
+    o.finite = g.all(fin);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         const float ov = __shfl_xor_sync(kFull, vmax, off);
         const int oi = __shfl_xor_sync(kFull, imax, off);
         if (ov > vmax || (ov == vmax && oi < imax)) { vmax = ov; imax = oi; }
         amax = fmaxf(amax, __shfl_xor_sync(kFull, amax, off));
+    }
+    if (NW > 1) {
+        // the same rule across the group's warps, in warp order
+        g.sync();
+        if (lane == 0) {
+            g.red[g.wi * 32] = vmax;
+            g.red[g.wi * 32 + 1] = __int_as_float(imax);
+            g.red[g.wi * 32 + 2] = amax;
+        }
+        g.sync();
+        vmax = g.red[0];
+        imax = __float_as_int(g.red[1]);
+        amax = g.red[2];
+        for (int k = 1; k < NW; ++k) {
+            const float ov = g.red[k * 32];
+            const int oi = __float_as_int(g.red[k * 32 + 1]);
+            if (ov > vmax || (ov == vmax && oi < imax)) { vmax = ov; imax = oi; }
+            amax = fmaxf(amax, g.red[k * 32 + 2]);
+        }
     }
     o.peak = imax;
     o.fallback = false;
@@ -806,11 +948,11 @@ __device__ InitOut stamp_init(const float* s, int h, int w, int npix, int lane,
     const float fs = ldexpf(1.f, S);
     const int dh = (h - 1 > pr ? h - 1 - pr : pr), dw = (w - 1 > pc ? w - 1 - pc : pc);
     const int kmax = static_cast<int>(ceilf(sqrtf(static_cast<float>(dh * dh + dw * dw)))) + 1;
-    for (int k = lane; k <= kmax; k += 32) hist[k] = 0ull;
-    __syncwarp();
+    for (int k = g.t; k <= kmax; k += NT) hist[k] = 0ull;
+    g.sync();
     long long tot = 0;
-    PixelWalk pw(lane, w);
-    for (int p = lane; p < npix; p += 32) {
+    PixelWalk pw(g.t, w, NT);
+    for (int p = g.t; p < npix; p += NT) {
         const long long q = __float2ll_rn(s[p] * fs);
         tot += q;
         const int di = pw.row - pr, dj = pw.col - pc;
@@ -820,8 +962,8 @@ __device__ InitOut stamp_init(const float* s, int h, int w, int npix, int lane,
         atomicAdd(&hist[k], static_cast<unsigned long long>(q));
         pw.next();
     }
-    tot = warp_allsum_ll(tot);
-    __syncwarp();
+    tot = g.allsum_ll(tot);
+    g.sync();   // every ring of the histogram is complete (the scan reads them)
     if (tot <= 0) {
         o.fallback = true;
         return o;
@@ -864,7 +1006,7 @@ __device__ InitOut stamp_init(const float* s, int h, int w, int npix, int lane,
         o.r50 = static_cast<float>(kc - 1) + static_cast<float>(tot - 2 * prev) /
                                                  (2.f * static_cast<float>(cur - prev));
     }
-    __syncwarp();
+    g.sync();   // the histogram's space is reused after this
     return o;
 }
 
@@ -883,9 +1025,9 @@ struct FitEval {
     float corr;     // (I0 - I0g)^2 sum E^2 / chi2: cancellation in chi2 when large
 };
 
-template <bool IVAR>
+template <bool IVAR, int NW>
 __device__ FitEval fit_eval(const float* __restrict__ s, const float* __restrict__ L,
-                            const float* __restrict__ sq, int npix, int lane, float I0g,
+                            const float* __restrict__ sq, int npix, const Grp<NW>& g, float I0g,
                             float re, float n, float lq) {
     float b, db;
     bn_eval_f(n, &b, &db);
@@ -896,7 +1038,7 @@ __device__ FitEval fit_eval(const float* __restrict__ s, const float* __restrict
 #pragma unroll
     for (int i = 0; i < 10; ++i) acc[i] = 0.f;
 #pragma unroll 2
-    for (int p = lane; p < npix; p += 32) {
+    for (int p = g.t; p < npix; p += Grp<NW>::NT) {
         const float a = L[p] - c0;
         const float u = ex2(a * inv_n);
         float E = ex2(u * nbl);
@@ -918,7 +1060,7 @@ __device__ FitEval fit_eval(const float* __restrict__ s, const float* __restrict
         acc[8] = fmaf(va, r, acc[8]);
         acc[9] = fmaf(r, r, acc[9]);
     }
-    warp_allsum(acc);
+    g.allsum(acc);
     FitEval f;
     const float sEE = acc[0], sEv = acc[1], sEva = acc[2], svv = acc[3], svva = acc[4],
                 svaa = acc[5], sEr = acc[6], svr = acc[7], svar = acc[8], srr = acc[9];
@@ -944,10 +1086,10 @@ __device__ FitEval fit_eval(const float* __restrict__ s, const float* __restrict
 
 // Start: r_e from the weight size, n the candidate of {0.5, 1, 2, 4} with the
 // lowest chi^2 at its closed-form I0 (chi^2 = sum I^2 - (sum I E)^2 / sum E^2).
-template <bool IVAR>
+template <bool IVAR, int NW>
 __device__ void fit_start(const float* __restrict__ s, const float* __restrict__ L,
-                          const float* __restrict__ sq, int npix, int lane, float re0, float lq,
-                          float* n0, float* I00) {
+                          const float* __restrict__ sq, int npix, const Grp<NW>& g, float re0,
+                          float lq, float* n0, float* I00) {
     const float nc[4] = {0.5f, 1.f, 2.f, 4.f};
     float inv_n[4], nbl[4];
 #pragma unroll
@@ -961,7 +1103,7 @@ __device__ void fit_start(const float* __restrict__ s, const float* __restrict__
     float acc[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) acc[i] = 0.f;
-    for (int p = lane; p < npix; p += 32) {
+    for (int p = g.t; p < npix; p += Grp<NW>::NT) {
         const float a = L[p] - c0;
         float I = s[p];
         const float q = IVAR ? sq[p] : 1.f;
@@ -975,7 +1117,7 @@ __device__ void fit_start(const float* __restrict__ s, const float* __restrict__
             acc[2 * c + 1] = fmaf(E, I, acc[2 * c + 1]);
         }
     }
-    warp_allsum(acc);
+    g.allsum(acc);
     int best = 0;
     float bc = INFINITY;
 #pragma unroll
@@ -1103,9 +1245,10 @@ __device__ Precise refine_tail(const float (&rh)[10], const float (&rl)[10], con
     return o;
 }
 
-template <bool IVAR>
+template <bool IVAR, int NW>
 __device__ Precise fit_refine(const float* __restrict__ s, const float* __restrict__ L,
-                              const float* __restrict__ sq, int w, int npix, int lane, float I0g,
+                              const float* __restrict__ sq, int w, int npix, const Grp<NW>& g,
+                              float I0g,
                               float re, float n, float lq, const MomState& st) {
     float bf, dbf;
     bn_eval_f(n, &bf, &dbf);
@@ -1133,8 +1276,8 @@ __device__ Precise fit_refine(const float* __restrict__ s, const float* __restri
     for (int i = 0; i < 10; ++i) rh[i] = rl[i] = 0.f;
 #pragma unroll
     for (int i = 0; i < 4; ++i) T[i] = 0.f;
-    PixelWalk pw(lane, w);
-    for (int p = lane; p < npix; p += 32) {
+    PixelWalk pw(g.t, w, Grp<NW>::NT);
+    for (int p = g.t; p < npix; p += Grp<NW>::NT) {
         const float a = L[p] - c0;
         const float u = exp2_acc(a * inv_n);
         float E = exp2_acc(u * nbl);
@@ -1180,8 +1323,8 @@ __device__ Precise fit_refine(const float* __restrict__ s, const float* __restri
             df_add(rh[9], rl[9], r * r);
         }
     }
-    warp_allsum_df(rh, rl);
-    warp_allsum(T);
+    g.allsum_df(rh, rl);
+    g.allsum(T);
     // The sums are exact to about 1e-14 relative; the quantities that vanish at
     // the optimum (the gradient) are formed from them only after the
     // cancellation has happened inside the double-float sums.
@@ -1202,23 +1345,24 @@ struct FitOut {
 
 // Levenberg-Marquardt over theta = (r_e, n) with I0 at its closed form after
 // every pass; damping by the gain ratio rho (Nielsen 1999).
-template <bool IVAR>
+template <bool IVAR, int NW>
 __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, int w, int npix,
-                             int lane, const DevOpts& o, const MomState& st, uint32_t& status) {
+                             const Grp<NW>& g, const DevOpts& o, const MomState& st,
+                             uint32_t& status) {
     // per-pixel 0.5 log2 R^2 about the fixed centre with the fixed ellipticity
     const float g1 = st.g1, g2 = st.g2;
     const float gg = g1 * g1 + g2 * g2;
     const float A = 1.f + gg - 2.f * g1, B = 1.f + gg + 2.f * g1, G4 = 4.f * g2;
     {
-        PixelWalk pw(lane, w);
-        for (int p = lane; p < npix; p += 32) {
+        PixelWalk pw(g.t, w, Grp<NW>::NT);
+        for (int p = g.t; p < npix; p += Grp<NW>::NT) {
             const float t1 = static_cast<float>(pw.col - st.xi) - st.xf;
             const float t2 = static_cast<float>(pw.row - st.yi) - st.yf;
             const float R2 = fmaf(A, t1 * t1, fmaf(B, t2 * t2, -G4 * (t1 * t2)));
             L[p] = R2 > 0.f ? 0.5f * log2f(R2) : -1000.f;
             pw.next();
         }
-        __syncwarp();
+        g.sync();
     }
     const float gabs = sqrtf(gg);
     const float lq = log2f(1.f - gabs);          // log2 r = 0.5 log2 R^2 - log2(1 - |g|)
@@ -1227,7 +1371,7 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
     float re = static_cast<float>(kSqrt2Ln2) * st.sw / (1.f - gabs);
     re = re < re_min ? re_min : (re > re_max ? re_max : re);
     float n, I0g;
-    fit_start<IVAR>(s, L, sq, npix, lane, re, lq, &n, &I0g);
+    fit_start<IVAR>(s, L, sq, npix, g, re, lq, &n, &I0g);
     // One evaluation site: every pass of the profile goes through the single
     // fit_eval call at the top of this loop (first the start, then each trial
     // step, and a repeat at I0* when the amplitude jumped).
@@ -1239,7 +1383,7 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
     int evals = 0, band_accepts = 0, it = 0;
 #pragma unroll 1
     for (;;) {
-        const FitEval ev = fit_eval<IVAR>(s, L, sq, npix, lane, I0t, ret, nt, lq);
+        const FitEval ev = fit_eval<IVAR>(s, L, sq, npix, g, I0t, ret, nt, lq);
         ++evals;
         if (ev.corr > 0.5f && !retried) {
             // the amplitude moved so far that chi^2 lost precision: evaluate again at I0*
@@ -1334,7 +1478,7 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
         int passes = 0;
 #pragma unroll 1
         for (;;) {
-            const Precise E = fit_refine<IVAR>(s, L, sq, w, npix, lane, tI0, te, tn, lq, st);
+            const Precise E = fit_refine<IVAR>(s, L, sq, w, npix, g, tI0, te, tn, lq, st);
             ++passes;
             // a step within 1e-2 is taken on the Newton model alone: its chi^2
             // decrease can be below the rounding of the fp32 model values
@@ -1393,24 +1537,34 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
 }
 
 // ------------------------------------------------------------------ kernel
-template <int STAGE, int DT, bool IVAR>
+// NW warps share each stamp (a stamp group); a CTA holds blockDim.x / (32 NW)
+// groups, each with its own tile and, for NW > 1, named barrier 1 + group.
+template <int STAGE, int DT, bool IVAR, int NW>
 // 168 registers per thread let three CTAs of four warps share an SM (the
 // launch shape of 48x48 and smaller tiles); more would leave two.
 __global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
+    const int grp = warp / NW;
+    Grp<NW> g;
+    g.lane = lane;
+    g.wi = warp - grp * NW;
+    g.t = g.wi * 32 + lane;
+    g.bar = 1 + grp;
     const int max_pix = a.opts.max_pix;
-    unsigned char* wbase = smem + static_cast<size_t>(warp) * warp_bytes(max_pix, IVAR);
+    unsigned char* wbase = smem + static_cast<size_t>(grp) * group_bytes(max_pix, IVAR, NW);
     float* pixbuf = reinterpret_cast<float*>(wbase);
     float* aux = reinterpret_cast<float*>(wbase + pix_bytes(max_pix));
     float* ivbuf = IVAR ? reinterpret_cast<float*>(wbase + pix_bytes(max_pix) + aux_bytes(max_pix))
                         : nullptr;
     uint64_t* bar = reinterpret_cast<uint64_t*>(wbase + warp_bytes(max_pix, IVAR) - 16);
-    if (lane == 0) mbar_init(bar);
-    __syncwarp();
-    if (lane == 0) fence_proxy_async();
-    __syncwarp();
+    g.red = reinterpret_cast<float*>(wbase + warp_bytes(max_pix, IVAR));   // used when NW > 1
+    unsigned* slot = reinterpret_cast<unsigned*>(wbase + warp_bytes(max_pix, IVAR) + NW * 128);
+    if (g.t == 0) mbar_init(bar);
+    g.sync();
+    if (g.t == 0) fence_proxy_async();
+    g.sync();
     uint32_t phase = 0;
     const DevOpts& o = a.opts;
     // this launch's stamps: all of them, or one size class through perm
@@ -1420,12 +1574,17 @@ __global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
     for (int round = 0;; ++round) {
         unsigned sidx = 0;
         if (a.static_assign) {
-            // one stamp per warp, no work counter (used by the per-stamp launches)
+            // one stamp per group, no work counter (used by the per-stamp launches)
             if (round > 0) break;
-            sidx = blockIdx.x * (blockDim.x >> 5) + warp;
-        } else {
+            sidx = blockIdx.x * (blockDim.x / Grp<NW>::NT) + grp;
+        } else if (NW == 1) {
             if (lane == 0) sidx = atomicAdd(a.queue, 1u);
             sidx = __shfl_sync(kFull, sidx, 0);
+        } else {
+            g.sync();   // the whole group has read the previous stamp's word
+            if (g.t == 0) *slot = atomicAdd(a.queue, 1u);
+            g.sync();
+            sidx = *slot;
         }
         if (sidx >= count) break;
         const int64_t si = a.perm ? static_cast<int64_t>(a.perm[base + sidx]) : static_cast<int64_t>(sidx);
@@ -1452,18 +1611,19 @@ __global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
         }
         float* s = pixbuf;
         if (!skip) {
-            const char* g = static_cast<const char*>(a.pix) + ix.offset * (DT == FSE_BF16 ? 2 : 4);
+            const char* gsrc = static_cast<const char*>(a.pix) + ix.offset * (DT == FSE_BF16 ? 2 : 4);
             const float scale = (DT == FSE_BF16 && a.scale) ? a.scale[si] : 1.f;
-            const bool ok = stage_stamp<DT>(pixbuf, &s, aux, g, static_cast<int>(npl), scale, bar,
-                                            &phase, lane);
+            const bool ok = stage_stamp<DT>(pixbuf, &s, aux, gsrc, static_cast<int>(npl), scale, bar,
+                                            &phase, g);
             if (IVAR && ok) {
                 const float* gv = a.inv_var + ix.offset;
-                for (int p = lane; p < npl; p += 32) ivbuf[p] = sqrtf(fmaxf(__ldg(gv + p), 0.f));
-                __syncwarp();
+                for (int p = g.t; p < npl; p += Grp<NW>::NT) ivbuf[p] = sqrtf(fmaxf(__ldg(gv + p), 0.f));
+                g.sync();
             }
             if (!ok) {
-                // the copy did not complete within the bound: report and stop this warp
-                if (lane == 0) {
+                // the copy did not complete within the bound: report and stop this
+                // group (the verdict is the same in all its threads)
+                if (g.t == 0) {
                     atomicOr(a.err, 1u);
                     res.status = status | FSE_ST_TIMEOUT;
                     a.out[si] = res;
@@ -1475,7 +1635,7 @@ __global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
         MomState st;
         if (!skip && (STAGE == kStageCentroid || STAGE == kStageAll)) {
             const InitOut in =
-                stamp_init(s, h, w, npix, lane, reinterpret_cast<unsigned long long*>(aux));
+                stamp_init(s, h, w, npix, g, reinterpret_cast<unsigned long long*>(aux));
             if (!in.finite) {
                 status |= FSE_ST_NONFINITE;
                 skip = true;
@@ -1496,8 +1656,8 @@ __global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
         } else if (!skip) {
             // centre (and for the fit, ellipticity) from the previous stage
             bool fin = true;
-            for (int p = lane; p < npix; p += 32) fin = fin && isfinite(s[p]);
-            if (!__all_sync(kFull, fin)) {
+            for (int p = g.t; p < npix; p += Grp<NW>::NT) fin = fin && isfinite(s[p]);
+            if (!g.all(fin)) {
                 status |= FSE_ST_NONFINITE;
                 skip = true;
             }
@@ -1516,7 +1676,7 @@ __global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
         }
         if (!skip && STAGE != kStageFit) {
             const bool ellip = STAGE != kStageCentroid;
-            res.it_mom = moment_iterate(s, reinterpret_cast<__half2*>(aux), h, w, npix, lane, o,
+            res.it_mom = moment_iterate(s, reinterpret_cast<__half2*>(aux), h, w, npix, g, o,
                                         ellip, st, status);
             res.x0 = static_cast<float>(st.xi) + st.xf;
             res.y0 = static_cast<float>(st.yi) + st.yf;
@@ -1528,7 +1688,7 @@ __global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
             if (!(status & FSE_ST_MOM_CONVERGED)) skip = true;
         }
         if (!skip && (STAGE == kStageFit || STAGE == kStageAll)) {
-            const FitOut f = sersic_fit<IVAR>(s, aux, ivbuf, h, w, npix, lane, o, st, status);
+            const FitOut f = sersic_fit<IVAR>(s, aux, ivbuf, h, w, npix, g, o, st, status);
             res.I0 = static_cast<float>(f.I0);
             res.re = static_cast<float>(f.re);
             res.n = static_cast<float>(f.n);
@@ -1537,8 +1697,8 @@ __global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
             res.it_fit = f.iters;
         }
         res.status = status;
-        if (lane == 0) a.out[si] = res;
-        __syncwarp();
+        if (g.t == 0) a.out[si] = res;
+        g.sync();
     }
 }
 
@@ -1720,11 +1880,12 @@ cudaError_t launch_grad_dt(const GradArgs& a, cudaStream_t stream) {
     return launch_grad_t<DT, IVAR, false, false>(a, stream);
 }
 
-template <int STAGE, int DT, bool IVAR>
+template <int STAGE, int DT, bool IVAR, int NW>
 cudaError_t launch_t(const LaunchArgs& a, cudaStream_t stream) {
-    const size_t spw = warp_bytes(a.opts.max_pix, IVAR);
-    const size_t smem = spw * a.warps_per_cta;
-    auto kern = estimator_kernel<STAGE, DT, IVAR>;
+    const int groups = a.warps_per_cta / NW;
+    if (groups < 1 || groups * NW != a.warps_per_cta || groups > 15) return cudaErrorInvalidValue;
+    const size_t smem = group_bytes(a.opts.max_pix, IVAR, NW) * groups;
+    auto kern = estimator_kernel<STAGE, DT, IVAR, NW>;
     // the shared-memory opt-in is raised once per instantiation and size (per device)
     static size_t opted[64] = {0};
     int dev = 0;
@@ -1745,34 +1906,57 @@ cudaError_t launch_t(const LaunchArgs& a, cudaStream_t stream) {
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         grid = static_cast<long long>(per_sm) * sms;
     }
-    const long long need = (a.count + a.warps_per_cta - 1) / a.warps_per_cta;
+    const long long need = (a.count + groups - 1) / groups;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     kern<<<static_cast<unsigned>(grid), 32 * a.warps_per_cta, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
+// Warps per stamp: several only for the whole chain (the large-stamp launches
+// of the ragged path); the single stages keep one warp per stamp.
+template <int STAGE, int DT, bool IVAR>
+cudaError_t launch_nw(const LaunchArgs& a, cudaStream_t stream) {
+    const int nw = a.warps_per_stamp > 1 ? a.warps_per_stamp : 1;
+    if constexpr (STAGE == kStageAll) {
+        switch (nw) {
+            case 1: return launch_t<STAGE, DT, IVAR, 1>(a, stream);
+            case 2: return launch_t<STAGE, DT, IVAR, 2>(a, stream);
+            case 4: return launch_t<STAGE, DT, IVAR, 4>(a, stream);
+            case 8: return launch_t<STAGE, DT, IVAR, 8>(a, stream);
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        if (nw != 1) return cudaErrorInvalidValue;
+        return launch_t<STAGE, DT, IVAR, 1>(a, stream);
+    }
+}
+
 template <int STAGE>
 cudaError_t launch_stage(const LaunchArgs& a, cudaStream_t stream) {
     const bool iv = a.inv_var != nullptr;
     if (a.dtype == FSE_BF16)
-        return iv ? launch_t<STAGE, FSE_BF16, true>(a, stream) : launch_t<STAGE, FSE_BF16, false>(a, stream);
-    return iv ? launch_t<STAGE, FSE_F32, true>(a, stream) : launch_t<STAGE, FSE_F32, false>(a, stream);
+        return iv ? launch_nw<STAGE, FSE_BF16, true>(a, stream) : launch_nw<STAGE, FSE_BF16, false>(a, stream);
+    return iv ? launch_nw<STAGE, FSE_F32, true>(a, stream) : launch_nw<STAGE, FSE_F32, false>(a, stream);
 }
 
 }  // namespace
 
 // ------------------------------------------------------------------ host wrappers
-size_t smem_per_warp(int max_pix) { return warp_bytes(max_pix, false); }
-size_t smem_per_warp_iv(int max_pix, bool ivar) { return warp_bytes(max_pix, ivar); }
+size_t smem_per_group(int max_pix, bool ivar, int warps_per_stamp) {
+    return group_bytes(max_pix, ivar, warps_per_stamp);
+}
 
-void choose_launch(int max_pix, int* warps_per_cta, int* ctas_per_sm) {
-    const size_t spw = warp_bytes(max_pix, false);
+void choose_launch(int max_pix, int* warps_per_cta, int* warps_per_stamp) {
+    // one warp per stamp up to 48x48 tiles; larger tiles leave room for few
+    // stamps per SM, so several warps share each of them
+    const int nw = max_pix <= 48 * 48 ? 1 : max_pix <= 64 * 64 ? 2 : max_pix <= 96 * 96 ? 4 : 8;
+    const size_t spg = group_bytes(max_pix, false, nw);
     const size_t budget = 227 * 1024;
-    int wpc = 4;
-    while (wpc > 1 && spw * wpc > budget) wpc >>= 1;
-    *warps_per_cta = wpc;
-    *ctas_per_sm = static_cast<int>((228 * 1024) / (spw * wpc + 1024));
+    int groups = nw == 1 ? 4 : 1;
+    while (groups > 1 && spg * groups > budget) groups >>= 1;
+    *warps_per_cta = groups * nw;
+    *warps_per_stamp = nw;
 }
 
 cudaError_t build_bn_table(cudaStream_t stream) {

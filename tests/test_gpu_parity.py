@@ -211,7 +211,9 @@ def test_plain_equals_batched(ctx):
     o1 = ctx.fit_batch(b.pix, idx, opts=opts_for(batch))
     o2 = ctx.fit_batch_plain(b.pix, idx, opts=opts_for(batch))
     o3 = ctx.fit_batch(b.pix, idx, opts=opts_for(batch, warps_per_cta=1))
-    o4 = ctx.fit_batch(b.pix, idx)
+    # the full 128x128 tile, still one warp per stamp (several warps sum in
+    # another order: tests/test_gpu_multiwarp.py)
+    o4 = ctx.fit_batch(b.pix, idx, opts=B.default_opts(warps_per_stamp=1))
     torch.cuda.synchronize()
     assert torch.equal(o1, o2) and torch.equal(o1, o3) and torch.equal(o1, o4)
 

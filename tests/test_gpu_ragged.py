@@ -1,19 +1,22 @@
 """Ragged batches through size-class launches (fse_fit_batch_ragged), the CUDA
 graph replay and the launch-shape autotuner, through the C ABI (needs a GB300).
 
-Each stamp is measured on its own by one warp, so its result cannot depend
-on which launch, tile size or launch shape processed it: the ragged path must
-reproduce fse_fit_batch byte for byte.  fse_fit_batch itself is held to the
-FP64 oracle by the parity tests.
+A stamp's result depends only on its pixels and on how many warps share it
+(the summation order).  With one warp per stamp the ragged path must reproduce
+fse_fit_batch byte for byte; with the library's or the autotuner's shapes
+(several warps on large stamps) it must meet the parity gate against the FP64
+oracle, and a captured graph must replay the eager launches byte for byte.
 """
 import numpy as np
 import pytest
 import torch
 
+import parity as PR
 from paper_1203_0571_gb300 import binding as B
 from paper_1203_0571_gb300 import synth
 
 pytestmark = pytest.mark.gpu
+ONE = dict(warps_per_stamp=1)
 
 
 @pytest.fixture(scope="module")
@@ -24,18 +27,19 @@ def ctx():
 
 @pytest.fixture(scope="module")
 def ragged():
-    b = synth.make_workload(2, count=3000).to("cuda")
-    return b, B.make_index(b.offset, b.h, b.w)
+    cpu = synth.make_workload(2, count=3000)
+    b = cpu.to("cuda")
+    return cpu, b, B.make_index(b.offset, b.h, b.w)
 
 
-def reference(ctx, b, idx):
-    return ctx.fit_batch(b.pix, idx, opts=B.default_opts(max_pix=128 * 128))
+def single(ctx, b, idx, **kw):
+    return ctx.fit_batch(b.pix, idx, scale=b.scale, opts=B.default_opts(max_pix=128 * 128, **ONE, **kw))
 
 
 def test_ragged_equals_single_launch(ctx, ragged):
-    b, idx = ragged
-    ref = reference(ctx, b, idx)
-    out = ctx.fit_batch_ragged(b.pix, idx)
+    _, b, idx = ragged
+    ref = single(ctx, b, idx)
+    out = ctx.fit_batch_ragged(b.pix, idx, opts=B.default_opts(**ONE))
     torch.cuda.synchronize()
     assert torch.equal(out, ref)
     # every size class is represented in this sample
@@ -46,34 +50,42 @@ def test_ragged_equals_single_launch(ctx, ragged):
 
 
 def test_graph_capture_and_replay(ctx, ragged):
-    b, idx = ragged
-    ref = reference(ctx, b, idx)
-    opts = B.default_opts(flags=1)
-    out = torch.zeros_like(ref)
-    ctx.fit_batch_ragged(b.pix, idx, opts=opts, out=out)      # captures
-    torch.cuda.synchronize()
-    assert torch.equal(out, ref)
-    out.zero_()
-    ctx.fit_batch_ragged(b.pix, idx, opts=opts, out=out)      # replays
-    torch.cuda.synchronize()
-    assert torch.equal(out, ref)
-    other = torch.zeros_like(ref)                             # new pointer: captures again
-    ctx.fit_batch_ragged(b.pix, idx, opts=opts, out=other)
-    torch.cuda.synchronize()
-    assert torch.equal(other, ref)
+    _, b, idx = ragged
+    for kw in (ONE, {}):
+        ref = ctx.fit_batch_ragged(b.pix, idx, opts=B.default_opts(**kw))          # eager
+        opts = B.default_opts(flags=1, **kw)
+        out = torch.zeros_like(ref)
+        ctx.fit_batch_ragged(b.pix, idx, opts=opts, out=out)      # captures
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+        out.zero_()
+        ctx.fit_batch_ragged(b.pix, idx, opts=opts, out=out)      # replays
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+        other = torch.zeros_like(ref)                             # new pointer: captures again
+        ctx.fit_batch_ragged(b.pix, idx, opts=opts, out=other)
+        torch.cuda.synchronize()
+        assert torch.equal(other, ref)
 
 
-def test_autotune_keeps_results(ctx, ragged):
-    b, idx = ragged
-    ref = reference(ctx, b, idx)
-    out = ctx.autotune(b.pix, idx)
+def test_default_and_tuned_shapes_meet_parity(ctx, oracle, ragged):
+    cpu, b, idx = ragged
+    O = oracle.get()
+    ids = np.sort(np.random.default_rng(13).choice(cpu.count, 300, replace=False))
+    o = PR.oracle_results(O, cpu, ids)
+    default = B.results(ctx.fit_batch_ragged(b.pix, idx))
+    rep = PR.compare(default[ids], o, O=O, batch=cpu, ids=ids)
+    assert rep["within_tolerance"] == rep["gated"] >= 0.8 * rep["n"], (rep["failing"], rep["max_err"])
+    ctx.autotune(b.pix, idx)
+    shapes = ctx.tuned_warps()
+    assert len(shapes) == 7 and all(c in (1, 2, 4, 8) and n in (1, 2, 4, 8) and c % n == 0
+                                    for c, n in shapes), shapes
+    eager = ctx.fit_batch_ragged(b.pix, idx)
+    graph = ctx.fit_batch_ragged(b.pix, idx, opts=B.default_opts(flags=1))
     torch.cuda.synchronize()
-    assert torch.equal(out, ref)
-    w = ctx.tuned_warps()
-    assert len(w) == 7 and all(x in (1, 2, 4, 8) for x in w), w
-    out2 = ctx.fit_batch_ragged(b.pix, idx, opts=B.default_opts(flags=1))
-    torch.cuda.synchronize()
-    assert torch.equal(out2, ref)
+    assert torch.equal(eager, graph)
+    rep = PR.compare(B.results(eager)[ids], o, O=O, batch=cpu, ids=ids)
+    assert rep["within_tolerance"] == rep["gated"] >= 0.8 * rep["n"], (rep["failing"], rep["max_err"])
 
 
 def test_ragged_with_invalid_sizes_and_bf16(ctx):
@@ -88,8 +100,8 @@ def test_ragged_with_invalid_sizes_and_bf16(ctx):
     bad = B.make_index(offs, [0, 129, 40, 1, 70], [5, 129, 33, 1, 66])
     px = torch.as_tensor(pix).cuda()
     for ix in (idx, bad):
-        ref = ctx.fit_batch(px, ix)
-        out = ctx.fit_batch_ragged(px, ix)
+        ref = ctx.fit_batch(px, ix, opts=B.default_opts(**ONE))
+        out = ctx.fit_batch_ragged(px, ix, opts=B.default_opts(**ONE))
         torch.cuda.synchronize()
         assert torch.equal(out, ref)
     r = B.results(ctx.fit_batch_ragged(px, bad))
@@ -97,7 +109,7 @@ def test_ragged_with_invalid_sizes_and_bf16(ctx):
     # bf16 pixels with per-stamp scales
     bb = synth.encode_bf16(synth.make_workload(2, count=500)).to("cuda")
     ib = B.make_index(bb.offset, bb.h, bb.w)
-    ref = ctx.fit_batch(bb.pix, ib, scale=bb.scale)
-    out = ctx.fit_batch_ragged(bb.pix, ib, scale=bb.scale, opts=B.default_opts(flags=1))
+    ref = single(ctx, bb, ib)
+    out = ctx.fit_batch_ragged(bb.pix, ib, scale=bb.scale, opts=B.default_opts(flags=1, **ONE))
     torch.cuda.synchronize()
     assert torch.equal(out, ref)
