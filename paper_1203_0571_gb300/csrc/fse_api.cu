@@ -758,6 +758,8 @@ int fse_sersic_chi2_grad(fse_ctx* ctx, const void* pix, int dtype, const float* 
     a.dparams = dparams;
     a.dpix = dpix;
     a.queue = ctx->d_queue + (ctx->next_queue++ % kQueues);
+    a.bnf = fse::bn_table_f32();
+    if (!a.bnf) return set_error(ctx, FSE_ECUDA, "b(n) table address");
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "work counter reset");

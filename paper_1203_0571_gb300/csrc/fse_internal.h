@@ -78,6 +78,7 @@ struct GradArgs {
     float* dparams;          // count x 7, or NULL
     float* dpix;             // laid out like pix (fp32), or NULL
     unsigned int* queue;     // work counter (zeroed before launch)
+    const float2* bnf;       // the device's fp32 b(n), b'(n) table (bn_table_f32)
 };
 
 // Number of nodes of the b(n) table and its range.
@@ -85,6 +86,8 @@ constexpr double kBnLo = 0.125;
 constexpr double kBnStep = 1.0 / 512.0;
 constexpr int kBnNodes = 5200;   // covers [0.125, 10.28]
 
+// Device address of the fp32 b(n), b'(n) table of the current device.
+const float2* bn_table_f32();
 // Builds the b(n), b'(n) table of the current device (idempotent per device).
 cudaError_t build_bn_table(cudaStream_t stream);
 // Evaluates the table at count points (device arrays).

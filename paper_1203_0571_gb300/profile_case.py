@@ -1,12 +1,15 @@
-"""A small, self-contained launch of fse_fit_batch for profiler captures.
+"""A small, self-contained launch of libfse for profiler captures.
 
-    python -m paper_1203_0571_gb300.profile_case [--workload 1] [--stamps 20000]
-                                                 [--warmup 3] [--launches 1]
+    python -m paper_1203_0571_gb300.profile_case [--what fit_batch|adjoint]
+        [--workload 1] [--stamps 20000] [--warmup 3] [--launches 1]
 
 Generates the first `stamps` stamps of a synthetic workload on the GPU, runs
-`warmup` launches, then `launches` more, and prints the per-launch time.  The
-inputs of the default case (20,000 stamps of 48x48 fp32, 184 MB) are larger
-than the 129 MB L2, so DRAM counters taken on it are meaningful.
+`warmup` launches, then `launches` more, and prints the per-launch time.
+fit_batch runs the whole chain; adjoint runs fse_sersic_chi2_grad at the
+generating parameters with the pixel gradient (the backward launch of the
+autograd bridge).  The inputs of the default cases (20,000 stamps of 48x48
+fp32, 184 MB; for the adjoint, 16,384 stamps of 64x64, 268 MB) are larger
+than the 129 MB L2, so DRAM counters taken on them are meaningful.
 """
 from __future__ import annotations
 
@@ -21,13 +24,18 @@ from . import synth
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", type=int, default=1)
-    ap.add_argument("--stamps", type=int, default=20000)
+    ap.add_argument("--what", choices=["fit_batch", "adjoint"], default="fit_batch")
+    ap.add_argument("--workload", type=int, default=None)
+    ap.add_argument("--stamps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--launches", type=int, default=1)
     args = ap.parse_args()
     ctx = B.Context(0)
-    batch = synth.make_workload(args.workload, count=args.stamps, device="cuda")
+    if args.what == "adjoint":
+        return adjoint(ctx, args.workload if args.workload is not None else 3,
+                       args.stamps if args.stamps is not None else 16384, args.warmup, args.launches)
+    batch = synth.make_workload(args.workload if args.workload is not None else 1,
+                                count=args.stamps if args.stamps is not None else 20000, device="cuda")
     idx = B.make_index(batch.offset, batch.h, batch.w)
     opts = B.default_opts(max_pix=int((batch.h.long() * batch.w.long()).max()))
     out = torch.empty((batch.count, 64), dtype=torch.uint8, device="cuda")
@@ -44,6 +52,28 @@ def main():
     print(json.dumps({"stamps": batch.count, "ms_per_launch": a.elapsed_time(b) / args.launches,
                       "converged": float(((res["status"] & 3) == 3).mean()),
                       "it_mom": float(res["it_mom"].mean()), "it_fit": float(res["it_fit"].mean())}))
+
+
+def adjoint(ctx, workload, stamps, warmup, launches):
+    import numpy as np
+    batch = synth.make_workload(workload, count=stamps, device="cuda")
+    idx = B.make_index(batch.offset, batch.h, batch.w)
+    t = batch.truth
+    p = torch.as_tensor(np.stack([t["xc"], t["yc"], t["g1"], t["g2"], t["I0"], t["re"], t["n"]], axis=1)
+                        .astype(np.float32)).cuda()
+    gout = torch.ones(batch.count, dtype=torch.float64, device="cuda")
+    kw = dict(gout=gout, want_chi2=False, want_dpix=True)
+    for _ in range(warmup):
+        ctx.chi2_grad(batch.pix, idx, p, **kw)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(launches):
+        ctx.chi2_grad(batch.pix, idx, p, **kw)
+    b.record()
+    ctx.sync_check()
+    print(json.dumps({"stamps": batch.count, "pixels": batch.pix.numel(),
+                      "ms_per_launch": a.elapsed_time(b) / launches}))
 
 
 if __name__ == "__main__":
