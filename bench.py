@@ -148,6 +148,21 @@ def kernel_traffic():
     return d.get("dram_bytes_per_launch") if d.get("kernel_sha256") == h else None
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over the ranks of the process group (x itself alone)."""
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: int, slowest_s: float) -> float:
+    """Units per second of the whole job: every rank (a replica) processes
+    units_per_rank, and the job ends with the slowest rank."""
+    return world * units_per_rank / slowest_s
+
+
 def cpu_oracle_rate(batch, target_s: float, max_stamps: int):
     """The FP64 oracle on the host cores over a bounded sample of the workload."""
     import oracle as O
@@ -260,17 +275,13 @@ def main():
     clk = clocks.stop()
     total_ms = t0.elapsed_time(t1)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    ms = total_ms / args.steps
-    if dist:
-        tt = torch.tensor([ms], device=f"cuda:{local}")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(total_ms / args.steps, f"cuda:{local}")
     res = B.results(out)
     ops = algorithmic_ops(res)
     kernel_ms = statistics.mean(step_ms)
     peak_gops = SMS * LANES_PER_SM * 2070.0 * 1e6 / 1e9     # at the maximum SM clock
     achieved = ops / (kernel_ms / 1e3) / 1e9
-    value = world * n / (ms / 1e3)
+    value = whole_job_rate(world, n, ms / 1e3)
 
     # end to end through the host-buffer entry point (pinned host memory)
     host_pix = batch.pix.cpu().pin_memory()
@@ -281,12 +292,8 @@ def main():
     t = time.perf_counter()
     for _ in range(args.e2e_steps):
         ctx.fit_batch_host(host_pix, host_idx, out=host_out)
-    e2e_s = (time.perf_counter() - t) / args.e2e_steps
-    if dist:
-        tt = torch.tensor([e2e_s], device=f"cuda:{local}")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": world * n / e2e_s, "unit": UNIT,
+    e2e_s = max_over_ranks((time.perf_counter() - t) / args.e2e_steps, f"cuda:{local}")
+    e2e = {"value": whole_job_rate(world, n, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(host_pix.numel() * 4 + host_idx.numel() * 8),
            "d2h_bytes_per_step": int(n * 64), "entry": "fse_fit_batch_host", "ms_per_step": 1e3 * e2e_s}
     same = bool(np.array_equal(host_out.numpy(), out.cpu().numpy()))
