@@ -47,6 +47,12 @@ class Result(ctypes.Structure):
                 ("status", ctypes.c_uint32)]
 
 
+class StarResult(ctypes.Structure):
+    _fields_ = [("size", ctypes.c_double), ("beta", ctypes.c_double), ("I0", ctypes.c_double),
+                ("flux", ctypes.c_double), ("r50", ctypes.c_double), ("iters", ctypes.c_int32),
+                ("status", ctypes.c_uint32)]
+
+
 RESULT_DTYPE = np.dtype([(k, "f8") for k in
                          ("x0", "y0", "e1", "e2", "sigma_w", "r50", "I0", "re", "n", "flux", "chi2")] +
                         [("npix", "i4"), ("it_mom", "i4"), ("it_fit", "i4"), ("status", "u4")])
@@ -83,6 +89,9 @@ class Oracle:
                                      [ctypes.c_int, _dp]
         L.orc_fit_eval.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + \
                                   [_dp, _dp]
+        L.orc_star.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Opts), ctypes.c_int] + \
+            [ctypes.c_double] * 5 + [ctypes.POINTER(StarResult)]
+        L.orc_star.restype = None
         L.orc_chi2_grad.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
         L.orc_chi2_grad.restype = None
         L.orc_batch.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -161,6 +170,16 @@ class Oracle:
         self.L.orc_fit_eval(_as_dp(I), None if iv is None else _as_dp(iv), I.shape[0], I.shape[1],
                             xc, yc, g1, g2, _as_dp(pp), _as_dp(out))
         return out[0], out[1:4].copy(), out[4:].reshape(3, 3).copy()
+
+    def star(self, I, xc, yc, g1, g2, size0, profile: str = "gauss", opts: Opts | None = None) -> dict:
+        """Sec. 4.2 star profile from weighted radial moments at a fixed centre and
+        ellipticity: size (Gaussian sigma or Moffat r_d along the major axis),
+        beta (Moffat), I0, flux, r50, iters, status."""
+        I = _img(I)
+        r = StarResult()
+        self.L.orc_star(_as_dp(I), I.shape[0], I.shape[1], ctypes.byref(opts or self.default_opts()),
+                        {"gauss": 0, "moffat": 1}[profile], xc, yc, g1, g2, size0, ctypes.byref(r))
+        return {k: getattr(r, k) for k, _ in StarResult._fields_}
 
     def chi2_grad(self, I, p, ivar=None, pixels: bool = False, scales: bool = False):
         """chi^2 and its gradient with respect to p = (x0, y0, g1, g2, I0, r_e, n)

@@ -305,6 +305,24 @@ def encode_bf16(batch: StampBatch) -> StampBatch:
     return dataclasses.replace(batch, pix=out, scale=scale)
 
 
+def moffat_stamp(h: int, w: int, *, beta: float, rd: float, g1: float, g2: float,
+                 xc: float, yc: float, I0: float, noise_sigma: float = 0.0,
+                 seed: int = 0) -> np.ndarray:
+    """One elliptical Moffat star (Sec. 4.2), I0 (1 + (r / r_d)^2)^-beta with the
+    semi-major-axis radius r = R(g) / (1 - |g|), sampled at pixel centres,
+    float64 (h, w); noise from the same counter-based normals as single_stamp."""
+    gabs = math.hypot(g1, g2)
+    yy, xx = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
+    d1, d2 = xx - xc, yy - yc
+    R2 = ((1 - g1) ** 2 + g2 ** 2) * d1 * d1 + ((1 + g1) ** 2 + g2 ** 2) * d2 * d2 - 4 * g2 * d1 * d2
+    r2 = np.maximum(R2, 0.0) / (1 - gabs) ** 2
+    img = I0 * (1.0 + r2 / (rd * rd)) ** (-beta)
+    if noise_sigma:
+        cnt = torch.arange(h * w, dtype=torch.int64)
+        img = img + noise_sigma * normal(seed, 7, cnt).numpy().reshape(h, w)
+    return img
+
+
 def single_stamp(h: int, w: int, *, n: float, re: float, g1: float, g2: float,
                  xc: float, yc: float, I0: float, noise_sigma: float = 0.0,
                  seed: int = 0, supersample: int = 1) -> np.ndarray:

@@ -330,6 +330,42 @@ def pin_chi2_grad_noiseless(O):
     assert chi2 <= 1e-18 and np.abs(g).max() <= 1e-7, (chi2, g)
 
 
+def pin_star_gaussian(O):
+    """Sec. 4.2 Gaussian star: on a noiseless, well-sampled elliptical Gaussian
+    the matched-weight iteration returns its sigma along the major axis and I0
+    (Eqs. for sigma and I0 with s_w = s), and the flux closed form
+    2 pi s^2 I0 q equals the pixel sum."""
+    for s_, g1, g2 in ((2.3, 0.15, -0.1), (3.1, -0.2, 0.05), (2.0, 0.0, 0.0)):
+        re = s_ * math.sqrt(2 * math.log(2))      # the n = 0.5 Sersic profile is this Gaussian
+        img = synth.single_stamp(64, 64, n=0.5, re=re, g1=g1, g2=g2, xc=31.3, yc=32.6, I0=500.0)
+        r = O.star(img, 31.3, 32.6, g1, g2, 1.5, "gauss")
+        assert r["status"] & 1, r
+        assert abs(r["size"] / s_ - 1) <= 1e-9 and abs(r["I0"] / 500.0 - 1) <= 1e-9, r
+        assert abs(r["flux"] / img.sum() - 1) <= 1e-9, (r["flux"], img.sum())
+        assert abs(r["r50"] - re) <= 1e-8 * re
+
+
+def pin_star_moffat(O):
+    """Sec. 4.2 Moffat star with the Moffat weight of exponent 3: on noiseless,
+    well-sampled elliptical Moffat profiles (r_d 10-12 px, beta 4.5-5, so that
+    pixelisation and the stamp edge are negligible) the iteration returns beta,
+    r_d and I0; the flux closed form pi r_d^2 I0 q / (beta - 1) equals the pixel
+    sum, and half of the flux of the profile lies inside
+    r50 = r_d sqrt(2^(1/(beta-1)) - 1) (numerical integration)."""
+    for beta, rd, g1, g2 in ((4.5, 10.0, 0.1, -0.05), (5.0, 12.0, 0.0, 0.2)):
+        img = synth.moffat_stamp(128, 128, beta=beta, rd=rd, g1=g1, g2=g2, xc=63.4, yc=64.2, I0=300.0)
+        r = O.star(img, 63.4, 64.2, g1, g2, 9.4, "moffat")
+        assert r["status"] & 1, r
+        assert abs(r["beta"] / beta - 1) <= 1e-5 and abs(r["size"] / rd - 1) <= 1e-5, r
+        assert abs(r["I0"] / 300.0 - 1) <= 1e-5, r
+        assert abs(r["flux"] / img.sum() - 1) <= 1e-5, (r["flux"], img.sum())
+        b, d = r["beta"], r["size"]
+        prof = lambda x: (1 + x * x / (d * d)) ** -b * 2 * math.pi * x
+        tot = integrate.quad(prof, 0, np.inf)[0]
+        half = integrate.quad(prof, 0, r["r50"])[0]
+        assert abs(half / tot - 0.5) <= 1e-9, half / tot
+
+
 def pin_edge_cases(O):
     """Status codes: non-finite pixels, empty flux, out-of-range sizes."""
     img = np.ones((8, 8))
@@ -346,4 +382,5 @@ ALL_PINS = [pin_gamma_p_library, pin_sersic_b, pin_sersic_db, pin_flux_closed_fo
             pin_flux_pixel_sum, pin_centroid_symmetric, pin_centroid_gain, pin_ellipticity_exact,
             pin_ellipticity_step_newton, pin_matched_sigma_w, pin_stages_chain, pin_fit_noiseless,
             pin_fit_gradient_fd, pin_fit_minimum, pin_fit_chi2_distribution, pin_r50_gaussian,
-            pin_chi2_grad_fd, pin_chi2_grad_noiseless, pin_edge_cases]
+            pin_chi2_grad_fd, pin_chi2_grad_noiseless, pin_star_gaussian, pin_star_moffat,
+            pin_edge_cases]

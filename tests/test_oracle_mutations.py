@@ -58,6 +58,15 @@ MUTATIONS = {
                            "const double dR2_x0 = -(2.0 * A * t1 + 4.0 * g2 * t2);"),
     # adjoint: sign of the pixel gradient
     "grad_dpix_sign": ("if (dpix) dpix[k] = -c;", "if (dpix) dpix[k] = c;"),
+    # star (Sec. 4.2): Moffat weight with exponent 2 instead of 3
+    "star_moffat_weight": ("W = 1.0 / (t * t * t);", "W = 1.0 / (t * t);"),
+    # star: the factor 2 of the Moffat beta
+    "star_moffat_beta": ("double ratio = m[2] * m[0] / (2.0 * m[1] * m[1]);",
+                         "double ratio = m[2] * m[0] / (m[1] * m[1]);"),
+    # star: Gaussian I0 without the axis ratio of the elliptical pixel sums
+    "star_gauss_I0_q": ("res->I0 = m[0] / (M_PI * size * size * q);", "res->I0 = m[0] / (M_PI * size * size);"),
+    # star: Moffat r50 exponent
+    "star_moffat_r50": ("pow(2.0, 1.0 / (beta - 1.0)) - 1.0", "pow(2.0, 1.0 / beta) - 1.0"),
     # non-finite input no longer flagged
     "nonfinite_check": ("if (!isfinite(I[p])) { *status |= ORC_NONFINITE; return 0; }", ""),
 }
