@@ -109,6 +109,10 @@ WORKLOADS = {
                 "4,000,000 stamps, side U{32..64}, pixels bf16 (per-stamp scale) or fp32"),
     5: Workload("precision-lowsnr", 10_000, 5,
                 "10,000 stamps, side U{32..64}, SNR U[10,30], n U[0.5,8] (error subsample)"),
+    6: Workload("stars-gauss-32px", 20_000, 6,
+                "20,000 Gaussian stars 32x32 fp32 (Sec. 4.2): r50 U[1.5,2.5] px, |g| U[0,0.25], SNR 300"),
+    7: Workload("stars-moffat-48px", 20_000, 7,
+                "20,000 Moffat stars 48x48 fp32 (Sec. 4.2): beta U[3,5], r50 U[1.5,2.5] px, |g| U[0,0.25], SNR 300"),
 }
 
 
@@ -188,14 +192,28 @@ def _draw_params(wl: Workload, ids: np.ndarray) -> dict:
         n = np.where(star, 0.5, n)
         re = np.where(star, fwhm / 2.0, re)
         gabs = np.where(star, U(9, 0.0, 0.05), gabs)
-    if wl.seed in (0, 1, 3):
-        side = np.full(N, {0: 32, 1: 48, 3: 64}[wl.seed], dtype=np.int64)
+    beta = np.zeros(N)
+    if wl.seed in (6, 7):
+        # Sec. 4.2 star simulations: r50 1.5-2.5 px, |g| up to 0.25, SNR 300.
+        # Gaussian: the n = 0.5 Sersic profile, whose r_e is r50.  Moffat: r_d
+        # from r50 = r_d sqrt(2^(1/(beta-1)) - 1), kept in `re`.
+        star[:] = True
+        r50 = U(1, 1.5, 2.5)
+        gabs = U(2, 0.0, 0.25)
+        snr = np.full(N, 300.0)
+        n = np.full(N, 0.5)
+        re = r50
+        if wl.seed == 7:
+            beta = U(11, 3.0, 5.0)
+            re = r50 / np.sqrt(2.0 ** (1.0 / (beta - 1.0)) - 1.0)
+    if wl.seed in (0, 1, 3, 6, 7):
+        side = np.full(N, {0: 32, 1: 48, 3: 64, 6: 32, 7: 48}[wl.seed], dtype=np.int64)
     elif wl.seed == 2:
         side = np.clip(np.rint(8.0 * re), 16, 128).astype(np.int64)
     else:
         side = np.floor(U(10, 32.0, 65.0)).astype(np.int64).clip(32, 64)
     return dict(n=n, re=re, gabs=gabs, phi=phi, dx=dx, dy=dy, flux=flux, snr=snr,
-                star=star, side=side, by_snr=np.full(N, wl.seed in (1, 5)))
+                star=star, side=side, beta=beta, by_snr=np.full(N, wl.seed in (1, 5, 6, 7)))
 
 
 def _render(side: int, p: dict, sel: np.ndarray, ids: np.ndarray, seed: int,
@@ -214,6 +232,10 @@ def _render(side: int, p: dict, sel: np.ndarray, ids: np.ndarray, seed: int,
     R2 = ((1 - g1) ** 2 + g2 ** 2) * d1 * d1 + ((1 + g1) ** 2 + g2 ** 2) * d2 * d2 - 4 * g2 * d1 * d2
     r = torch.sqrt(torch.clamp(R2, min=0.0)) / (1 - gabs)
     prof = torch.exp(-b * (r / re) ** (1.0 / n))
+    beta = t(p["beta"])
+    if bool((beta > 0).any()):
+        # Moffat stars (Sec. 4.2): re holds r_d
+        prof = torch.where(beta > 0, (1.0 + (r / re) ** 2) ** (-beta), prof)
     by_snr = torch.as_tensor(p["by_snr"][sel], device=device).view(k, 1, 1)
     amp_snr = t(p["snr"]) / torch.sqrt((prof * prof).sum(dim=(1, 2), keepdim=True))
     I0_flux = t(p["flux"]) / torch.as_tensor(
@@ -263,7 +285,7 @@ def make_workload(which: int, count: int | None = None, first: int = 0, device="
             pix[dst.reshape(-1)] = img32.reshape(-1)
             for k_, v in (("I0", I0), ("g1", g1), ("g2", g2), ("xc", xc), ("yc", yc), ("b", b)):
                 truth[k_][cs] = v
-    truth.update(n=p["n"], re=p["re"], star=p["star"], id=ids)
+    truth.update(n=p["n"], re=p["re"], star=p["star"], beta=p["beta"], id=ids)
     truth["flux"] = sersic_flux(truth["I0"], p["re"], p["n"], p["gabs"])
     return StampBatch(pix=pix,
                       offset=torch.as_tensor(offset, device=device),
