@@ -82,6 +82,10 @@ extern "C" {
  * CUDA graph on first use and replays it while its arguments are unchanged. */
 #define FSE_FLAG_GRAPH        (1u << 0)
 
+/* Star profiles of Sec. 4.2 (fse_star_fit). */
+#define FSE_STAR_GAUSS        0
+#define FSE_STAR_MOFFAT       1
+
 typedef struct fse_ctx fse_ctx;
 
 /* Stamp index entry (16 bytes).  offset counts elements (not bytes). */
@@ -137,6 +141,18 @@ typedef struct {
     float    sigma_w;       /* weight size used by the moments, px                      */
     float    r50;           /* growth-curve half-light radius of the start-up, px       */
 } fse_result;
+
+/* Star profile result (32 bytes), fse_star_fit. */
+typedef struct {
+    float    size;          /* Gaussian sigma or Moffat r_d along the major axis, px   */
+    float    beta;          /* Moffat beta (0 for the Gaussian)                         */
+    float    I0;            /* central intensity                                        */
+    float    flux;          /* Gaussian 2 pi s^2 I0 q; Moffat pi r_d^2 I0 q / (beta-1)  */
+    float    r50;           /* half-light radius along the major axis, px               */
+    int32_t  iters;         /* weight-size iterations                                   */
+    uint32_t status;        /* FSE_ST_MOM_CONVERGED / _MAXITER / _FAILED, BAD_SIZE, ... */
+    float    reserved;
+} fse_star_result;
 
 /* Create a context on CUDA device `device`: selects the device, builds the
  * device table of the Sérsic b(n) (root of P(2n, b) = 1/2, Eq. 10) and b'(n),
@@ -236,6 +252,25 @@ int fse_autotune(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
  * may be NULL). */
 int fse_tuned_warps(const fse_ctx *ctx, int dtype, int has_inv_var, int32_t *warps_per_cta,
                     int32_t *warps_per_stamp);
+
+/* Star profiles of Sec. 4.2 from weighted radial moments, at the centre and
+ * ellipticity of moments[s] (x0, y0, e1, e2 and sigma_w of a converged moment
+ * stage: fse_ellipticity or fse_fit_batch).  r is the semi-major-axis radius
+ * R(g)/(1-|g|); the pixel sums r_k = sum I W r^k carry the axis ratio
+ * q = (1-|g|)/(1+|g|), which cancels from every ratio.
+ *   FSE_STAR_GAUSS: W = exp(-r^2/2 s_w^2), sigma = sqrt(r2/r0), s_w <- sigma to
+ *     its fixed point (started at sigma_w/(1-|g|)), I0 = r0/(pi sigma^2 q).
+ *   FSE_STAR_MOFFAT: W = (1 + r^2/r_dw^2)^-3, beta = 1/(r4 r0/(2 r2^2) - 1),
+ *     r_d = sqrt(r2/r0 (beta+1)), r_dw <- r_d (started at 2.35 sigma_w/(1-|g|)),
+ *     I0 = r0 (beta+2)/(pi r_d^2 q).
+ * The iteration stops at a relative size step of opts->tol_sig within
+ * opts->max_iter_mom passes; opts->max_pix sizes the shared-memory tile.
+ * A stamp whose moments did not converge gets FSE_ST_MOM_FAILED.  The sums are
+ * over pixel centres (no pixel integration), so small stars carry the
+ * pixelation bias the paper reports.  Device pointers; asynchronous. */
+int fse_star_fit(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
+                 const fse_stamp *idx, int64_t count, const fse_result *moments, int profile,
+                 const fse_opts *opts, fse_star_result *out, void *stream);
 
 /* Evaluate the device b(n) table (Eq. 10: P(2n, b) = 1/2) and its derivative
  * at count values n[i] in [0.2, 10] (device pointers, doubles).  For tests. */

@@ -33,7 +33,11 @@ ST = dict(MOM_CONVERGED=1 << 0, FIT_CONVERGED=1 << 1, MOM_MAXITER=1 << 2, FIT_MA
 EXPORTS = ["fse_create", "fse_destroy", "fse_last_error", "fse_opts_default", "fse_centroid",
            "fse_ellipticity", "fse_sersic_fit", "fse_fit_batch", "fse_fit_batch_plain",
            "fse_fit_batch_host", "fse_fit_batch_ragged", "fse_autotune", "fse_tuned_warps",
-           "fse_sersic_b", "fse_sersic_chi2_grad", "fse_sync_check", "fse_fit_batch_static"]
+           "fse_star_fit", "fse_sersic_b", "fse_sersic_chi2_grad", "fse_sync_check",
+           "fse_fit_batch_static"]
+FSE_STAR_GAUSS, FSE_STAR_MOFFAT = 0, 1
+STAR_DTYPE = np.dtype([("size", "<f4"), ("beta", "<f4"), ("I0", "<f4"), ("flux", "<f4"), ("r50", "<f4"),
+                       ("iters", "<i4"), ("status", "<u4"), ("reserved", "<f4")])
 
 
 class Opts(ctypes.Structure):
@@ -91,6 +95,9 @@ def load(build: bool = True, path: str | None = None) -> ctypes.CDLL:
     L.fse_fit_batch_host.restype = ctypes.c_int
     L.fse_sersic_b.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int64, _vp]
     L.fse_sersic_b.restype = ctypes.c_int
+    L.fse_star_fit.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_int,
+                               ctypes.POINTER(Opts), _vp, _vp]
+    L.fse_star_fit.restype = ctypes.c_int
     L.fse_tuned_warps.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                   ctypes.POINTER(ctypes.c_int32)]
     L.fse_tuned_warps.restype = ctypes.c_int
@@ -136,6 +143,11 @@ def make_index(offset, h, w, device="cuda") -> torch.Tensor:
     hh = torch.as_tensor(h, dtype=torch.int64)
     ww = torch.as_tensor(w, dtype=torch.int64)
     return torch.stack([off, hh | (ww << 32)], dim=1).contiguous().to(device)
+
+
+def star_results(out: torch.Tensor) -> np.ndarray:
+    """Copy a star result tensor (uint8 [N, 32]) to a numpy structured array."""
+    return out.detach().cpu().contiguous().numpy().view(STAR_DTYPE).reshape(-1)
 
 
 def results(out: torch.Tensor) -> np.ndarray:
@@ -236,6 +248,19 @@ class Context:
         self._check(load().fse_tuned_warps(self._h, dtype, int(inv_var), w, n))
         return list(zip(w, n))
 
+    def star_fit(self, pix, index, moments, *, profile: str = "gauss", scale=None, opts=None,
+                 out=None, stream=None):
+        """fse_star_fit: Sec. 4.2 star profile at the moments' centre and ellipticity.
+        moments is a result tensor (uint8 [N, 64]); returns uint8 [N, 32]."""
+        n = int(index.shape[0])
+        if out is None:
+            out = torch.zeros((n, 32), dtype=torch.uint8, device=pix.device)
+        rc = load().fse_star_fit(self._h, _ptr(pix), _dtype_of(pix), _ptr(scale), _ptr(index), n,
+                                 _ptr(moments), {"gauss": FSE_STAR_GAUSS, "moffat": FSE_STAR_MOFFAT}[profile],
+                                 ctypes.byref(opts or default_opts()), _ptr(out), _stream(stream))
+        self._check(rc)
+        return out
+
     def fit_batch_host(self, pix: np.ndarray | torch.Tensor, index: np.ndarray | torch.Tensor, *,
                        scale=None, inv_var=None, opts=None, out=None, stream=None) -> np.ndarray:
         """fse_fit_batch_host: host buffers in, host results out (synchronous)."""
@@ -332,6 +357,10 @@ def fse_autotune(ctx: Context, *a, **k):
 
 def fse_tuned_warps(ctx: Context, *a, **k):
     return ctx.tuned_warps(*a, **k)
+
+
+def fse_star_fit(ctx: Context, *a, **k):
+    return ctx.star_fit(*a, **k)
 
 
 def fse_sersic_b(ctx: Context, *a, **k):

@@ -715,6 +715,49 @@ int fse_tuned_warps(const fse_ctx* ctx, int dtype, int has_inv_var, int32_t* war
     return FSE_OK;
 }
 
+int fse_star_fit(fse_ctx* ctx, const void* pix, int dtype, const float* scale, const fse_stamp* idx,
+                 int64_t count, const fse_result* moments, int profile, const fse_opts* opts,
+                 fse_star_result* out, void* stream) {
+    if (!ctx) return FSE_EINVAL;
+    if (count < 0 || count > 0x7fffffffLL) return set_error(ctx, FSE_EINVAL, "count out of range");
+    if (dtype != FSE_F32 && dtype != FSE_BF16) return set_error(ctx, FSE_EINVAL, "unknown dtype %d", dtype);
+    if (profile != FSE_STAR_GAUSS && profile != FSE_STAR_MOFFAT)
+        return set_error(ctx, FSE_EINVAL, "unknown star profile %d", profile);
+    fse_opts o;
+    if (opts) o = *opts; else fse_opts_default(&o);
+    int rc = check_opts(ctx, &o);
+    if (rc) return rc;
+    if (count == 0) return FSE_OK;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return set_error(ctx, FSE_ECUDA, "cannot select device %d", ctx->device);
+    if (!pix || !idx || !moments || !out)
+        return set_error(ctx, FSE_EINVAL, "pix, idx, moments and out must not be NULL");
+    const void* dev_ptrs[] = {pix, idx, moments, out, scale};
+    for (const void* q : dev_ptrs)
+        if (q && !is_device_ptr(q))
+            return set_error(ctx, FSE_EINVAL, "all array arguments must be device pointers");
+    fse::StarArgs a;
+    memset(&a, 0, sizeof a);
+    a.pix = pix;
+    a.dtype = dtype;
+    a.scale = scale;
+    a.idx = idx;
+    a.count = count;
+    a.moments = moments;
+    a.out = out;
+    a.profile = profile;
+    a.max_pix = o.max_pix > 0 ? o.max_pix : FSE_MAX_PIX;
+    a.tol = static_cast<float>(o.tol_sig);
+    a.max_iter = o.max_iter_mom;
+    a.queue = ctx->d_queue + (ctx->next_queue++ % kQueues);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "work counter reset");
+    e = fse::launch_star(a, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "star launch");
+    return FSE_OK;
+}
+
 int fse_sersic_b(fse_ctx* ctx, const double* n, double* b, double* db, int64_t count, void* stream) {
     if (!ctx) return FSE_EINVAL;
     if (count == 0) return FSE_OK;

@@ -81,6 +81,22 @@ struct GradArgs {
     const float2* bnf;       // the device's fp32 b(n), b'(n) table (bn_table_f32)
 };
 
+// Arguments of the star-profile kernel (fse_star_fit, Sec. 4.2).
+struct StarArgs {
+    const void* pix;
+    int dtype;
+    const float* scale;
+    const fse_stamp* idx;
+    int64_t count;
+    const fse_result* moments;   // centre, ellipticity and sigma_w of each stamp
+    fse_star_result* out;
+    int profile;                 // FSE_STAR_GAUSS or FSE_STAR_MOFFAT
+    int max_pix;                 // shared-memory tile (pixels per warp)
+    float tol;                   // relative step of the weight size that stops
+    int max_iter;
+    unsigned int* queue;         // work counter (zeroed before launch)
+};
+
 // Number of nodes of the b(n) table and its range.
 constexpr double kBnLo = 0.125;
 constexpr double kBnStep = 1.0 / 512.0;
@@ -94,6 +110,8 @@ cudaError_t build_bn_table(cudaStream_t stream);
 cudaError_t eval_bn(const double* n, double* b, double* db, int64_t count, cudaStream_t stream);
 // Launches the estimator kernel; returns the launch error.
 cudaError_t launch_estimator(const LaunchArgs& a, cudaStream_t stream);
+// Launches the star-profile kernel; returns the launch error.
+cudaError_t launch_star(const StarArgs& a, cudaStream_t stream);
 // Launches the chi^2 / adjoint kernel; returns the launch error.
 cudaError_t launch_chi2_grad(const GradArgs& a, cudaStream_t stream);
 // Shared memory of one stamp group (warps_per_stamp warps) for stamps of up
