@@ -10,7 +10,9 @@
 //     r_d = sqrt(r2 / r0 (beta + 1)); r_dw <- r_d; I0 = r0 (beta+2) / (pi r_d^2 q).
 // One warp per stamp: the stamp is read once from HBM (coalesced lane loads)
 // into shared memory, where the iteration makes its passes over it; sums are
-// double-float, reduced across the warp with xor shuffles.
+// double-float, within a lane and across the warp (xor shuffles), so that the
+// step that stops the iteration is not swamped by rounding: near tol_sig = 1e-6
+// the Moffat step is within a few fp32 ulps of the beta-amplified rounding.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -57,7 +59,7 @@ __device__ __forceinline__ void star_pixel(float2 v, float c, float& a0, float& 
 // One warp per stamp.  The stamp is staged once into shared memory as
 // (I, r^2) pairs, r^2 = R(g)^2 / (1 - |g|)^2 at the fixed centre and
 // ellipticity, so that each pass of the iteration reads one 8-byte word per
-// pixel and evaluates only the weight.  A lane sums four pixels in fp32 and
+// pixel and evaluates only the weight.  A lane sums eight pixels in fp32 and
 // adds the partial to a double-float accumulator.
 template <int DT, int PROF>
 __global__ void __launch_bounds__(256) star_kernel(StarArgs a) {
@@ -91,16 +93,30 @@ __global__ void __launch_bounds__(256) star_kernel(StarArgs a) {
             const float sc = (DT == FSE_BF16 && a.scale) ? a.scale[si] : 1.f;
             bool fin = true;
             PixelWalk pw(lane, ix.w);
-            for (int p = lane; p < npix; p += 32) {
-                const float v = DT == FSE_BF16
-                    ? __bfloat162float(static_cast<const __nv_bfloat16*>(a.pix)[ix.offset + p]) * sc
-                    : __ldg(static_cast<const float*>(a.pix) + ix.offset + p);
-                const float t1 = static_cast<float>(pw.col) - mom.x0;
-                const float t2 = static_cast<float>(pw.row) - mom.y0;
-                pw.next();
-                const float R2 = fmaf(A, t1 * t1, fmaf(B, t2 * t2, -G4 * (t1 * t2)));
-                sp[p] = make_float2(v, fmaxf(R2, 0.f) * inv1g2);
-                fin = fin && isfinite(v);
+            for (int p0 = lane; p0 < npix; p0 += 256) {
+                // eight loads in flight per lane before any is used
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int p = p0 + 32 * u;
+                    v[u] = 0.f;
+                    if (p < npix)
+                        v[u] = DT == FSE_BF16
+                            ? __bfloat162float(static_cast<const __nv_bfloat16*>(a.pix)[ix.offset + p]) * sc
+                            : __ldg(static_cast<const float*>(a.pix) + ix.offset + p);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int p = p0 + 32 * u;
+                    if (p < npix) {
+                        const float t1 = static_cast<float>(pw.col) - mom.x0;
+                        const float t2 = static_cast<float>(pw.row) - mom.y0;
+                        pw.next();
+                        const float R2 = fmaf(A, t1 * t1, fmaf(B, t2 * t2, -G4 * (t1 * t2)));
+                        sp[p] = make_float2(v[u], fmaxf(R2, 0.f) * inv1g2);
+                        fin = fin && isfinite(v[u]);
+                    }
+                }
             }
             __syncwarp();
             if (!__all_sync(kFull, fin)) res.status = FSE_ST_NONFINITE;
@@ -116,13 +132,17 @@ __global__ void __launch_bounds__(256) star_kernel(StarArgs a) {
                 float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
                 const float c = PROF == FSE_STAR_GAUSS ? -kLog2e / (2.f * sw * sw) : 1.f / (sw * sw);
                 int p = lane;
-                for (; p + 96 < npix; p += 128) {
-                    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+                for (; p + 224 < npix; p += 256) {
+                    // eight pixels in two interleaved fp32 chains
+                    float a0 = 0.f, a1 = 0.f, a2 = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f;
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) star_pixel<PROF>(sp[p + 32 * u], c, a0, a1, a2);
-                    df_add(hi[0], lo[0], a0);
-                    df_add(hi[1], lo[1], a1);
-                    if (PROF == FSE_STAR_MOFFAT) df_add(hi[2], lo[2], a2);
+                    for (int u = 0; u < 8; u += 2) {
+                        star_pixel<PROF>(sp[p + 32 * u], c, a0, a1, a2);
+                        star_pixel<PROF>(sp[p + 32 * u + 32], c, b0, b1, b2);
+                    }
+                    df_add(hi[0], lo[0], a0 + b0);
+                    df_add(hi[1], lo[1], a1 + b1);
+                    if (PROF == FSE_STAR_MOFFAT) df_add(hi[2], lo[2], a2 + b2);
                 }
                 {
                     float a0 = 0.f, a1 = 0.f, a2 = 0.f;

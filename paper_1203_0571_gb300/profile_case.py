@@ -1,15 +1,18 @@
 """A small, self-contained launch of libfse for profiler captures.
 
-    python -m paper_1203_0571_gb300.profile_case [--what fit_batch|adjoint]
-        [--workload 1] [--stamps 20000] [--warmup 3] [--launches 1]
+    python -m paper_1203_0571_gb300.profile_case [--what fit_batch|adjoint|star]
+        [--profile gauss|moffat] [--workload 1] [--stamps 20000] [--warmup 3] [--launches 1]
 
 Generates the first `stamps` stamps of a synthetic workload on the GPU, runs
 `warmup` launches, then `launches` more, and prints the per-launch time.
 fit_batch runs the whole chain; adjoint runs fse_sersic_chi2_grad at the
 generating parameters with the pixel gradient (the backward launch of the
-autograd bridge).  The inputs of the default cases (20,000 stamps of 48x48
-fp32, 184 MB; for the adjoint, 16,384 stamps of 64x64, 268 MB) are larger
-than the 129 MB L2, so DRAM counters taken on them are meaningful.
+autograd bridge); star runs fse_star_fit (Sec. 4.2) at the centre and
+ellipticity of a preceding fse_centroid + fse_ellipticity.  The inputs of the
+default cases (20,000 stamps of 48x48 fp32, 184 MB; for the adjoint, 16,384
+stamps of 64x64, 268 MB; for the stars, 50,000 Gaussian stars of 32x32, 205
+MB, or 50,000 Moffat stars of 48x48, 461 MB) are larger than the 129 MB L2,
+so DRAM counters taken on them are meaningful.
 """
 from __future__ import annotations
 
@@ -24,7 +27,8 @@ from . import synth
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--what", choices=["fit_batch", "adjoint"], default="fit_batch")
+    ap.add_argument("--what", choices=["fit_batch", "adjoint", "star"], default="fit_batch")
+    ap.add_argument("--profile", choices=["gauss", "moffat"], default="gauss")
     ap.add_argument("--workload", type=int, default=None)
     ap.add_argument("--stamps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
@@ -34,6 +38,10 @@ def main():
     if args.what == "adjoint":
         return adjoint(ctx, args.workload if args.workload is not None else 3,
                        args.stamps if args.stamps is not None else 16384, args.warmup, args.launches)
+    if args.what == "star":
+        return star(ctx, args.profile, args.workload if args.workload is not None else
+                    (6 if args.profile == "gauss" else 7),
+                    args.stamps if args.stamps is not None else 50000, args.warmup, args.launches)
     batch = synth.make_workload(args.workload if args.workload is not None else 1,
                                 count=args.stamps if args.stamps is not None else 20000, device="cuda")
     idx = B.make_index(batch.offset, batch.h, batch.w)
@@ -74,6 +82,29 @@ def adjoint(ctx, workload, stamps, warmup, launches):
     ctx.sync_check()
     print(json.dumps({"stamps": batch.count, "pixels": batch.pix.numel(),
                       "ms_per_launch": a.elapsed_time(b) / launches}))
+
+
+def star(ctx, profile, workload, stamps, warmup, launches):
+    batch = synth.make_workload(workload, count=stamps, device="cuda")
+    idx = B.make_index(batch.offset, batch.h, batch.w)
+    opts = B.default_opts(max_pix=int((batch.h.long() * batch.w.long()).max()))
+    mom = ctx.centroid(batch.pix, idx, opts=opts)
+    ctx.ellipticity(batch.pix, idx, mom, opts=opts)
+    out = torch.empty((batch.count, 32), dtype=torch.uint8, device="cuda")
+    for _ in range(warmup):
+        ctx.star_fit(batch.pix, idx, mom, profile=profile, opts=opts, out=out)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(launches):
+        ctx.star_fit(batch.pix, idx, mom, profile=profile, opts=opts, out=out)
+    b.record()
+    ctx.sync_check()
+    r = B.star_results(out)
+    conv = (r["status"] & 1) == 1
+    print(json.dumps({"stamps": batch.count, "pixels": batch.pix.numel(), "profile": profile,
+                      "ms_per_launch": a.elapsed_time(b) / launches, "converged": float(conv.mean()),
+                      "passes": int(r["iters"][conv].sum()), "passes_mean": float(r["iters"][conv].mean())}))
 
 
 if __name__ == "__main__":

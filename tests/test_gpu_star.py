@@ -109,9 +109,14 @@ def tolerance(profile, k, beta):
     return t
 
 
-def compare(g, o, mom, profile, min_converged=None, max_iter=STOP["max_iter_mom"]):
+def compare(g, o, mom, profile, min_converged=None, max_iter=STOP["max_iter_mom"],
+            tol_sig=STOP["tol_sig"]):
     """Statuses equal, values within tolerance(), pass counts within
-    ITER_SLACK; all mismatches are collected and the largest errors printed."""
+    ITER_SLACK; all mismatches are collected and the largest errors printed.
+    Where the two sides stopped after different numbers of passes, their last
+    sizes are one step of at most tol_sig apart, so each value's tolerance is
+    widened to 1.5 tol_sig (size) or 5 tol_sig (the values derived from it and
+    from the sums at the last weight)."""
     n = len(o)
     conv, errs, bad, dit, at_cap = 0, {k: 0.0 for k in TOL[profile]}, [], 0, 0
     for i in range(n):
@@ -141,6 +146,8 @@ def compare(g, o, mom, profile, min_converged=None, max_iter=STOP["max_iter_mom"
                 continue
             e = abs(gv / ov - 1.0)
             tol = tolerance(profile, k, float(o[i]["beta"]))
+            if int(g["iters"][i]) != int(o[i]["iters"]):
+                tol = max(tol, (1.5 if k == "size" else 5.0) * tol_sig)
             errs[k] = max(errs[k], e / tol)
             if not e <= tol:
                 bad.append((i, k, gv, ov, e, tol))
@@ -226,4 +233,4 @@ def test_star_paper_stopping_rule(ctx, O, profile, which):
     mom = oracle_moments(O, batch)
     o = oracle_stars(O, batch, mom, profile, tol_sig=1e-4, max_iter_mom=20)
     g = gpu_stars(ctx, batch, mom, profile, tol_sig=1e-4, max_iter_mom=20)
-    compare(g, o, mom, profile, min_converged=0.5, max_iter=20)
+    compare(g, o, mom, profile, min_converged=0.5, max_iter=20, tol_sig=1e-4)
