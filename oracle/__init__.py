@@ -63,11 +63,17 @@ MOM_CONVERGED, FIT_CONVERGED, MOM_MAXITER, FIT_MAXITER = 1, 2, 4, 8
 NONFINITE, BAD_SIZE, MOM_FAILED, FIT_BOUND = 16, 32, 64, 128
 FIT_SINGULAR, NONPOS_FLUX, SIGW_CLAMPED, INIT_FALLBACK = 256, 512, 1024, 2048
 
+# implicit-gradient modes: g a parameter (Secs. 2-3); sigma_w held, or from
+# the start-up growth curve (else the matched weight)
+MOM_ELLIP, MOM_SIGW_FIXED, MOM_SIGW_R50 = 1, 2, 4
+
 _dp = ctypes.POINTER(ctypes.c_double)
 
 
 class Oracle:
     """The oracle's entry points, bound to one compiled copy of fse_oracle.c."""
+
+    MOM_ELLIP, MOM_SIGW_FIXED, MOM_SIGW_R50 = MOM_ELLIP, MOM_SIGW_FIXED, MOM_SIGW_R50
 
     def __init__(self, path: str):
         L = ctypes.CDLL(path)
@@ -94,6 +100,12 @@ class Oracle:
         L.orc_star.restype = None
         L.orc_chi2_grad.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
         L.orc_chi2_grad.restype = None
+        L.orc_moment_jacobian.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp]
+        L.orc_moment_jacobian.restype = None
+        L.orc_moment_jvp.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]
+        L.orc_moment_jvp.restype = ctypes.c_int
+        L.orc_moment_vjp.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]
+        L.orc_moment_vjp.restype = ctypes.c_int
         L.orc_batch.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(Opts), ctypes.c_int,
                                 ctypes.c_void_p, ctypes.c_int]
@@ -201,6 +213,35 @@ class Oracle:
         if scales:
             out += (sc,)
         return out
+
+    def moment_jacobian(self, I, theta):
+        """F(theta) and J = dF/dtheta (5 x 5) of the moment fixed-point equations
+        at theta = (xc, yc, g1, g2, sigma_w)."""
+        I = _img(I)
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        F, J = np.zeros(5), np.zeros(25)
+        self.L.orc_moment_jacobian(_as_dp(I), I.shape[0], I.shape[1], _as_dp(th), _as_dp(F), _as_dp(J))
+        return F, J.reshape(5, 5)
+
+    def moment_jvp(self, I, theta, u, mode: int = MOM_ELLIP):
+        """d theta along the pixel tangent u (implicit function theorem).
+        Returns (dtheta[5], singular)."""
+        I = _img(I)
+        uu = _img(u)
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        d = np.zeros(5)
+        rc = self.L.orc_moment_jvp(_as_dp(I), I.shape[0], I.shape[1], _as_dp(th), mode, _as_dp(uu), _as_dp(d))
+        return d, bool(rc)
+
+    def moment_vjp(self, I, theta, v, mode: int = MOM_ELLIP):
+        """dL/dI for dL/dtheta = v (implicit function theorem).  Returns
+        (dI[h, w], singular)."""
+        I = _img(I)
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        vv = np.ascontiguousarray(v, dtype=np.float64)
+        d = np.zeros(I.shape)
+        rc = self.L.orc_moment_vjp(_as_dp(I), I.shape[0], I.shape[1], _as_dp(th), mode, _as_dp(vv), _as_dp(d))
+        return d, bool(rc)
 
     def batch(self, pix, offset, h, w, stage: str = "measure", ivar=None,
               opts: Opts | None = None, init=None, threads: int = 0):

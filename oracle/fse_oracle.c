@@ -20,6 +20,10 @@
  *     here Levenberg-Marquardt over (r_e, n)).
  *   - Sec. 4.1 start-up: brightest pixel and the half-light radius from the
  *     growth curve around it.
+ *   - Sec. 4.2: Gaussian and Moffat star profiles from weighted radial moments.
+ *   - Gradients: the chi^2 adjoint (Eqs. 10-12) and the implicit-function
+ *     derivatives of the moment fixed point (Secs. 2-3) with respect to the
+ *     pixels.
  *
  * Results are defined as converged fixed points / minima: the iterations run
  * to 1e-12 (moments) and 1e-10 (fit), far below the paper's 1e-4 stop, so that
@@ -216,9 +220,21 @@ static double ellip_R2(double t1, double t2, double g1, double g2)
 /* ------------------------------------------------------------------------ */
 /* Start-up (Sec. 4.1): brightest pixel, total, growth-curve r50.            */
 /* ------------------------------------------------------------------------ */
+static int init_stamp_k(const double *I, int h, int w, int *pk_row, int *pk_col,
+                        double *r50, uint32_t *status, int *k_cross);
+
 static int init_stamp(const double *I, int h, int w, int *pk_row, int *pk_col,
                       double *r50, uint32_t *status)
 {
+    return init_stamp_k(I, h, w, pk_row, pk_col, r50, status, NULL);
+}
+
+/* As init_stamp; *k_cross (if not NULL) receives the ring in which the growth
+ * curve crosses half the total, or -1 for the fallback radius. */
+static int init_stamp_k(const double *I, int h, int w, int *pk_row, int *pk_col,
+                        double *r50, uint32_t *status, int *k_cross)
+{
+    if (k_cross) *k_cross = -1;
     int npix = h * w, best = 0;
     for (int p = 0; p < npix; ++p) {
         if (!isfinite(I[p])) { *status |= ORC_NONFINITE; return 0; }
@@ -243,6 +259,7 @@ static int init_stamp(const double *I, int h, int w, int *pk_row, int *pk_col,
                 if (di * di + dj * dj <= k * k) S += I[i * w + j];
             }
         if (S >= half) {
+            if (k_cross) *k_cross = k;
             if (k == 0) *r50 = 0.5 * half / S;
             else        *r50 = (k - 1) + (half - prev) / (S - prev);
             return 1;
@@ -852,6 +869,248 @@ void orc_star(const double *I, int h, int w, const orc_opts *o, int profile, dou
         res->flux = beta > 1.0 ? M_PI * size * size * res->I0 * q / (beta - 1.0) : INFINITY;
         res->r50 = beta > 1.0 ? size * sqrt(pow(2.0, 1.0 / (beta - 1.0)) - 1.0) : INFINITY;
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Implicit gradients of the moment fixed point (Secs. 2-3).                  */
+/* ------------------------------------------------------------------------ */
+/* The moment iteration stops where its steps vanish.  With
+ * theta = (xc, yc, g1, g2, sigma_w), t = pixel - centre, R^2 of Eq. A1 at g,
+ * W = exp(-R^2 / 2 sigma_w^2) and e_w = 2 g / (1 + g^2), that point solves
+ *   F1 = sum I W t1 = 0,  F2 = sum I W t2 = 0          zero centroid step (Eqs. 3-6)
+ *   F3 = sum I W [(t1^2 - t2^2) - e_w1 (t1^2 + t2^2)]   e^obs = e_w, the zero of
+ *   F4 = sum I W [2 t1 t2 - e_w2 (t1^2 + t2^2)]           the step of Eq. 9, times T
+ *   F5 = sum I W [R^2 - sigma_w^2] = 0                  the matched weight,
+ *                                                       sigma_w^2 = sum I W R^2 / sum I W
+ * Each F_k = sum_p I_p psi_k(p; theta) is linear in the pixels, so by the
+ * implicit function theorem d theta / d I_p = -J^-1 psi(p; theta), with
+ * J_kl = sum_p I_p d psi_k / d theta_l.
+ * mode bit 0 (ORC_MOM_ELLIP): g is a parameter (the Secs. 2-3 fixed point);
+ * without it g = 0 is held (Sec. 2 alone: F3, F4 dropped).  sigma_w follows
+ * one of three rules:
+ *   (default)            the matched weight, F5 above;
+ *   ORC_MOM_SIGW_FIXED   held (F5 dropped; d sigma_w = 0), e.g. a clamped weight;
+ *   ORC_MOM_SIGW_R50     sigma_w = r50 / sqrt(2 ln 2) with r50 from the growth
+ *                        curve of the start-up (Sec. 4.1): F5 is dropped and
+ *                        sigma_w enters as an explicit function of the pixels,
+ *                        d theta_a = -J_aa^-1 (psi_a + J_as d sigma_w).
+ * Held parameters have zero derivatives. */
+#define ORC_MOM_ELLIP      1
+#define ORC_MOM_SIGW_FIXED 2
+#define ORC_MOM_SIGW_R50   4
+
+/* d sigma_w / d I_p for sigma_w = r50 / sqrt(2 ln 2).  r50 interpolates
+ * linearly in the ring k that crosses half the total H:
+ *   r50 = (k - 1) + (H - P) / (S - P),  P, S = sums over the discs d <= k-1, d <= k
+ *   (k = 0: r50 = H / (2 S), S the brightest pixel),
+ * with the brightest pixel and k held (they change only at isolated points).
+ * The derivative is zero where r50 is the fallback or sigma_w is clamped.
+ * Returns 1 if sigma_w depends on the pixels. */
+static int sigw_r50_grad(const double *I, int h, int w, double *ds)
+{
+    int pr, pc, k;
+    double r50;
+    uint32_t st = 0;
+    for (int p = 0; p < h * w; ++p) ds[p] = 0.0;
+    if (!init_stamp_k(I, h, w, &pr, &pc, &r50, &st, &k) || k < 0) return 0;
+    uint32_t cl = 0;
+    clamp_sigw(r50 / SQRT_2LN2, h, w, &cl);
+    if (cl) return 0;
+    double H = 0.0, P = 0.0, S = 0.0;
+    for (int i = 0; i < h; ++i)
+        for (int j = 0; j < w; ++j) {
+            int d2 = (i - pr) * (i - pr) + (j - pc) * (j - pc);
+            H += 0.5 * I[i * w + j];
+            if (k >= 1 && d2 <= (k - 1) * (k - 1)) P += I[i * w + j];
+            if (d2 <= k * k) S += I[i * w + j];
+        }
+    for (int i = 0; i < h; ++i)
+        for (int j = 0; j < w; ++j) {
+            int d2 = (i - pr) * (i - pr) + (j - pc) * (j - pc);
+            double inP = (k >= 1 && d2 <= (k - 1) * (k - 1)) ? 1.0 : 0.0;
+            double inS = d2 <= k * k ? 1.0 : 0.0;
+            double dr;
+            if (k == 0) dr = 0.5 * (0.5 * S - H * inS) / (S * S);
+            else dr = ((0.5 - inP) * (S - P) - (H - P) * (inS - inP)) / ((S - P) * (S - P));
+            ds[i * w + j] = dr / SQRT_2LN2;
+        }
+    return 1;
+}
+
+static int moment_is_active(int mode, int l)
+{
+    if ((l == 2 || l == 3) && !(mode & ORC_MOM_ELLIP)) return 0;
+    if (l == 4 && (mode & (ORC_MOM_SIGW_FIXED | ORC_MOM_SIGW_R50))) return 0;
+    return 1;
+}
+
+/* psi_k(p; theta) and, if dpsi != NULL, d psi_k / d theta_l (row k, column l). */
+static void moment_psi(double t1, double t2, const double th[5], double psi[5], double dpsi[5][5])
+{
+    double g1 = th[2], g2 = th[3], s = th[4];
+    double gg = g1 * g1 + g2 * g2;
+    double A = 1.0 + gg - 2.0 * g1, B = 1.0 + gg + 2.0 * g1;
+    double R2 = ellip_R2(t1, t2, g1, g2);
+    double W = exp(-R2 / (2.0 * s * s));
+    double ew1 = 2.0 * g1 / (1.0 + gg), ew2 = 2.0 * g2 / (1.0 + gg);
+    double th2 = t1 * t1 + t2 * t2;
+    double m[5] = { t1, t2, (t1 * t1 - t2 * t2) - ew1 * th2, 2.0 * t1 * t2 - ew2 * th2, R2 - s * s };
+    for (int k = 0; k < 5; ++k) psi[k] = W * m[k];
+    if (!dpsi) return;
+    /* derivatives of R^2 (t1 = x - xc, t2 = y - yc, so d t / d xc = -1) */
+    double dR2[5];
+    dR2[0] = -(2.0 * A * t1 - 4.0 * g2 * t2);
+    dR2[1] = -(2.0 * B * t2 - 4.0 * g2 * t1);
+    dR2[2] = (2.0 * g1 - 2.0) * t1 * t1 + (2.0 * g1 + 2.0) * t2 * t2;
+    dR2[3] = 2.0 * g2 * th2 - 4.0 * t1 * t2;
+    dR2[4] = 0.0;
+    /* derivatives of W: through R^2, and through sigma_w */
+    double dW[5];
+    for (int l = 0; l < 4; ++l) dW[l] = -W * dR2[l] / (2.0 * s * s);
+    dW[4] = W * R2 / (s * s * s);
+    /* derivatives of e_w = 2 g / (1 + g^2) */
+    double q = (1.0 + gg) * (1.0 + gg);
+    double dew1[2] = { 2.0 * (1.0 - g1 * g1 + g2 * g2) / q, -4.0 * g1 * g2 / q };
+    double dew2[2] = { -4.0 * g1 * g2 / q, 2.0 * (1.0 + g1 * g1 - g2 * g2) / q };
+    /* derivatives of the polynomial factors m_k */
+    double dm[5][5] = { { 0 } };
+    dm[0][0] = -1.0;
+    dm[1][1] = -1.0;
+    dm[2][0] = -2.0 * t1 + ew1 * 2.0 * t1;
+    dm[2][1] = 2.0 * t2 + ew1 * 2.0 * t2;
+    dm[2][2] = -dew1[0] * th2;
+    dm[2][3] = -dew1[1] * th2;
+    dm[3][0] = -2.0 * t2 + ew2 * 2.0 * t1;
+    dm[3][1] = -2.0 * t1 + ew2 * 2.0 * t2;
+    dm[3][2] = -dew2[0] * th2;
+    dm[3][3] = -dew2[1] * th2;
+    for (int l = 0; l < 4; ++l) dm[4][l] = dR2[l];
+    dm[4][4] = -2.0 * s;
+    for (int k = 0; k < 5; ++k)
+        for (int l = 0; l < 5; ++l) dpsi[k][l] = dW[l] * m[k] + W * dm[k][l];
+}
+
+/* F(theta) and J = dF/dtheta over the whole stamp (all 5 x 5 entries). */
+void orc_moment_jacobian(const double *I, int h, int w, const double th[5], double F[5], double J[25])
+{
+    double psi[5], dpsi[5][5];
+    for (int k = 0; k < 5; ++k) F[k] = 0.0;
+    for (int k = 0; k < 25; ++k) J[k] = 0.0;
+    for (int i = 0; i < h; ++i)
+        for (int j = 0; j < w; ++j) {
+            double f = I[i * w + j];
+            moment_psi(j - th[0], i - th[1], th, psi, dpsi);
+            for (int k = 0; k < 5; ++k) {
+                F[k] += f * psi[k];
+                for (int l = 0; l < 5; ++l) J[k * 5 + l] += f * dpsi[k][l];
+            }
+        }
+}
+
+/* Solve M x = b (n x n, row-major, n <= 5) by Gaussian elimination with
+ * partial pivoting; returns 0, or 1 if M is singular. */
+static int solve_small(int n, const double *M_in, const double *b_in, double *x)
+{
+    double M[25], b[5], big = 0.0;
+    for (int k = 0; k < n * n; ++k) { M[k] = M_in[k]; if (fabs(M[k]) > big) big = fabs(M[k]); }
+    for (int k = 0; k < n; ++k) b[k] = b_in[k];
+    if (!(big > 0.0)) return 1;
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r) if (fabs(M[r * n + c]) > fabs(M[piv * n + c])) piv = r;
+        if (!(fabs(M[piv * n + c]) > 1e-14 * big)) return 1;
+        if (piv != c) {
+            for (int k = 0; k < n; ++k) { double t = M[c * n + k]; M[c * n + k] = M[piv * n + k]; M[piv * n + k] = t; }
+            double t = b[c]; b[c] = b[piv]; b[piv] = t;
+        }
+        for (int r = c + 1; r < n; ++r) {
+            double f = M[r * n + c] / M[c * n + c];
+            for (int k = c; k < n; ++k) M[r * n + k] -= f * M[c * n + k];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int r = n - 1; r >= 0; --r) {
+        double acc = b[r];
+        for (int k = r + 1; k < n; ++k) acc -= M[r * n + k] * x[k];
+        x[r] = acc / M[r * n + r];
+    }
+    return 0;
+}
+
+/* The active block of J (rows and columns of the active parameters), or its
+ * transpose; returns the number of active parameters and their indices. */
+static int moment_active_block(const double J[25], int mode, int transpose, double *Ja, int act[5])
+{
+    int n = 0;
+    for (int l = 0; l < 5; ++l) if (moment_is_active(mode, l)) act[n++] = l;
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b)
+            Ja[a * n + b] = transpose ? J[act[b] * 5 + act[a]] : J[act[a] * 5 + act[b]];
+    return n;
+}
+
+/* JVP: the derivative of theta along a pixel tangent u,
+ *   dtheta_a = -J_aa^-1 (sum_p u_p psi_a(p) + J_as dsigma_w),
+ * dsigma_w = sum_p u_p d sigma_w / d I_p under ORC_MOM_SIGW_R50 (else 0).
+ * Returns 0, or 1 if J_aa is singular (dtheta = 0). */
+int orc_moment_jvp(const double *I, int h, int w, const double th[5], int mode, const double *u,
+                   double dth[5])
+{
+    double F[5], J[25], Ja[25], rhs[5] = { 0 }, x[5], S[5] = { 0 }, psi[5], dsw = 0.0;
+    int act[5];
+    for (int l = 0; l < 5; ++l) dth[l] = 0.0;
+    orc_moment_jacobian(I, h, w, th, F, J);
+    for (int i = 0; i < h; ++i)
+        for (int j = 0; j < w; ++j) {
+            moment_psi(j - th[0], i - th[1], th, psi, NULL);
+            for (int k = 0; k < 5; ++k) S[k] += u[i * w + j] * psi[k];
+        }
+    if (mode & ORC_MOM_SIGW_R50) {
+        double *ds = (double *)malloc(sizeof(double) * h * w);
+        if (sigw_r50_grad(I, h, w, ds))
+            for (int p = 0; p < h * w; ++p) dsw += u[p] * ds[p];
+        free(ds);
+    }
+    int n = moment_active_block(J, mode, 0, Ja, act);
+    for (int a = 0; a < n; ++a) rhs[a] = -(S[act[a]] + J[act[a] * 5 + 4] * dsw);
+    if (solve_small(n, Ja, rhs, x)) return 1;
+    for (int a = 0; a < n; ++a) dth[act[a]] = x[a];
+    if (mode & ORC_MOM_SIGW_R50) dth[4] = dsw;
+    return 0;
+}
+
+/* VJP: dL/dI for v = dL/dtheta (entries of held parameters ignored):
+ *   J_aa^T lambda = v_a,
+ *   dL/dI_p = -lambda . psi_a(p) + (v_s - lambda . J_as) d sigma_w / d I_p
+ * (the last term under ORC_MOM_SIGW_R50 only).  Returns 0, or 1 if J_aa is
+ * singular (dI = 0). */
+int orc_moment_vjp(const double *I, int h, int w, const double th[5], int mode, const double v[5],
+                   double *dI)
+{
+    double F[5], J[25], Ja[25], rhs[5] = { 0 }, lam_a[5], lam[5] = { 0 }, psi[5];
+    int act[5];
+    for (int p = 0; p < h * w; ++p) dI[p] = 0.0;
+    orc_moment_jacobian(I, h, w, th, F, J);
+    int n = moment_active_block(J, mode, 1, Ja, act);
+    for (int a = 0; a < n; ++a) rhs[a] = v[act[a]];
+    if (solve_small(n, Ja, rhs, lam_a)) return 1;
+    for (int a = 0; a < n; ++a) lam[act[a]] = lam_a[a];
+    for (int i = 0; i < h; ++i)
+        for (int j = 0; j < w; ++j) {
+            moment_psi(j - th[0], i - th[1], th, psi, NULL);
+            double acc = 0.0;
+            for (int k = 0; k < 5; ++k) acc += lam[k] * psi[k];
+            dI[i * w + j] = -acc;
+        }
+    if (mode & ORC_MOM_SIGW_R50) {
+        double kappa = v[4];
+        for (int k = 0; k < 5; ++k) kappa -= lam[k] * J[k * 5 + 4];
+        double *ds = (double *)malloc(sizeof(double) * h * w);
+        if (sigw_r50_grad(I, h, w, ds))
+            for (int p = 0; p < h * w; ++p) dI[p] += kappa * ds[p];
+        free(ds);
+    }
+    return 0;
 }
 
 /* Batch over a flat fp32 buffer (stamp s at pix + offset[s], h[s] x w[s]),

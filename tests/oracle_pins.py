@@ -366,6 +366,90 @@ def pin_star_moffat(O):
         assert abs(half / tot - 0.5) <= 1e-9, half / tot
 
 
+def _ellip_gaussian(h, w, xc, yc, g1, g2, sig, amp):
+    """amp exp(-R^2 / 2 sig^2) with R^2 of Eq. A1, and its derivatives with
+    respect to the centre, g1, g2, sig and amp, written from that formula."""
+    yy, xx = np.mgrid[0:h, 0:w].astype(float)
+    t1, t2 = xx - xc, yy - yc
+    A, B = (1 - g1) ** 2 + g2 ** 2, (1 + g1) ** 2 + g2 ** 2
+    R2 = A * t1 * t1 + B * t2 * t2 - 4 * g2 * t1 * t2
+    G = amp * np.exp(-R2 / (2 * sig * sig))
+    k = G / (2 * sig * sig)
+    tangents = [k * (2 * A * t1 - 4 * g2 * t2),                          # d/d xc
+                k * (2 * B * t2 - 4 * g2 * t1),                          # d/d yc
+                -k * ((2 * g1 - 2) * t1 * t1 + (2 * g1 + 2) * t2 * t2),  # d/d g1
+                -k * (2 * g2 * (t1 * t1 + t2 * t2) - 4 * t1 * t2),       # d/d g2
+                G * R2 / sig ** 3,                                       # d/d sig
+                G / amp]                                                 # d/d amp
+    return G, tangents
+
+
+def _moment_theta(O, I, sigw_mode, ellip=True):
+    """The oracle's moment fixed point (xc, yc, g1, g2, sigma_w), converged far
+    below the differences taken from it."""
+    o = O.default_opts(tol_pos=1e-13, tol_g=1e-13, tol_sig=1e-13, max_iter_mom=5000, sigw_mode=sigw_mode)
+    r = O.centroid(I, o)
+    if ellip:
+        r = O.ellipticity(I, r["x0"], r["y0"], r["sigma_w"], o)
+    assert r["status"] & 1, r
+    return np.array([r["x0"], r["y0"], r["e1"] if ellip else 0.0, r["e2"] if ellip else 0.0, r["sigma_w"]])
+
+
+def pin_moment_gradient_closed_forms(O):
+    """Implicit gradients of the moment fixed point (Secs. 2-3), matched weight.
+    On a well-sampled elliptical Gaussian the fixed point is its own centre, g
+    and sigma (the weight then has the image's shape and sigma_w^2 =
+    sum I W R^2 / sum I W = sigma^2), so it moves with the image: the derivative
+    along the image's change of centre, g1, g2 or sigma is the unit vector of
+    that parameter, and along its amplitude it is zero (the conditions are
+    homogeneous in the pixels).  The fixed-point equations vanish there."""
+    for xc, yc, g1, g2, sig in ((47.3, 48.6, 0.2, -0.15, 3.0), (40.8, 44.1, -0.1, 0.25, 3.4)):
+        G, tangents = _ellip_gaussian(96, 96, xc, yc, g1, g2, sig, 100.0)
+        th = _moment_theta(O, G, 0)
+        assert np.allclose(th, [xc, yc, g1, g2, sig], atol=1e-9), th
+        F, J = O.moment_jacobian(G, th)
+        assert np.abs(F).max() <= 1e-9 * np.abs(J).max(), F
+        for k, u in enumerate(tangents):
+            d, singular = O.moment_jvp(G, th, u, mode=1)
+            want = np.zeros(5)
+            if k < 5:
+                want[k] = 1.0
+            assert not singular and np.abs(d - want).max() <= 1e-8, (k, d)
+
+
+def pin_moment_gradient_fd(O):
+    """Implicit gradients of the moment fixed point against central differences
+    of the converged iteration itself, on a noisy stamp: Secs. 2-3 together and
+    Sec. 2 alone, with the matched weight and with sigma_w from the growth-curve
+    r50 (Sec. 4.1).  The VJP is the transpose of the JVP: <v, JVP u> = <VJP v, u>."""
+    rng = np.random.default_rng(11)
+    G, _ = _ellip_gaussian(64, 64, 31.6, 30.2, 0.18, 0.1, 3.0, 100.0)
+    S = G + rng.normal(0.0, 0.5, G.shape)
+    u = rng.normal(0.0, 1.0, G.shape)
+    eps = 1e-4
+    for sigw_mode, ellip in ((0, True), (1, True), (0, False), (1, False)):
+        mode = (O.MOM_ELLIP if ellip else 0) | (O.MOM_SIGW_R50 if sigw_mode == 1 else 0)
+        th = _moment_theta(O, S, sigw_mode, ellip)
+        fd = (_moment_theta(O, S + eps * u, sigw_mode, ellip) -
+              _moment_theta(O, S - eps * u, sigw_mode, ellip)) / (2 * eps)
+        d, singular = O.moment_jvp(S, th, u, mode=mode)
+        assert not singular and np.abs(d - fd).max() <= 1e-6 * np.abs(d).max(), (sigw_mode, ellip, d, fd)
+        v = rng.normal(0.0, 1.0, 5)
+        if not ellip:
+            v[2:4] = 0.0
+        dI, singular = O.moment_vjp(S, th, v, mode=mode)
+        assert not singular and abs(v @ d - (dI * u).sum()) <= 1e-10 * np.abs(v).max() * np.abs(dI).sum()
+    # J = dF/dtheta also away from the fixed point (where terms proportional to
+    # F1, F2 no longer vanish): central differences of F in each parameter
+    th = _moment_theta(O, S, 0) + np.array([0.3, -0.2, 0.05, -0.04, 0.2])
+    _, J = O.moment_jacobian(S, th)
+    for l in range(5):
+        e = np.zeros(5)
+        e[l] = 1e-5
+        fd = (O.moment_jacobian(S, th + e)[0] - O.moment_jacobian(S, th - e)[0]) / 2e-5
+        assert np.abs(J[:, l] - fd).max() <= 1e-6 * np.abs(J).max(), (l, J[:, l], fd)
+
+
 def pin_edge_cases(O):
     """Status codes: non-finite pixels, empty flux, out-of-range sizes."""
     img = np.ones((8, 8))
@@ -383,4 +467,4 @@ ALL_PINS = [pin_gamma_p_library, pin_sersic_b, pin_sersic_db, pin_flux_closed_fo
             pin_ellipticity_step_newton, pin_matched_sigma_w, pin_stages_chain, pin_fit_noiseless,
             pin_fit_gradient_fd, pin_fit_minimum, pin_fit_chi2_distribution, pin_r50_gaussian,
             pin_chi2_grad_fd, pin_chi2_grad_noiseless, pin_star_gaussian, pin_star_moffat,
-            pin_edge_cases]
+            pin_moment_gradient_closed_forms, pin_moment_gradient_fd, pin_edge_cases]

@@ -67,6 +67,22 @@ MUTATIONS = {
     "star_gauss_I0_q": ("res->I0 = m[0] / (M_PI * size * size * q);", "res->I0 = m[0] / (M_PI * size * size);"),
     # star: Moffat r50 exponent
     "star_moffat_r50": ("pow(2.0, 1.0 / (beta - 1.0)) - 1.0", "pow(2.0, 1.0 / beta) - 1.0"),
+    # implicit gradient: sign of the cross term in dR^2/dxc
+    "mom_grad_dR2_cross": ("dR2[0] = -(2.0 * A * t1 - 4.0 * g2 * t2);", "dR2[0] = -(2.0 * A * t1 + 4.0 * g2 * t2);"),
+    # implicit gradient: d e_w1 / d g1 with the signs of d e_w2 / d g2
+    "mom_grad_dew": ("2.0 * (1.0 - g1 * g1 + g2 * g2) / q", "2.0 * (1.0 + g1 * g1 - g2 * g2) / q"),
+    # implicit gradient: d W / d sigma_w loses a power of sigma_w
+    "mom_grad_dW_sigma": ("dW[4] = W * R2 / (s * s * s);", "dW[4] = W * R2 / (s * s);"),
+    # implicit gradient: sign of the e_w term of d m_3 / d yc
+    "mom_grad_dm3": ("dm[2][1] = 2.0 * t2 + ew1 * 2.0 * t2;", "dm[2][1] = 2.0 * t2 - ew1 * 2.0 * t2;"),
+    # implicit gradient: VJP solved with J instead of J^T
+    "mom_grad_vjp_transpose": ("int n = moment_active_block(J, mode, 1, Ja, act);",
+                               "int n = moment_active_block(J, mode, 0, Ja, act);"),
+    # implicit gradient: growth-curve r50 derivative with the wrong disc
+    "mom_grad_r50_disc": ("dr = ((0.5 - inP) * (S - P)", "dr = ((0.5 - inS) * (S - P)"),
+    # implicit gradient: sign of the sigma_w coupling in the VJP
+    "mom_grad_kappa_sign": ("for (int k = 0; k < 5; ++k) kappa -= lam[k] * J[k * 5 + 4];",
+                            "for (int k = 0; k < 5; ++k) kappa += lam[k] * J[k * 5 + 4];"),
     # non-finite input no longer flagged
     "nonfinite_check": ("if (!isfinite(I[p])) { *status |= ORC_NONFINITE; return 0; }", ""),
 }
