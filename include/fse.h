@@ -86,6 +86,11 @@ extern "C" {
 #define FSE_STAR_GAUSS        0
 #define FSE_STAR_MOFFAT       1
 
+/* Implicit gradients of the moment fixed point (fse_moment_vjp / _jvp). */
+#define FSE_MOM_ELLIP         1   /* g1, g2 are parameters (Secs. 2-3); else g = 0 (Sec. 2)  */
+#define FSE_MOM_SIGW_FIXED    2   /* sigma_w held                                           */
+#define FSE_MOM_SIGW_R50      4   /* sigma_w = r50/sqrt(2 ln 2) of the start-up growth curve */
+
 typedef struct fse_ctx fse_ctx;
 
 /* Stamp index entry (16 bytes).  offset counts elements (not bytes). */
@@ -271,6 +276,38 @@ int fse_tuned_warps(const fse_ctx *ctx, int dtype, int has_inv_var, int32_t *war
 int fse_star_fit(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
                  const fse_stamp *idx, int64_t count, const fse_result *moments, int profile,
                  const fse_opts *opts, fse_star_result *out, void *stream);
+
+/* Implicit-function derivatives of the moment fixed point (Secs. 2-3) with
+ * respect to the pixels.  The moment stage stops at theta = (x0, y0, e1, e2,
+ * sigma_w) where its steps vanish: with t = pixel - centre, R^2 of Eq. A1,
+ * W = exp(-R^2 / 2 sigma_w^2) and e_w = 2g/(1+g^2),
+ *   F_k = sum_p I_p W m_k(t) = 0,  m = (t1, t2, (t1^2 - t2^2) - e_w1 (t1^2 + t2^2),
+ *                                      2 t1 t2 - e_w2 (t1^2 + t2^2), R^2 - sigma_w^2)
+ * (zero centroid step, Eqs. 3-6; e^obs = e_w, the zero of the step of Eq. 9;
+ * the matched weight).  Hence d theta / d I_p = -J^-1 W(p) m(p) with
+ * J = dF/dtheta.  mode: FSE_MOM_ELLIP for the Secs. 2-3 fixed point (without
+ * it g = 0 is held: the Sec. 2 centroid stage), and the sigma_w rule of the
+ * moment stage: the matched weight (default; fse_opts.sigw_mode = 0),
+ * FSE_MOM_SIGW_FIXED (held), or FSE_MOM_SIGW_R50 (sigw_mode = 1: sigma_w =
+ * r50/sqrt(2 ln 2) from the start-up growth curve, Sec. 4.1, differentiated
+ * with the brightest pixel and the crossing ring held).  A stamp whose status
+ * has FSE_ST_SIGW_CLAMPED holds sigma_w.
+ * moments[s]: x0, y0, e1, e2, sigma_w, r50 and status of a moment stage
+ * (fse_centroid, fse_ellipticity or fse_fit_batch).
+ * fse_moment_vjp: v[s*5 + k] = dL/dtheta_k (entries of held parameters are
+ * ignored); writes dL/dI to dpix (fp32, at the element offsets of pix).
+ * fse_moment_jvp: tangent (fp32, offsets of pix) = dI; writes dtheta[s*5 + k].
+ * status[s] (optional): 0, or FSE_ST_MOM_FAILED (moments not converged),
+ * FSE_ST_NONFINITE, FSE_ST_BAD_SIZE (h*w above FSE_MAX_PIX: nothing written),
+ * FSE_ST_FIT_SINGULAR (J singular); such stamps get zero derivatives.
+ * bf16 pixels are decoded with scale[s]; the derivatives are with respect to
+ * the decoded intensities.  Device pointers; asynchronous on `stream`. */
+int fse_moment_vjp(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
+                   const fse_stamp *idx, int64_t count, const fse_result *moments, int mode,
+                   const float *v, float *dpix, uint32_t *status, void *stream);
+int fse_moment_jvp(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
+                   const fse_stamp *idx, int64_t count, const fse_result *moments, int mode,
+                   const float *tangent, float *dtheta, uint32_t *status, void *stream);
 
 /* Evaluate the device b(n) table (Eq. 10: P(2n, b) = 1/2) and its derivative
  * at count values n[i] in [0.2, 10] (device pointers, doubles).  For tests. */

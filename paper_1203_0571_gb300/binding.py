@@ -33,8 +33,9 @@ ST = dict(MOM_CONVERGED=1 << 0, FIT_CONVERGED=1 << 1, MOM_MAXITER=1 << 2, FIT_MA
 EXPORTS = ["fse_create", "fse_destroy", "fse_last_error", "fse_opts_default", "fse_centroid",
            "fse_ellipticity", "fse_sersic_fit", "fse_fit_batch", "fse_fit_batch_plain",
            "fse_fit_batch_host", "fse_fit_batch_ragged", "fse_autotune", "fse_tuned_warps",
-           "fse_star_fit", "fse_sersic_b", "fse_sersic_chi2_grad", "fse_sync_check",
-           "fse_fit_batch_static"]
+           "fse_star_fit", "fse_moment_vjp", "fse_moment_jvp", "fse_sersic_b", "fse_sersic_chi2_grad",
+           "fse_sync_check", "fse_fit_batch_static"]
+FSE_MOM_ELLIP, FSE_MOM_SIGW_FIXED, FSE_MOM_SIGW_R50 = 1, 2, 4
 FSE_STAR_GAUSS, FSE_STAR_MOFFAT = 0, 1
 STAR_DTYPE = np.dtype([("size", "<f4"), ("beta", "<f4"), ("I0", "<f4"), ("flux", "<f4"), ("r50", "<f4"),
                        ("iters", "<i4"), ("status", "<u4"), ("reserved", "<f4")])
@@ -98,6 +99,10 @@ def load(build: bool = True, path: str | None = None) -> ctypes.CDLL:
     L.fse_star_fit.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_int,
                                ctypes.POINTER(Opts), _vp, _vp]
     L.fse_star_fit.restype = ctypes.c_int
+    for f in ("fse_moment_vjp", "fse_moment_jvp"):
+        getattr(L, f).argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_int,
+                                  _vp, _vp, _vp, _vp]
+        getattr(L, f).restype = ctypes.c_int
     L.fse_tuned_warps.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                   ctypes.POINTER(ctypes.c_int32)]
     L.fse_tuned_warps.restype = ctypes.c_int
@@ -261,6 +266,34 @@ class Context:
         self._check(rc)
         return out
 
+    def moment_vjp(self, pix, index, moments, v, *, mode: int = FSE_MOM_ELLIP | FSE_MOM_SIGW_R50,
+                   scale=None, out=None, status=None, stream=None):
+        """fse_moment_vjp: dL/dI (float32, laid out like pix) for v = dL/d(x0, y0,
+        e1, e2, sigma_w) (float32 [N, 5]) at the moment fixed point in moments."""
+        n = int(index.shape[0])
+        v = v.to(torch.float32).contiguous()
+        if v.shape != (n, 5):
+            raise TypeError("v must be [N, 5]")
+        if out is None:
+            out = torch.zeros(pix.numel(), dtype=torch.float32, device=pix.device)
+        self._check(load().fse_moment_vjp(self._h, _ptr(pix), _dtype_of(pix), _ptr(scale), _ptr(index), n,
+                                          _ptr(moments), mode, _ptr(v), _ptr(out), _ptr(status),
+                                          _stream(stream)))
+        return out
+
+    def moment_jvp(self, pix, index, moments, tangent, *, mode: int = FSE_MOM_ELLIP | FSE_MOM_SIGW_R50,
+                   scale=None, out=None, status=None, stream=None):
+        """fse_moment_jvp: d(x0, y0, e1, e2, sigma_w) (float32 [N, 5]) along the
+        pixel tangent (float32, laid out like pix)."""
+        n = int(index.shape[0])
+        tangent = tangent.to(torch.float32).contiguous()
+        if out is None:
+            out = torch.empty((n, 5), dtype=torch.float32, device=pix.device)
+        self._check(load().fse_moment_jvp(self._h, _ptr(pix), _dtype_of(pix), _ptr(scale), _ptr(index), n,
+                                          _ptr(moments), mode, _ptr(tangent), _ptr(out), _ptr(status),
+                                          _stream(stream)))
+        return out
+
     def fit_batch_host(self, pix: np.ndarray | torch.Tensor, index: np.ndarray | torch.Tensor, *,
                        scale=None, inv_var=None, opts=None, out=None, stream=None) -> np.ndarray:
         """fse_fit_batch_host: host buffers in, host results out (synchronous)."""
@@ -361,6 +394,14 @@ def fse_tuned_warps(ctx: Context, *a, **k):
 
 def fse_star_fit(ctx: Context, *a, **k):
     return ctx.star_fit(*a, **k)
+
+
+def fse_moment_vjp(ctx: Context, *a, **k):
+    return ctx.moment_vjp(*a, **k)
+
+
+def fse_moment_jvp(ctx: Context, *a, **k):
+    return ctx.moment_jvp(*a, **k)
 
 
 def fse_sersic_b(ctx: Context, *a, **k):

@@ -758,6 +758,64 @@ int fse_star_fit(fse_ctx* ctx, const void* pix, int dtype, const float* scale, c
     return FSE_OK;
 }
 
+static int moment_grad(fse_ctx* ctx, bool jvp, const void* pix, int dtype, const float* scale,
+                       const fse_stamp* idx, int64_t count, const fse_result* moments, int mode, const float* v,
+                       float* dpix, const float* tangent, float* dtheta, uint32_t* status, void* stream) {
+    if (!ctx) return FSE_EINVAL;
+    if (count < 0 || count > 0x7fffffffLL) return set_error(ctx, FSE_EINVAL, "count out of range");
+    if (dtype != FSE_F32 && dtype != FSE_BF16) return set_error(ctx, FSE_EINVAL, "unknown dtype %d", dtype);
+    if (mode & ~(FSE_MOM_ELLIP | FSE_MOM_SIGW_FIXED | FSE_MOM_SIGW_R50))
+        return set_error(ctx, FSE_EINVAL, "unknown mode bits 0x%x", mode);
+    if ((mode & FSE_MOM_SIGW_FIXED) && (mode & FSE_MOM_SIGW_R50))
+        return set_error(ctx, FSE_EINVAL, "FSE_MOM_SIGW_FIXED and FSE_MOM_SIGW_R50 exclude each other");
+    if (count == 0) return FSE_OK;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return set_error(ctx, FSE_ECUDA, "cannot select device %d", ctx->device);
+    const void* need[] = {pix, idx, moments, jvp ? static_cast<const void*>(tangent) : v,
+                          jvp ? static_cast<const void*>(dtheta) : dpix};
+    for (const void* q : need)
+        if (!q) return set_error(ctx, FSE_EINVAL, "a required array argument is NULL");
+    const void* dev_ptrs[] = {pix, idx, moments, v, dpix, tangent, dtheta, scale, status};
+    for (const void* q : dev_ptrs)
+        if (q && !is_device_ptr(q))
+            return set_error(ctx, FSE_EINVAL, "all array arguments must be device pointers");
+    fse::MomentGradArgs a;
+    memset(&a, 0, sizeof a);
+    a.pix = pix;
+    a.dtype = dtype;
+    a.scale = scale;
+    a.idx = idx;
+    a.count = count;
+    a.moments = moments;
+    a.mode = mode;
+    a.v = v;
+    a.dpix = dpix;
+    a.tangent = tangent;
+    a.dtheta = dtheta;
+    a.status = status;
+    a.queue = ctx->d_queue + (ctx->next_queue++ % kQueues);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "work counter reset");
+    e = fse::launch_moment_grad(a, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "moment gradient launch");
+    return FSE_OK;
+}
+
+int fse_moment_vjp(fse_ctx* ctx, const void* pix, int dtype, const float* scale, const fse_stamp* idx,
+                   int64_t count, const fse_result* moments, int mode, const float* v, float* dpix,
+                   uint32_t* status, void* stream) {
+    return moment_grad(ctx, false, pix, dtype, scale, idx, count, moments, mode, v, dpix, nullptr, nullptr,
+                       status, stream);
+}
+
+int fse_moment_jvp(fse_ctx* ctx, const void* pix, int dtype, const float* scale, const fse_stamp* idx,
+                   int64_t count, const fse_result* moments, int mode, const float* tangent, float* dtheta,
+                   uint32_t* status, void* stream) {
+    return moment_grad(ctx, true, pix, dtype, scale, idx, count, moments, mode, nullptr, nullptr, tangent,
+                       dtheta, status, stream);
+}
+
 int fse_sersic_b(fse_ctx* ctx, const double* n, double* b, double* db, int64_t count, void* stream) {
     if (!ctx) return FSE_EINVAL;
     if (count == 0) return FSE_OK;

@@ -97,6 +97,24 @@ struct StarArgs {
     unsigned int* queue;         // work counter (zeroed before launch)
 };
 
+// Arguments of the implicit-gradient kernel of the moment fixed point
+// (fse_moment_vjp / fse_moment_jvp).
+struct MomentGradArgs {
+    const void* pix;
+    int dtype;
+    const float* scale;
+    const fse_stamp* idx;
+    int64_t count;
+    const fse_result* moments;   // theta = (x0, y0, e1, e2, sigma_w), status, r50
+    int mode;                    // FSE_MOM_* bits
+    const float* v;              // VJP: count x 5 upstream gradients
+    float* dpix;                 // VJP: laid out like pix (fp32)
+    const float* tangent;        // JVP: laid out like pix (fp32); NULL selects the VJP
+    float* dtheta;               // JVP: count x 5
+    uint32_t* status;            // count, or NULL
+    unsigned int* queue;         // work counter (zeroed before launch)
+};
+
 // Number of nodes of the b(n) table and its range.
 constexpr double kBnLo = 0.125;
 constexpr double kBnStep = 1.0 / 512.0;
@@ -110,6 +128,8 @@ cudaError_t build_bn_table(cudaStream_t stream);
 cudaError_t eval_bn(const double* n, double* b, double* db, int64_t count, cudaStream_t stream);
 // Launches the estimator kernel; returns the launch error.
 cudaError_t launch_estimator(const LaunchArgs& a, cudaStream_t stream);
+// Launches the implicit-gradient kernel; returns the launch error.
+cudaError_t launch_moment_grad(const MomentGradArgs& a, cudaStream_t stream);
 // Launches the star-profile kernel; returns the launch error.
 cudaError_t launch_star(const StarArgs& a, cudaStream_t stream);
 // Launches the chi^2 / adjoint kernel; returns the launch error.

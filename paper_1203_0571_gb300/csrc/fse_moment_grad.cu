@@ -1,0 +1,542 @@
+// fse_moment_grad.cu -- implicit-function derivatives of the moment fixed
+// point (Secs. 2-3) with respect to the pixels: VJP (fse_moment_vjp) and JVP
+// (fse_moment_jvp).
+//
+// The moment iteration stops where its steps vanish.  With theta = (xc, yc,
+// g1, g2, sigma_w), t = pixel - centre, R^2 of Eq. A1, W = exp(-R^2/2 s^2) and
+// e_w = 2g/(1+g^2), that point solves F_k = sum_p I_p W m_k(t) = 0 with
+//   m_1 = t1, m_2 = t2                         zero centroid step (Eqs. 3-6)
+//   m_3 = (t1^2 - t2^2) - e_w1 (t1^2 + t2^2)   e^obs = e_w, where the step of
+//   m_4 = 2 t1 t2 - e_w2 (t1^2 + t2^2)         Eq. 9 vanishes
+//   m_5 = R^2 - s^2                            matched weight
+// so d theta / d I_p = -J^-1 W(p) m(p) with J_kl = sum_p I_p d(W m_k)/d theta_l.
+// Every m_k and every d R^2 / d theta_l is a polynomial of degree <= 2 in t,
+// so J is a fixed combination of the 15 weighted moments
+// M_ab = sum I W t1^a t2^b (a + b <= 4): one pass accumulates them, 25 lanes
+// assemble one entry of J each, and every lane solves the 5 x 5 system.
+// sigma_w from the start-up growth curve (r50 / sqrt(2 ln 2), Sec. 4.1) is
+// an explicit function of the pixels: it is piecewise constant in the three
+// regions of the crossing ring (inside the disc k-1, in ring k, outside),
+// found with the same exact fixed-point sums as the start-up.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "fse_device.cuh"
+#include "fse_internal.h"
+
+namespace fse {
+namespace {
+
+constexpr float kInvSqrt2Ln2F = 0.849321800f;   // 1 / sqrt(2 ln 2)
+
+// Index of the monomial t1^a t2^b among the 15 of degree <= 4, by degree and
+// then by the power of t2.
+__host__ __device__ constexpr int mono(int a, int b) { return (a + b) * (a + b + 1) / 2 + b; }
+// The six monomials of degree <= 2: 1, t1, t2, t1^2, t1 t2, t2^2.
+__host__ __device__ constexpr int pa(int i) { return i == 1 || i == 3 || i == 4 ? (i == 3 ? 2 : 1) : 0; }
+__host__ __device__ constexpr int pb(int i) { return i == 2 || i == 4 || i == 5 ? (i == 5 ? 2 : 1) : 0; }
+
+template <int DT>
+__device__ __forceinline__ float load_pix(const MomentGradArgs& a, int64_t off, float sc) {
+    return DT == FSE_BF16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(a.pix)[off]) * sc
+                          : __ldg(static_cast<const float*>(a.pix) + off);
+}
+
+// Stamp geometry at theta.
+struct Geom {
+    float x0, y0, g1, g2, s;
+    float A, B, G4, cw;      // R^2 = A t1^2 + B t2^2 - G4 t1 t2; W = 2^(cw R^2)
+};
+
+// Polynomial factors of degree <= 2 (coefficients of 1, t1, t2, t1^2, t1 t2,
+// t2^2) for J_kl = sum I W [a_l m_k + dm_k/dtheta_l]: m_k, a_l (the derivative
+// of log W: -R^2_l / 2 s^2, or R^2 / s^3 for sigma_w) and dm_k/dtheta_l.
+__device__ void jac_polys(const Geom& q, int k, int l, float mk[6], float al[6], float dm[6]) {
+    const float g1 = q.g1, g2 = q.g2, s = q.s, gg = g1 * g1 + g2 * g2;
+    const float ew1 = 2.f * g1 / (1.f + gg), ew2 = 2.f * g2 / (1.f + gg);
+    const float qq = (1.f + gg) * (1.f + gg);
+    const float dew[2][2] = {{2.f * (1.f - g1 * g1 + g2 * g2) / qq, -4.f * g1 * g2 / qq},
+                             {-4.f * g1 * g2 / qq, 2.f * (1.f + g1 * g1 - g2 * g2) / qq}};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) mk[i] = al[i] = dm[i] = 0.f;
+    // d R^2 / d theta_l
+    float du[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (l == 0) { du[1] = -2.f * q.A; du[2] = q.G4; }
+    if (l == 1) { du[1] = q.G4; du[2] = -2.f * q.B; }
+    if (l == 2) { du[3] = 2.f * (g1 - 1.f); du[5] = 2.f * (g1 + 1.f); }
+    if (l == 3) { du[3] = 2.f * g2; du[4] = -4.f; du[5] = 2.f * g2; }
+    const float c = 1.f / (2.f * s * s);
+    if (l < 4) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) al[i] = -c * du[i];
+    } else {
+        const float is3 = 1.f / (s * s * s);
+        al[3] = q.A * is3; al[4] = -q.G4 * is3; al[5] = q.B * is3;
+    }
+    if (k == 0) { mk[1] = 1.f; if (l == 0) dm[0] = -1.f; }
+    if (k == 1) { mk[2] = 1.f; if (l == 1) dm[0] = -1.f; }
+    if (k == 2) {
+        mk[3] = 1.f - ew1; mk[5] = -(1.f + ew1);
+        if (l == 0) dm[1] = -2.f * (1.f - ew1);
+        if (l == 1) dm[2] = 2.f * (1.f + ew1);
+        if (l == 2 || l == 3) { dm[3] = dm[5] = -dew[0][l - 2]; }
+    }
+    if (k == 3) {
+        mk[3] = -ew2; mk[4] = 2.f; mk[5] = -ew2;
+        if (l == 0) { dm[1] = 2.f * ew2; dm[2] = -2.f; }
+        if (l == 1) { dm[1] = -2.f; dm[2] = 2.f * ew2; }
+        if (l == 2 || l == 3) { dm[3] = dm[5] = -dew[1][l - 2]; }
+    }
+    if (k == 4) {
+        mk[0] = -s * s; mk[3] = q.A; mk[4] = -q.G4; mk[5] = q.B;
+        if (l < 4) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) dm[i] = du[i];
+        } else {
+            dm[0] = -2.f * s;
+        }
+    }
+}
+
+// One entry of J from the 15 moments (hi + lo pairs).  The combination
+// cancels by up to an order of magnitude (e.g. J_55 = sum I W [R^2 (R^2 - s^2)
+// / s^3 - 2 s]), so it is summed in fp64: once per stamp, 42 terms per lane.
+__device__ float jac_entry(const Geom& q, int k, int l, const float Mh[15], const float Ml[15]) {
+    float mk[6], al[6], dm[6];
+    jac_polys(q, k, l, mk, al, dm);
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const int a = mono(pa(i), pb(i));
+        acc = fma(static_cast<double>(dm[i]), static_cast<double>(Mh[a]) + static_cast<double>(Ml[a]), acc);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            const int b = mono(pa(i) + pa(j), pb(i) + pb(j));
+            acc = fma(static_cast<double>(al[i]) * static_cast<double>(mk[j]),
+                      static_cast<double>(Mh[b]) + static_cast<double>(Ml[b]), acc);
+        }
+    }
+    return static_cast<float>(acc);
+}
+
+// Solve X x = r for 5 x 5 X (row-major) by Gaussian elimination with partial
+// pivoting, every index known at compile time.  Returns false if a pivot is
+// below 1e-6 of the largest entry.
+__device__ bool solve5(float X[25], float r[5], float x[5]) {
+    float big = 0.f;
+#pragma unroll
+    for (int i = 0; i < 25; ++i) big = fmaxf(big, fabsf(X[i]));
+    if (!(big > 0.f)) return false;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        int piv = c;
+        float pv = fabsf(X[c * 5 + c]);
+#pragma unroll
+        for (int rr = c + 1; rr < 5; ++rr)
+            if (fabsf(X[rr * 5 + c]) > pv) { pv = fabsf(X[rr * 5 + c]); piv = rr; }
+        if (!(pv > 1e-6f * big)) return false;
+#pragma unroll
+        for (int rr = c + 1; rr < 5; ++rr) {
+            if (rr == piv) {
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    const float t = X[c * 5 + k];
+                    X[c * 5 + k] = X[rr * 5 + k];
+                    X[rr * 5 + k] = t;
+                }
+                const float t = r[c];
+                r[c] = r[rr];
+                r[rr] = t;
+            }
+        }
+        const float inv = 1.f / X[c * 5 + c];
+#pragma unroll
+        for (int rr = c + 1; rr < 5; ++rr) {
+            const float f = X[rr * 5 + c] * inv;
+#pragma unroll
+            for (int k = c; k < 5; ++k) X[rr * 5 + k] = fmaf(-f, X[c * 5 + k], X[rr * 5 + k]);
+            r[rr] = fmaf(-f, r[c], r[rr]);
+        }
+    }
+#pragma unroll
+    for (int rr = 4; rr >= 0; --rr) {
+        float acc = r[rr];
+#pragma unroll
+        for (int k = rr + 1; k < 5; ++k) acc = fmaf(-X[rr * 5 + k], x[k], acc);
+        x[rr] = acc / X[rr * 5 + rr];
+    }
+    return true;
+}
+
+// The growth curve of the start-up (Sec. 4.1) around the brightest pixel, in
+// the same exact fixed-point sums: the crossing ring k (the first whose
+// enclosed sum reaches half the total) and the constants of d sigma_w / d I_p
+// in the three regions d <= k-1, k-1 < d <= k, d > k.
+struct R50Grad {
+    bool on;                 // sigma_w depends on the pixels
+    int pr, pc, k;
+    float c_in, c_ring, c_out;
+};
+
+template <int DT>
+__device__ R50Grad r50_grad(const MomentGradArgs& a, const fse_stamp& ix, int npix, float sc, float r50_hint,
+                            int lane, bool& finite) {
+    R50Grad o;
+    o.on = false;
+    o.pr = o.pc = o.k = 0;
+    o.c_in = o.c_ring = o.c_out = 0.f;
+    float vmax = -INFINITY, amax = 0.f;
+    int imax = 0x7fffffff;
+    bool fin = true;
+    for (int p = lane; p < npix; p += 32) {
+        const float v = load_pix<DT>(a, ix.offset + p, sc);
+        fin = fin && isfinite(v);
+        if (v > vmax) { vmax = v; imax = p; }
+        amax = fmaxf(amax, fabsf(v));
+    }
+    finite = __all_sync(kFull, fin);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float ov = __shfl_xor_sync(kFull, vmax, off);
+        const int oi = __shfl_xor_sync(kFull, imax, off);
+        if (ov > vmax || (ov == vmax && oi < imax)) { vmax = ov; imax = oi; }
+        amax = fmaxf(amax, __shfl_xor_sync(kFull, amax, off));
+    }
+    if (!finite) return o;
+    o.pr = imax / ix.w;
+    o.pc = imax - o.pr * ix.w;
+    int e;
+    frexpf(amax * static_cast<float>(npix), &e);
+    int S = 62 - e;
+    S = S > 100 ? 100 : (S < -100 ? -100 : S);
+    const float fs = ldexpf(1.f, S);
+    // candidate ring from the start-up radius: r50 = (k-1) + frac, frac in (0, 1]
+    int k = r50_hint > 0.5f ? static_cast<int>(ceilf(r50_hint)) : 0;
+    long long tot = 0, ein = 0, ek = 0;
+    bool found = false;
+    for (int tries = 0; tries < 8 && !found; ++tries) {
+        long long t = 0, e0 = 0, e1 = 0;
+        PixelWalk pw(lane, ix.w);
+        for (int p = lane; p < npix; p += 32) {
+            const long long qv = __float2ll_rn(load_pix<DT>(a, ix.offset + p, sc) * fs);
+            const int di = pw.row - o.pr, dj = pw.col - o.pc;
+            const int d2 = di * di + dj * dj;
+            pw.next();
+            t += qv;
+            if (k >= 1 && d2 <= (k - 1) * (k - 1)) e0 += qv;
+            if (d2 <= k * k) e1 += qv;
+        }
+        t = warp_allsum_ll(t);
+        e0 = warp_allsum_ll(e0);
+        e1 = warp_allsum_ll(e1);
+        tot = t;
+        if (tot <= 0) return o;                  // fallback radius: no dependence
+        if (2 * e1 < tot) {
+            ++k;
+        } else if (k >= 1 && 2 * e0 >= tot) {
+            --k;
+        } else {
+            found = true;
+            ein = e0;
+            ek = e1;
+        }
+    }
+    if (!found) return o;
+    o.k = k;
+    o.on = true;
+    if (k == 0) {
+        // r50 = H / (2 S) with S the brightest pixel
+        const float Sf = static_cast<float>(ek) / fs, H = 0.5f * static_cast<float>(tot) / fs;
+        o.c_ring = 0.5f * (0.5f * Sf - H) / (Sf * Sf) * kInvSqrt2Ln2F;
+        o.c_out = 0.25f / Sf * kInvSqrt2Ln2F;
+        o.c_in = 0.f;
+    } else {
+        // r50 = (k-1) + (H - P) / (S - P), differences taken exactly in integers
+        const float D = static_cast<float>(ek - ein) / fs;
+        const float HP = 0.5f * static_cast<float>(tot - 2 * ein) / fs;
+        o.c_out = 0.5f / D * kInvSqrt2Ln2F;
+        o.c_ring = (0.5f * D - HP) / (D * D) * kInvSqrt2Ln2F;
+        o.c_in = -0.5f / D * kInvSqrt2Ln2F;
+    }
+    return o;
+}
+
+// One warp per stamp.  JVP = true: dtheta along a.tangent; false: the pixel
+// gradient for a.v.
+template <int DT, bool JVP>
+__global__ void __launch_bounds__(256) moment_grad_kernel(MomentGradArgs a) {
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned sidx = 0;
+        if (lane == 0) sidx = atomicAdd(a.queue, 1u);
+        sidx = __shfl_sync(kFull, sidx, 0);
+        if (sidx >= static_cast<unsigned long long>(a.count)) break;
+        const int64_t si = static_cast<int64_t>(sidx);
+        const fse_stamp ix = a.idx[si];
+        const fse_result mom = a.moments[si];
+        uint32_t status = 0;
+        const long long npl = static_cast<long long>(ix.h) * ix.w;
+        if (ix.h < 1 || ix.w < 1 || npl > FSE_MAX_PIX) {
+            if (lane == 0 && a.status) a.status[si] = FSE_ST_BAD_SIZE;
+            if (JVP && lane < 5) a.dtheta[si * 5 + lane] = 0.f;
+            continue;
+        }
+        const int npix = static_cast<int>(npl);
+        if (!(mom.status & FSE_ST_MOM_CONVERGED)) status |= FSE_ST_MOM_FAILED;
+        const bool ellip = (a.mode & FSE_MOM_ELLIP) != 0;
+        const bool sig_held = (a.mode & FSE_MOM_SIGW_FIXED) || (mom.status & FSE_ST_SIGW_CLAMPED);
+        const bool sig_r50 = !sig_held && (a.mode & FSE_MOM_SIGW_R50);
+        const float sc = (DT == FSE_BF16 && a.scale) ? a.scale[si] : 1.f;
+        Geom q;
+        q.x0 = mom.x0;
+        q.y0 = mom.y0;
+        q.g1 = ellip ? mom.e1 : 0.f;
+        q.g2 = ellip ? mom.e2 : 0.f;
+        q.s = mom.sigma_w;
+        {
+            const float gg = q.g1 * q.g1 + q.g2 * q.g2;
+            q.A = 1.f + gg - 2.f * q.g1;
+            q.B = 1.f + gg + 2.f * q.g1;
+            q.G4 = 4.f * q.g2;
+            q.cw = -kLog2e / (2.f * q.s * q.s);
+        }
+        if (!(q.s > 0.f) || !isfinite(q.cw)) status |= FSE_ST_MOM_FAILED;
+        bool finite = true;
+        R50Grad rg;
+        rg.on = false;
+        rg.pr = rg.pc = rg.k = 0;
+        rg.c_in = rg.c_ring = rg.c_out = 0.f;
+        if (status == 0 && sig_r50) rg = r50_grad<DT>(a, ix, npix, sc, mom.r50, lane, finite);
+        // weighted moments (and, for the JVP, the tangent's sums)
+        float Mh[15], Ml[15], Uh[9], Ul[9];
+#pragma unroll
+        for (int i = 0; i < 15; ++i) Mh[i] = Ml[i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Uh[i] = Ul[i] = 0.f;
+        if (status == 0 && finite) {
+            PixelWalk pw(lane, ix.w);
+            bool fin = true;
+            for (int p0 = lane; p0 < npix; p0 += 256) {
+                float P[15], PU[9];
+#pragma unroll
+                for (int i = 0; i < 15; ++i) P[i] = 0.f;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) PU[i] = 0.f;
+                float v[8], uu[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int p = p0 + 32 * u;
+                    v[u] = p < npix ? load_pix<DT>(a, ix.offset + p, sc) : 0.f;
+                    if (JVP) uu[u] = p < npix ? __ldg(a.tangent + ix.offset + p) : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int p = p0 + 32 * u;
+                    if (p < npix) {
+                        const float t1 = static_cast<float>(pw.col) - q.x0;
+                        const float t2 = static_cast<float>(pw.row) - q.y0;
+                        const int di = pw.row - rg.pr, dj = pw.col - rg.pc;
+                        pw.next();
+                        fin = fin && isfinite(v[u]);
+                        const float R2 = fmaf(q.A, t1 * t1, fmaf(q.B, t2 * t2, -q.G4 * (t1 * t2)));
+                        const float W = ex2(fmaxf(R2, 0.f) * q.cw);
+                        const float f = v[u] * W;
+                        const float f1 = f * t1, f2 = f * t2;
+                        const float f11 = f1 * t1, f12 = f1 * t2, f22 = f2 * t2;
+                        const float f111 = f11 * t1, f112 = f11 * t2, f122 = f12 * t2, f222 = f22 * t2;
+                        P[mono(0, 0)] += f;
+                        P[mono(1, 0)] += f1;
+                        P[mono(0, 1)] += f2;
+                        P[mono(2, 0)] += f11;
+                        P[mono(1, 1)] += f12;
+                        P[mono(0, 2)] += f22;
+                        P[mono(3, 0)] += f111;
+                        P[mono(2, 1)] += f112;
+                        P[mono(1, 2)] += f122;
+                        P[mono(0, 3)] += f222;
+                        P[mono(4, 0)] = fmaf(f111, t1, P[mono(4, 0)]);
+                        P[mono(3, 1)] = fmaf(f111, t2, P[mono(3, 1)]);
+                        P[mono(2, 2)] = fmaf(f112, t2, P[mono(2, 2)]);
+                        P[mono(1, 3)] = fmaf(f122, t2, P[mono(1, 3)]);
+                        P[mono(0, 4)] = fmaf(f222, t2, P[mono(0, 4)]);
+                        if (JVP) {
+                            fin = fin && isfinite(uu[u]);
+                            const float h = uu[u] * W;
+                            const float h1 = h * t1, h2 = h * t2;
+                            PU[0] += h;
+                            PU[1] += h1;
+                            PU[2] += h2;
+                            PU[3] = fmaf(h1, t1, PU[3]);
+                            PU[4] = fmaf(h1, t2, PU[4]);
+                            PU[5] = fmaf(h2, t2, PU[5]);
+                            // tangent over the growth-curve regions: all, disc k, disc k-1
+                            const int d2 = di * di + dj * dj;
+                            PU[6] += uu[u];
+                            if (d2 <= rg.k * rg.k) PU[7] += uu[u];
+                            if (rg.k >= 1 && d2 <= (rg.k - 1) * (rg.k - 1)) PU[8] += uu[u];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 15; ++i) df_add(Mh[i], Ml[i], P[i]);
+                if (JVP) {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) df_add(Uh[i], Ul[i], PU[i]);
+                }
+            }
+            finite = __all_sync(kFull, fin);
+        }
+        if (!finite) status |= FSE_ST_NONFINITE;
+        float Su[9];
+        if (status == 0) {
+            warp_allsum_df(Mh, Ml);
+            if (JVP) {
+                warp_allsum_df(Uh, Ul);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) Su[i] = Uh[i] + Ul[i];
+            }
+        }
+        // J: lane 5k + l assembles J_kl; then every lane holds all 25
+        float X[25], xs[5], rhs[5];
+        bool solved = false;
+        float Jcol4[5];
+        if (status == 0) {
+            const int k = lane < 25 ? lane / 5 : 0, l = lane < 25 ? lane - 5 * (lane / 5) : 0;
+            const float mine = jac_entry(q, k, l, Mh, Ml);
+#pragma unroll
+            for (int i = 0; i < 25; ++i) X[i] = __shfl_sync(kFull, mine, i);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) Jcol4[i] = X[i * 5 + 4];
+            // held parameters: rows and columns of a diagonal entry as large
+            // as the active block's largest, with a zero right-hand side
+            bool act[5] = {true, true, ellip, ellip, !(sig_held || sig_r50)};
+            float big = 0.f;
+#pragma unroll
+            for (int i = 0; i < 5; ++i)
+#pragma unroll
+                for (int j = 0; j < 5; ++j)
+                    if (act[i] && act[j]) big = fmaxf(big, fabsf(X[i * 5 + j]));
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                if (!act[i]) {
+#pragma unroll
+                    for (int j = 0; j < 5; ++j) X[i * 5 + j] = X[j * 5 + i] = 0.f;
+                    X[i * 5 + i] = big;
+                }
+            }
+            if (JVP) {
+                // rhs = -(sum u psi + J_as dsigma_w); psi_k = W m_k
+                float dsw = 0.f;
+                if (rg.on)
+                    dsw = rg.c_out * Su[6] + (rg.c_ring - rg.c_out) * Su[7] + (rg.c_in - rg.c_ring) * Su[8];
+                const float ew1 = 2.f * q.g1 / (1.f + q.g1 * q.g1 + q.g2 * q.g2);
+                const float ew2 = 2.f * q.g2 / (1.f + q.g1 * q.g1 + q.g2 * q.g2);
+                float S5[5];
+                S5[0] = Su[1];
+                S5[1] = Su[2];
+                S5[2] = (1.f - ew1) * Su[3] - (1.f + ew1) * Su[5];
+                S5[3] = 2.f * Su[4] - ew2 * (Su[3] + Su[5]);
+                S5[4] = q.A * Su[3] - q.G4 * Su[4] + q.B * Su[5] - q.s * q.s * Su[0];
+#pragma unroll
+                for (int i = 0; i < 5; ++i) rhs[i] = act[i] ? -(S5[i] + Jcol4[i] * dsw) : 0.f;
+                solved = solve5(X, rhs, xs);
+                if (solved && rg.on) xs[4] = dsw;
+            } else {
+                // transpose for J^T lambda = v
+#pragma unroll
+                for (int i = 0; i < 5; ++i)
+#pragma unroll
+                    for (int j = i + 1; j < 5; ++j) {
+                        const float t = X[i * 5 + j];
+                        X[i * 5 + j] = X[j * 5 + i];
+                        X[j * 5 + i] = t;
+                    }
+#pragma unroll
+                for (int i = 0; i < 5; ++i) rhs[i] = act[i] ? a.v[si * 5 + i] : 0.f;
+                solved = solve5(X, rhs, xs);
+            }
+            if (!solved) status |= FSE_ST_FIT_SINGULAR;
+        }
+        if (JVP) {
+            float val = 0.f;
+#pragma unroll
+            for (int i = 0; i < 5; ++i)
+                if (lane == i && status == 0) val = xs[i];
+            if (lane < 5) a.dtheta[si * 5 + lane] = val;
+        } else {
+            // dL/dI_p = -W(p) sum_k lambda_k m_k(p) + kappa d sigma_w / d I_p
+            float c[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float kc_in = 0.f, kc_ring = 0.f, kc_out = 0.f;
+            if (status == 0) {
+                const float gg = q.g1 * q.g1 + q.g2 * q.g2;
+                const float ew1 = 2.f * q.g1 / (1.f + gg), ew2 = 2.f * q.g2 / (1.f + gg);
+                c[0] = -xs[4] * q.s * q.s;
+                c[1] = xs[0];
+                c[2] = xs[1];
+                c[3] = xs[2] * (1.f - ew1) - xs[3] * ew2 + xs[4] * q.A;
+                c[4] = 2.f * xs[3] - xs[4] * q.G4;
+                c[5] = -xs[2] * (1.f + ew1) - xs[3] * ew2 + xs[4] * q.B;
+                if (rg.on) {
+                    float kappa = a.v[si * 5 + 4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) kappa = fmaf(-xs[i], Jcol4[i], kappa);
+                    kc_in = kappa * rg.c_in;
+                    kc_ring = kappa * rg.c_ring;
+                    kc_out = kappa * rg.c_out;
+                }
+            }
+            PixelWalk pw(lane, ix.w);
+            for (int p = lane; p < npix; p += 32) {
+                float g = 0.f;
+                if (status == 0) {
+                    const float t1 = static_cast<float>(pw.col) - q.x0;
+                    const float t2 = static_cast<float>(pw.row) - q.y0;
+                    const float R2 = fmaf(q.A, t1 * t1, fmaf(q.B, t2 * t2, -q.G4 * (t1 * t2)));
+                    const float W = ex2(fmaxf(R2, 0.f) * q.cw);
+                    const float Q = fmaf(t1, fmaf(c[3], t1, fmaf(c[4], t2, c[1])), fmaf(t2, fmaf(c[5], t2, c[2]), c[0]));
+                    g = -W * Q;
+                    if (rg.on) {
+                        const int di = pw.row - rg.pr, dj = pw.col - rg.pc;
+                        const int d2 = di * di + dj * dj;
+                        g += d2 <= (rg.k - 1) * (rg.k - 1) && rg.k >= 1 ? kc_in : (d2 <= rg.k * rg.k ? kc_ring : kc_out);
+                    }
+                }
+                pw.next();
+                __stcs(a.dpix + ix.offset + p, g);
+            }
+        }
+        if (lane == 0 && a.status) a.status[si] = status;
+    }
+}
+
+template <int DT, bool JVP>
+cudaError_t launch_t(const MomentGradArgs& a, cudaStream_t stream) {
+    auto kern = moment_grad_kernel<DT, JVP>;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long grid = static_cast<long long>(per_sm) * sms;
+    const long long need = (a.count + 7) / 8;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    kern<<<static_cast<unsigned>(grid), 256, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_moment_grad(const MomentGradArgs& a, cudaStream_t stream) {
+    if (a.count <= 0) return cudaSuccess;
+    const bool jvp = a.tangent != nullptr;
+    if (a.dtype == FSE_BF16) return jvp ? launch_t<FSE_BF16, true>(a, stream) : launch_t<FSE_BF16, false>(a, stream);
+    return jvp ? launch_t<FSE_F32, true>(a, stream) : launch_t<FSE_F32, false>(a, stream);
+}
+
+}  // namespace fse

@@ -1,6 +1,6 @@
 """A small, self-contained launch of libfse for profiler captures.
 
-    python -m paper_1203_0571_gb300.profile_case [--what fit_batch|adjoint|star]
+    python -m paper_1203_0571_gb300.profile_case [--what fit_batch|adjoint|star|moment_vjp|moment_jvp]
         [--profile gauss|moffat] [--workload 1] [--stamps 20000] [--warmup 3] [--launches 1]
 
 Generates the first `stamps` stamps of a synthetic workload on the GPU, runs
@@ -8,7 +8,10 @@ Generates the first `stamps` stamps of a synthetic workload on the GPU, runs
 fit_batch runs the whole chain; adjoint runs fse_sersic_chi2_grad at the
 generating parameters with the pixel gradient (the backward launch of the
 autograd bridge); star runs fse_star_fit (Sec. 4.2) at the centre and
-ellipticity of a preceding fse_centroid + fse_ellipticity.  The inputs of the
+ellipticity of a preceding fse_centroid + fse_ellipticity; moment_vjp and
+moment_jvp run the implicit gradients of that fixed point (sigma_w from the
+growth curve), on 100,000 stamps of 48x48 (922 MB read; the VJP writes as
+much).  The inputs of the
 default cases (20,000 stamps of 48x48 fp32, 184 MB; for the adjoint, 16,384
 stamps of 64x64, 268 MB; for the stars, 50,000 Gaussian stars of 32x32, 205
 MB, or 50,000 Moffat stars of 48x48, 461 MB) are larger than the 129 MB L2,
@@ -27,8 +30,11 @@ from . import synth
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--what", choices=["fit_batch", "adjoint", "star"], default="fit_batch")
+    ap.add_argument("--what", choices=["fit_batch", "adjoint", "star", "moment_vjp", "moment_jvp"],
+                    default="fit_batch")
     ap.add_argument("--profile", choices=["gauss", "moffat"], default="gauss")
+    ap.add_argument("--sigw", choices=["r50", "matched", "fixed"], default="r50",
+                    help="sigma_w rule of the implicit gradients (moment_vjp, moment_jvp)")
     ap.add_argument("--workload", type=int, default=None)
     ap.add_argument("--stamps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
@@ -38,6 +44,10 @@ def main():
     if args.what == "adjoint":
         return adjoint(ctx, args.workload if args.workload is not None else 3,
                        args.stamps if args.stamps is not None else 16384, args.warmup, args.launches)
+    if args.what in ("moment_vjp", "moment_jvp"):
+        return moment_grad(ctx, args.what == "moment_jvp", args.workload if args.workload is not None else 1,
+                           args.stamps if args.stamps is not None else 100000, args.warmup, args.launches,
+                           args.sigw)
     if args.what == "star":
         return star(ctx, args.profile, args.workload if args.workload is not None else
                     (6 if args.profile == "gauss" else 7),
@@ -105,6 +115,39 @@ def star(ctx, profile, workload, stamps, warmup, launches):
     print(json.dumps({"stamps": batch.count, "pixels": batch.pix.numel(), "profile": profile,
                       "ms_per_launch": a.elapsed_time(b) / launches, "converged": float(conv.mean()),
                       "passes": int(r["iters"][conv].sum()), "passes_mean": float(r["iters"][conv].mean())}))
+
+
+def moment_grad(ctx, jvp, workload, stamps, warmup, launches, sigw):
+    batch = synth.make_workload(workload, count=stamps, device="cuda")
+    idx = B.make_index(batch.offset, batch.h, batch.w)
+    opts = B.default_opts(max_pix=int((batch.h.long() * batch.w.long()).max()),
+                          sigw_mode=1 if sigw == "r50" else 0)
+    mode = B.FSE_MOM_ELLIP | {"r50": B.FSE_MOM_SIGW_R50, "matched": 0, "fixed": B.FSE_MOM_SIGW_FIXED}[sigw]
+    mom = ctx.centroid(batch.pix, idx, opts=opts)
+    ctx.ellipticity(batch.pix, idx, mom, opts=opts)
+    g = torch.Generator(device="cuda").manual_seed(1)
+    st = torch.zeros(batch.count, dtype=torch.int32, device="cuda")
+    if jvp:
+        arg = torch.randn(batch.pix.numel(), generator=g, device="cuda")
+        out = torch.empty((batch.count, 5), dtype=torch.float32, device="cuda")
+        call = lambda: ctx.moment_jvp(batch.pix, idx, mom, arg, out=out, status=st, mode=mode)
+    else:
+        arg = torch.randn((batch.count, 5), generator=g, device="cuda")
+        out = torch.empty(batch.pix.numel(), dtype=torch.float32, device="cuda")
+        call = lambda: ctx.moment_vjp(batch.pix, idx, mom, arg, out=out, status=st, mode=mode)
+    for _ in range(warmup):
+        call()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(launches):
+        call()
+    b.record()
+    ctx.sync_check()
+    print(json.dumps({"stamps": batch.count, "pixels": batch.pix.numel(), "what": "jvp" if jvp else "vjp",
+                      "sigw": sigw,
+                      "ms_per_launch": a.elapsed_time(b) / launches,
+                      "status_zero": float((st == 0).float().mean())}))
 
 
 if __name__ == "__main__":

@@ -22,7 +22,7 @@ ABS = {"x0", "y0", "e1", "e2"}
 MOM_CONVERGED, FIT_CONVERGED, FIT_BOUND = 1, 2, 128
 
 
-def oracle_results(O, batch, ids, stage="measure", init=None, ivar=None, threads=0):
+def oracle_results(O, batch, ids, stage="measure", init=None, ivar=None, threads=0, opts=None):
     """Oracle results for stamps `ids` of a StampBatch (pixels decoded to fp32 as the kernel does)."""
     offs, hs, ws, chunks, ivs = [], [], [], [], []
     pos = 0
@@ -39,7 +39,7 @@ def oracle_results(O, batch, ids, stage="measure", init=None, ivar=None, threads
     pix = np.concatenate(chunks) if chunks else np.zeros(0, np.float32)
     iv = np.concatenate(ivs).astype(np.float32) if ivar is not None else None
     res, _ = O.batch(pix, np.array(offs), np.array(hs), np.array(ws), stage=stage, init=init,
-                     ivar=iv, threads=threads)
+                     ivar=iv, threads=threads, opts=opts)
     return res
 
 
