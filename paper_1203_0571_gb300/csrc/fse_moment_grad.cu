@@ -17,7 +17,7 @@
 // sigma_w from the start-up growth curve (r50 / sqrt(2 ln 2), Sec. 4.1) is
 // an explicit function of the pixels: it is piecewise constant in the three
 // regions of the crossing ring (inside the disc k-1, in ring k, outside),
-// found with the same exact fixed-point sums as the start-up.
+// found from double-float disc sums around the brightest pixel.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -48,6 +48,28 @@ __device__ __forceinline__ float load_pix(const MomentGradArgs& a, int64_t off, 
 struct Geom {
     float x0, y0, g1, g2, s;
     float A, B, G4, cw;      // R^2 = A t1^2 + B t2^2 - G4 t1 t2; W = 2^(cw R^2)
+};
+
+// Pixel coordinates of p = t, t + 32, ... of a w-wide stamp as floats.  They
+// are integers, so every step is exact, and so is t = coordinate - centre.
+struct FWalk {
+    float c, r, dc, dr, wf;
+    __device__ FWalk(int t, int w) {
+        const int row = t / w;
+        c = static_cast<float>(t - row * w);
+        r = static_cast<float>(row);
+        dr = static_cast<float>(32 / w);
+        dc = static_cast<float>(32 - (32 / w) * w);
+        wf = static_cast<float>(w);
+    }
+    __device__ __forceinline__ void next() {
+        c += dc;
+        r += dr;
+        if (c >= wf) {
+            c -= wf;
+            r += 1.f;
+        }
+    }
 };
 
 // Polynomial factors of degree <= 2 (coefficients of 1, t1, t2, t1^2, t1 t2,
@@ -100,25 +122,44 @@ __device__ void jac_polys(const Geom& q, int k, int l, float mk[6], float al[6],
     }
 }
 
+// Double-float helpers: the exact product error by FMA, Knuth's two-sum.
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+
+__device__ __forceinline__ void df_acc(float& hi, float& lo, float p, float e) {
+    const float s = hi + p;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (p - bb);
+    hi = s;
+    lo += err + e;
+}
+
 // One entry of J from the 15 moments (hi + lo pairs).  The combination
 // cancels by up to an order of magnitude (e.g. J_55 = sum I W [R^2 (R^2 - s^2)
-// / s^3 - 2 s]), so it is summed in fp64: once per stamp, 42 terms per lane.
+// / s^3 - 2 s]), so each coefficient, product and partial sum is carried in
+// double-float: once per stamp, 42 terms per lane.
 __device__ float jac_entry(const Geom& q, int k, int l, const float Mh[15], const float Ml[15]) {
     float mk[6], al[6], dm[6];
     jac_polys(q, k, l, mk, al, dm);
-    double acc = 0.0;
+    float hi = 0.f, lo = 0.f;
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         const int a = mono(pa(i), pb(i));
-        acc = fma(static_cast<double>(dm[i]), static_cast<double>(Mh[a]) + static_cast<double>(Ml[a]), acc);
+        float p, e;
+        two_prod(dm[i], Mh[a], p, e);
+        df_acc(hi, lo, p, fmaf(dm[i], Ml[a], e));
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
             const int b = mono(pa(i) + pa(j), pb(i) + pb(j));
-            acc = fma(static_cast<double>(al[i]) * static_cast<double>(mk[j]),
-                      static_cast<double>(Mh[b]) + static_cast<double>(Ml[b]), acc);
+            float ch, cl;
+            two_prod(al[i], mk[j], ch, cl);
+            two_prod(ch, Mh[b], p, e);
+            df_acc(hi, lo, p, fmaf(ch, Ml[b], fmaf(cl, Mh[b], e)));
         }
     }
-    return static_cast<float>(acc);
+    return hi + lo;
 }
 
 // Solve X x = r for 5 x 5 X (row-major) by Gaussian elimination with partial
@@ -170,103 +211,140 @@ __device__ bool solve5(float X[25], float r[5], float x[5]) {
     return true;
 }
 
-// The growth curve of the start-up (Sec. 4.1) around the brightest pixel, in
-// the same exact fixed-point sums: the crossing ring k (the first whose
-// enclosed sum reaches half the total) and the constants of d sigma_w / d I_p
-// in the three regions d <= k-1, k-1 < d <= k, d > k.
+// The growth curve of the start-up (Sec. 4.1) around the brightest pixel:
+// the crossing ring k (the first whose enclosed sum reaches half the total)
+// and the constants of d sigma_w / d I_p in the three regions d <= k-1,
+// k-1 < d <= k and d > k.  The disc sums are double-float, so k is the
+// start-up's own except where an enclosed sum lies within ~1e-13 of half the
+// total.  For the JVP the tangent's sums over the two discs come with them.
 struct R50Grad {
     bool on;                 // sigma_w depends on the pixels
     int pr, pc, k;
     float c_in, c_ring, c_out;
+    float u_in, u_disc;      // JVP: tangent summed over d <= k-1 and d <= k
 };
 
-template <int DT>
-__device__ R50Grad r50_grad(const MomentGradArgs& a, const fse_stamp& ix, int npix, float sc, float r50_hint,
-                            int lane, bool& finite) {
+template <int DT, bool JVP>
+__device__ R50Grad r50_ring(const MomentGradArgs& a, const fse_stamp& ix, int npix, float sc, float r50_hint,
+                            int peak, float tot_h, float tot_l, int lane) {
     R50Grad o;
     o.on = false;
-    o.pr = o.pc = o.k = 0;
-    o.c_in = o.c_ring = o.c_out = 0.f;
-    float vmax = -INFINITY, amax = 0.f;
-    int imax = 0x7fffffff;
-    bool fin = true;
-    for (int p = lane; p < npix; p += 32) {
-        const float v = load_pix<DT>(a, ix.offset + p, sc);
-        fin = fin && isfinite(v);
-        if (v > vmax) { vmax = v; imax = p; }
-        amax = fmaxf(amax, fabsf(v));
-    }
-    finite = __all_sync(kFull, fin);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const float ov = __shfl_xor_sync(kFull, vmax, off);
-        const int oi = __shfl_xor_sync(kFull, imax, off);
-        if (ov > vmax || (ov == vmax && oi < imax)) { vmax = ov; imax = oi; }
-        amax = fmaxf(amax, __shfl_xor_sync(kFull, amax, off));
-    }
-    if (!finite) return o;
-    o.pr = imax / ix.w;
-    o.pc = imax - o.pr * ix.w;
-    int e;
-    frexpf(amax * static_cast<float>(npix), &e);
-    int S = 62 - e;
-    S = S > 100 ? 100 : (S < -100 ? -100 : S);
-    const float fs = ldexpf(1.f, S);
-    // candidate ring from the start-up radius: r50 = (k-1) + frac, frac in (0, 1]
+    o.pr = peak / ix.w;
+    o.pc = peak - o.pr * ix.w;
+    o.k = 0;
+    o.c_in = o.c_ring = o.c_out = o.u_in = o.u_disc = 0.f;
+    const float tot = tot_h + tot_l;
+    if (!(tot > 0.f)) return o;                  // fallback radius: no dependence
+    // candidate from the start-up radius: r50 = (k-1) + frac, frac in (0, 1]
     int k = r50_hint > 0.5f ? static_cast<int>(ceilf(r50_hint)) : 0;
-    long long tot = 0, ein = 0, ek = 0;
-    bool found = false;
-    for (int tries = 0; tries < 8 && !found; ++tries) {
-        long long t = 0, e0 = 0, e1 = 0;
-        PixelWalk pw(lane, ix.w);
-        for (int p = lane; p < npix; p += 32) {
-            const long long qv = __float2ll_rn(load_pix<DT>(a, ix.offset + p, sc) * fs);
-            const int di = pw.row - o.pr, dj = pw.col - o.pc;
-            const int d2 = di * di + dj * dj;
-            pw.next();
-            t += qv;
-            if (k >= 1 && d2 <= (k - 1) * (k - 1)) e0 += qv;
-            if (d2 <= k * k) e1 += qv;
+    for (int tries = 0; tries < 8; ++tries) {
+        float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+        const float km2 = static_cast<float>((k - 1) * (k - 1)), k2 = static_cast<float>(k * k);
+        const float pcf = static_cast<float>(o.pc), prf = static_cast<float>(o.pr);
+        FWalk pw(lane, ix.w);
+        int p0 = lane;
+        for (; p0 < npix; p0 += 256) {
+            // eight loads in flight per lane; the stamp is still in L1 or L2
+            float v[8], uu[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int p = p0 + 32 * u;
+                v[u] = p < npix ? load_pix<DT>(a, ix.offset + p, sc) : 0.f;
+                if (JVP) uu[u] = p < npix ? __ldg(a.tangent + ix.offset + p) : 0.f;
+            }
+            float ph[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float dj = pw.c - pcf, di = pw.r - prf;
+                const float d2 = fmaf(di, di, dj * dj);      // an exact integer
+                pw.next();
+                const bool in0 = k >= 1 && d2 <= km2, in1 = d2 <= k2;   // zero-filled past the end
+                ph[0] += in0 ? v[u] : 0.f;
+                ph[1] += in1 ? v[u] : 0.f;
+                if (JVP) {
+                    ph[2] += in0 ? uu[u] : 0.f;
+                    ph[3] += in1 ? uu[u] : 0.f;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) df_add(h[i], l[i], ph[i]);
         }
-        t = warp_allsum_ll(t);
-        e0 = warp_allsum_ll(e0);
-        e1 = warp_allsum_ll(e1);
-        tot = t;
-        if (tot <= 0) return o;                  // fallback radius: no dependence
-        if (2 * e1 < tot) {
+        warp_allsum_df(h, l);
+        // 2 E - tot in double-float: the sign decides the crossing
+        const float d1 = (2.f * h[1] - tot_h) + (2.f * l[1] - tot_l);
+        const float d0 = (2.f * h[0] - tot_h) + (2.f * l[0] - tot_l);
+        if (d1 < 0.f) {
             ++k;
-        } else if (k >= 1 && 2 * e0 >= tot) {
+        } else if (k >= 1 && d0 >= 0.f) {
             --k;
         } else {
-            found = true;
-            ein = e0;
-            ek = e1;
+            o.k = k;
+            o.on = true;
+            o.u_in = h[2] + l[2];
+            o.u_disc = h[3] + l[3];
+            if (k == 0) {
+                // r50 = H / (2 S) with S the brightest pixel
+                const float Sf = h[1] + l[1], H = 0.5f * tot;
+                o.c_ring = 0.5f * (0.5f * Sf - H) / (Sf * Sf) * kInvSqrt2Ln2F;
+                o.c_out = 0.25f / Sf * kInvSqrt2Ln2F;
+            } else {
+                // r50 = (k-1) + (H - P) / (S - P); the differences from the pair sums
+                const float D = (h[1] - h[0]) + (l[1] - l[0]);
+                const float HP = 0.5f * ((tot_h - 2.f * h[0]) + (tot_l - 2.f * l[0]));
+                o.c_out = 0.5f / D * kInvSqrt2Ln2F;
+                o.c_ring = (0.5f * D - HP) / (D * D) * kInvSqrt2Ln2F;
+                o.c_in = -0.5f / D * kInvSqrt2Ln2F;
+            }
+            return o;
         }
     }
-    if (!found) return o;
-    o.k = k;
-    o.on = true;
-    if (k == 0) {
-        // r50 = H / (2 S) with S the brightest pixel
-        const float Sf = static_cast<float>(ek) / fs, H = 0.5f * static_cast<float>(tot) / fs;
-        o.c_ring = 0.5f * (0.5f * Sf - H) / (Sf * Sf) * kInvSqrt2Ln2F;
-        o.c_out = 0.25f / Sf * kInvSqrt2Ln2F;
-        o.c_in = 0.f;
-    } else {
-        // r50 = (k-1) + (H - P) / (S - P), differences taken exactly in integers
-        const float D = static_cast<float>(ek - ein) / fs;
-        const float HP = 0.5f * static_cast<float>(tot - 2 * ein) / fs;
-        o.c_out = 0.5f / D * kInvSqrt2Ln2F;
-        o.c_ring = (0.5f * D - HP) / (D * D) * kInvSqrt2Ln2F;
-        o.c_in = -0.5f / D * kInvSqrt2Ln2F;
-    }
     return o;
+}
+
+// The moment terms of one pixel at t = (t1, t2): f = I W times the 15
+// monomials of degree <= 4 into P; for the JVP, the tangent u W times the
+// six of degree <= 2, and u itself, into PU.
+template <bool JVP>
+__device__ __forceinline__ void moment_terms(const Geom& q, float t1, float t2, float v, float uu, float (&P)[15],
+                                             float (&PU)[7]) {
+    const float R2 = fmaf(q.A, t1 * t1, fmaf(q.B, t2 * t2, -q.G4 * (t1 * t2)));
+    const float W = ex2(R2 * q.cw);
+    const float f = v * W;
+    const float f1 = f * t1, f2 = f * t2;
+    const float f11 = f1 * t1, f12 = f1 * t2, f22 = f2 * t2;
+    const float f111 = f11 * t1, f112 = f11 * t2, f122 = f12 * t2, f222 = f22 * t2;
+    P[mono(0, 0)] += f;
+    P[mono(1, 0)] += f1;
+    P[mono(0, 1)] += f2;
+    P[mono(2, 0)] += f11;
+    P[mono(1, 1)] += f12;
+    P[mono(0, 2)] += f22;
+    P[mono(3, 0)] += f111;
+    P[mono(2, 1)] += f112;
+    P[mono(1, 2)] += f122;
+    P[mono(0, 3)] += f222;
+    P[mono(4, 0)] = fmaf(f111, t1, P[mono(4, 0)]);
+    P[mono(3, 1)] = fmaf(f111, t2, P[mono(3, 1)]);
+    P[mono(2, 2)] = fmaf(f112, t2, P[mono(2, 2)]);
+    P[mono(1, 3)] = fmaf(f122, t2, P[mono(1, 3)]);
+    P[mono(0, 4)] = fmaf(f222, t2, P[mono(0, 4)]);
+    if (JVP) {
+        const float h = uu * W;
+        const float h1 = h * t1, h2 = h * t2;
+        PU[0] += h;
+        PU[1] += h1;
+        PU[2] += h2;
+        PU[3] = fmaf(h1, t1, PU[3]);
+        PU[4] = fmaf(h1, t2, PU[4]);
+        PU[5] = fmaf(h2, t2, PU[5]);
+        PU[6] += uu;
+    }
 }
 
 // One warp per stamp.  JVP = true: dtheta along a.tangent; false: the pixel
 // gradient for a.v.
 template <int DT, bool JVP>
-__global__ void __launch_bounds__(256) moment_grad_kernel(MomentGradArgs a) {
+__global__ void __launch_bounds__(256, 2) moment_grad_kernel(MomentGradArgs a) {
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned sidx = 0;
@@ -304,99 +382,104 @@ __global__ void __launch_bounds__(256) moment_grad_kernel(MomentGradArgs a) {
         }
         if (!(q.s > 0.f) || !isfinite(q.cw)) status |= FSE_ST_MOM_FAILED;
         bool finite = true;
-        R50Grad rg;
-        rg.on = false;
-        rg.pr = rg.pc = rg.k = 0;
-        rg.c_in = rg.c_ring = rg.c_out = 0.f;
-        if (status == 0 && sig_r50) rg = r50_grad<DT>(a, ix, npix, sc, mom.r50, lane, finite);
-        // weighted moments (and, for the JVP, the tangent's sums)
-        float Mh[15], Ml[15], Uh[9], Ul[9];
+        // pass 1: the 15 weighted moments; the tangent's weighted sums (JVP);
+        // and, for the growth curve, the brightest pixel and the total
+        float Mh[15], Ml[15], Uh[7], Ul[7];
 #pragma unroll
         for (int i = 0; i < 15; ++i) Mh[i] = Ml[i] = 0.f;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) Uh[i] = Ul[i] = 0.f;
-        if (status == 0 && finite) {
-            PixelWalk pw(lane, ix.w);
-            bool fin = true;
-            for (int p0 = lane; p0 < npix; p0 += 256) {
-                float P[15], PU[9];
+        for (int i = 0; i < 7; ++i) Uh[i] = Ul[i] = 0.f;
+        float vmax = -INFINITY, th_ = 0.f, tl_ = 0.f;
+        int imax = 0x7fffffff;
+        if (status == 0) {
+            FWalk pw(lane, ix.w);
+            int p0 = lane;
+            // eight pixels per lane per step, loads ahead of use; then the tail
+            for (; p0 + 224 < npix; p0 += 256) {
+                float P[15], PU[7], ptot = 0.f;
 #pragma unroll
                 for (int i = 0; i < 15; ++i) P[i] = 0.f;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) PU[i] = 0.f;
+                for (int i = 0; i < 7; ++i) PU[i] = 0.f;
                 float v[8], uu[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    const int p = p0 + 32 * u;
-                    v[u] = p < npix ? load_pix<DT>(a, ix.offset + p, sc) : 0.f;
-                    if (JVP) uu[u] = p < npix ? __ldg(a.tangent + ix.offset + p) : 0.f;
+                    v[u] = load_pix<DT>(a, ix.offset + p0 + 32 * u, sc);
+                    if (JVP) uu[u] = __ldg(a.tangent + ix.offset + p0 + 32 * u);
                 }
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    const int p = p0 + 32 * u;
-                    if (p < npix) {
-                        const float t1 = static_cast<float>(pw.col) - q.x0;
-                        const float t2 = static_cast<float>(pw.row) - q.y0;
-                        const int di = pw.row - rg.pr, dj = pw.col - rg.pc;
-                        pw.next();
-                        fin = fin && isfinite(v[u]);
-                        const float R2 = fmaf(q.A, t1 * t1, fmaf(q.B, t2 * t2, -q.G4 * (t1 * t2)));
-                        const float W = ex2(fmaxf(R2, 0.f) * q.cw);
-                        const float f = v[u] * W;
-                        const float f1 = f * t1, f2 = f * t2;
-                        const float f11 = f1 * t1, f12 = f1 * t2, f22 = f2 * t2;
-                        const float f111 = f11 * t1, f112 = f11 * t2, f122 = f12 * t2, f222 = f22 * t2;
-                        P[mono(0, 0)] += f;
-                        P[mono(1, 0)] += f1;
-                        P[mono(0, 1)] += f2;
-                        P[mono(2, 0)] += f11;
-                        P[mono(1, 1)] += f12;
-                        P[mono(0, 2)] += f22;
-                        P[mono(3, 0)] += f111;
-                        P[mono(2, 1)] += f112;
-                        P[mono(1, 2)] += f122;
-                        P[mono(0, 3)] += f222;
-                        P[mono(4, 0)] = fmaf(f111, t1, P[mono(4, 0)]);
-                        P[mono(3, 1)] = fmaf(f111, t2, P[mono(3, 1)]);
-                        P[mono(2, 2)] = fmaf(f112, t2, P[mono(2, 2)]);
-                        P[mono(1, 3)] = fmaf(f122, t2, P[mono(1, 3)]);
-                        P[mono(0, 4)] = fmaf(f222, t2, P[mono(0, 4)]);
-                        if (JVP) {
-                            fin = fin && isfinite(uu[u]);
-                            const float h = uu[u] * W;
-                            const float h1 = h * t1, h2 = h * t2;
-                            PU[0] += h;
-                            PU[1] += h1;
-                            PU[2] += h2;
-                            PU[3] = fmaf(h1, t1, PU[3]);
-                            PU[4] = fmaf(h1, t2, PU[4]);
-                            PU[5] = fmaf(h2, t2, PU[5]);
-                            // tangent over the growth-curve regions: all, disc k, disc k-1
-                            const int d2 = di * di + dj * dj;
-                            PU[6] += uu[u];
-                            if (d2 <= rg.k * rg.k) PU[7] += uu[u];
-                            if (rg.k >= 1 && d2 <= (rg.k - 1) * (rg.k - 1)) PU[8] += uu[u];
-                        }
+                    if (sig_r50) {
+                        if (v[u] > vmax) { vmax = v[u]; imax = p0 + 32 * u; }
+                        ptot += v[u];
                     }
+                    moment_terms<JVP>(q, pw.c - q.x0, pw.r - q.y0, v[u], JVP ? uu[u] : 0.f, P, PU);
+                    pw.next();
                 }
 #pragma unroll
                 for (int i = 0; i < 15; ++i) df_add(Mh[i], Ml[i], P[i]);
                 if (JVP) {
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) df_add(Uh[i], Ul[i], PU[i]);
+                    for (int i = 0; i < 7; ++i) df_add(Uh[i], Ul[i], PU[i]);
                 }
+                if (sig_r50) df_add(th_, tl_, ptot);
             }
-            finite = __all_sync(kFull, fin);
+            {
+                float P[15], PU[7], ptot = 0.f;
+#pragma unroll
+                for (int i = 0; i < 15; ++i) P[i] = 0.f;
+#pragma unroll
+                for (int i = 0; i < 7; ++i) PU[i] = 0.f;
+                for (int p = p0; p < npix; p += 32) {
+                    const float v = load_pix<DT>(a, ix.offset + p, sc);
+                    const float uu = JVP ? __ldg(a.tangent + ix.offset + p) : 0.f;
+                    if (sig_r50) {
+                        if (v > vmax) { vmax = v; imax = p; }
+                        ptot += v;
+                    }
+                    moment_terms<JVP>(q, pw.c - q.x0, pw.r - q.y0, v, uu, P, PU);
+                    pw.next();
+                }
+#pragma unroll
+                for (int i = 0; i < 15; ++i) df_add(Mh[i], Ml[i], P[i]);
+                if (JVP) {
+#pragma unroll
+                    for (int i = 0; i < 7; ++i) df_add(Uh[i], Ul[i], PU[i]);
+                }
+                if (sig_r50) df_add(th_, tl_, ptot);
+            }
+            // a NaN or Inf pixel (or tangent) makes I W (u W) non-finite
+            // whatever its weight, and with it the warp's total
+            float chk = (Mh[0] + Ml[0]) + (JVP ? Uh[6] + Uh[0] : 0.f) + (sig_r50 ? th_ : 0.f);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) chk += __shfl_xor_sync(kFull, chk, off);
+            finite = isfinite(chk);
         }
         if (!finite) status |= FSE_ST_NONFINITE;
-        float Su[9];
+        float Su[7];
         if (status == 0) {
             warp_allsum_df(Mh, Ml);
             if (JVP) {
                 warp_allsum_df(Uh, Ul);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) Su[i] = Uh[i] + Ul[i];
+                for (int i = 0; i < 7; ++i) Su[i] = Uh[i] + Ul[i];
             }
+        }
+        // pass 2 (growth-curve sigma_w): the crossing ring around the brightest pixel
+        R50Grad rg;
+        rg.on = false;
+        rg.pr = rg.pc = rg.k = 0;
+        rg.c_in = rg.c_ring = rg.c_out = rg.u_in = rg.u_disc = 0.f;
+        if (status == 0 && sig_r50) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const float ov = __shfl_xor_sync(kFull, vmax, off);
+                const int oi = __shfl_xor_sync(kFull, imax, off);
+                if (ov > vmax || (ov == vmax && oi < imax)) { vmax = ov; imax = oi; }
+            }
+            float t2h[1] = {th_}, t2l[1] = {tl_};
+            warp_allsum_df(t2h, t2l);
+            rg = r50_ring<DT, JVP>(a, ix, npix, sc, mom.r50, imax, t2h[0], t2l[0], lane);
         }
         // J: lane 5k + l assembles J_kl; then every lane holds all 25
         float X[25], xs[5], rhs[5];
@@ -430,7 +513,7 @@ __global__ void __launch_bounds__(256) moment_grad_kernel(MomentGradArgs a) {
                 // rhs = -(sum u psi + J_as dsigma_w); psi_k = W m_k
                 float dsw = 0.f;
                 if (rg.on)
-                    dsw = rg.c_out * Su[6] + (rg.c_ring - rg.c_out) * Su[7] + (rg.c_in - rg.c_ring) * Su[8];
+                    dsw = rg.c_out * Su[6] + (rg.c_ring - rg.c_out) * rg.u_disc + (rg.c_in - rg.c_ring) * rg.u_in;
                 const float ew1 = 2.f * q.g1 / (1.f + q.g1 * q.g1 + q.g2 * q.g2);
                 const float ew2 = 2.f * q.g2 / (1.f + q.g1 * q.g1 + q.g2 * q.g2);
                 float S5[5];
@@ -487,24 +570,23 @@ __global__ void __launch_bounds__(256) moment_grad_kernel(MomentGradArgs a) {
                     kc_out = kappa * rg.c_out;
                 }
             }
-            PixelWalk pw(lane, ix.w);
+            FWalk pw(lane, ix.w);
+            const float pcf = static_cast<float>(rg.pc), prf = static_cast<float>(rg.pr);
+            const float km2 = rg.k >= 1 ? static_cast<float>((rg.k - 1) * (rg.k - 1)) : -1.f;
+            const float k2 = static_cast<float>(rg.k * rg.k);
             for (int p = lane; p < npix; p += 32) {
-                float g = 0.f;
-                if (status == 0) {
-                    const float t1 = static_cast<float>(pw.col) - q.x0;
-                    const float t2 = static_cast<float>(pw.row) - q.y0;
-                    const float R2 = fmaf(q.A, t1 * t1, fmaf(q.B, t2 * t2, -q.G4 * (t1 * t2)));
-                    const float W = ex2(fmaxf(R2, 0.f) * q.cw);
-                    const float Q = fmaf(t1, fmaf(c[3], t1, fmaf(c[4], t2, c[1])), fmaf(t2, fmaf(c[5], t2, c[2]), c[0]));
-                    g = -W * Q;
-                    if (rg.on) {
-                        const int di = pw.row - rg.pr, dj = pw.col - rg.pc;
-                        const int d2 = di * di + dj * dj;
-                        g += d2 <= (rg.k - 1) * (rg.k - 1) && rg.k >= 1 ? kc_in : (d2 <= rg.k * rg.k ? kc_ring : kc_out);
-                    }
+                const float t1 = pw.c - q.x0, t2 = pw.r - q.y0;
+                const float R2 = fmaf(q.A, t1 * t1, fmaf(q.B, t2 * t2, -q.G4 * (t1 * t2)));
+                const float W = ex2(R2 * q.cw);
+                const float Q = fmaf(t1, fmaf(c[3], t1, fmaf(c[4], t2, c[1])), fmaf(t2, fmaf(c[5], t2, c[2]), c[0]));
+                float g = -W * Q;
+                if (rg.on) {
+                    const float dj = pw.c - pcf, di = pw.r - prf;
+                    const float d2 = fmaf(di, di, dj * dj);
+                    g += d2 <= km2 ? kc_in : (d2 <= k2 ? kc_ring : kc_out);
                 }
                 pw.next();
-                __stcs(a.dpix + ix.offset + p, g);
+                __stcs(a.dpix + ix.offset + p, status == 0 ? g : 0.f);
             }
         }
         if (lane == 0 && a.status) a.status[si] = status;
