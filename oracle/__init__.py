@@ -70,6 +70,11 @@ MOM_ELLIP, MOM_SIGW_FIXED, MOM_SIGW_R50 = 1, 2, 4
 _dp = ctypes.POINTER(ctypes.c_double)
 
 
+class CutoutInfo(ctypes.Structure):
+    _fields_ = [("row0", ctypes.c_int32), ("col0", ctypes.c_int32), ("h", ctypes.c_int32), ("w", ctypes.c_int32),
+                ("r50", ctypes.c_double), ("status", ctypes.c_uint32)]
+
+
 class Oracle:
     """The oracle's entry points, bound to one compiled copy of fse_oracle.c."""
 
@@ -106,6 +111,9 @@ class Oracle:
         L.orc_moment_jvp.restype = ctypes.c_int
         L.orc_moment_vjp.argtypes = [_dp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]
         L.orc_moment_vjp.restype = ctypes.c_int
+        L.orc_cutout.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(CutoutInfo)]
+        L.orc_cutout.restype = None
         L.orc_batch.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                 ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(Opts), ctypes.c_int,
                                 ctypes.c_void_p, ctypes.c_int]
@@ -242,6 +250,14 @@ class Oracle:
         d = np.zeros(I.shape)
         rc = self.L.orc_moment_vjp(_as_dp(I), I.shape[0], I.shape[1], _as_dp(th), mode, _as_dp(vv), _as_dp(d))
         return d, bool(rc)
+
+    def cutout(self, I, side_factor: float = 6.0, min_side: int = 8, max_side: int = 128) -> dict:
+        """Sec. 4.1 cut-out of a large image: the square of side side_factor * r50
+        around the brightest pixel.  Returns row0, col0, h, w, r50, status."""
+        I = _img(I)
+        r = CutoutInfo()
+        self.L.orc_cutout(_as_dp(I), I.shape[0], I.shape[1], side_factor, min_side, max_side, ctypes.byref(r))
+        return {k: getattr(r, k) for k, _ in CutoutInfo._fields_}
 
     def batch(self, pix, offset, h, w, stage: str = "measure", ivar=None,
               opts: Opts | None = None, init=None, threads: int = 0):

@@ -1113,6 +1113,46 @@ int orc_moment_vjp(const double *I, int h, int w, const double th[5], int mode, 
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* The cut-out of Sec. 4.1: a square of side six times r50 around the        */
+/* brightest pixel of a large image.                                         */
+/* ------------------------------------------------------------------------ */
+/* r50 is the start-up growth curve around the brightest pixel (the same as
+ * the stamp start-up).  The side is side_factor * r50 rounded to the nearest
+ * integer (halves up), clamped to [min_side, max_side]; the square starts
+ * side/2 (integer division) rows and columns before the brightest pixel and is
+ * cut to the image.  NONFINITE: no cut-out (h = w = 0). */
+typedef struct {
+    int32_t row0, col0, h, w;
+    double r50;
+    uint32_t status;
+} orc_cutout_info;
+
+void orc_cutout(const double *I, int H, int W, double side_factor, int min_side, int max_side,
+                orc_cutout_info *out)
+{
+    int pr, pc;
+    double r50;
+    uint32_t st = 0;
+    memset(out, 0, sizeof *out);
+    if (!init_stamp(I, H, W, &pr, &pc, &r50, &st)) { out->status = st; return; }
+    long side = (long)floor(side_factor * r50 + 0.5);
+    if (side < min_side) side = min_side;
+    if (side > max_side) side = max_side;
+    int r0 = pr - (int)(side / 2), c0 = pc - (int)(side / 2);
+    int r1 = r0 + (int)side, c1 = c0 + (int)side;
+    if (r0 < 0) r0 = 0;
+    if (c0 < 0) c0 = 0;
+    if (r1 > H) r1 = H;
+    if (c1 > W) c1 = W;
+    out->row0 = r0;
+    out->col0 = c0;
+    out->h = r1 - r0;
+    out->w = c1 - c0;
+    out->r50 = r50;
+    out->status = st;
+}
+
 /* Batch over a flat fp32 buffer (stamp s at pix + offset[s], h[s] x w[s]),
  * parallel over stamps with OpenMP.  stage: 0 = whole chain (orc_measure),
  * 1 = centroid, 2 = ellipticity (uses res[s] x0, y0, sigma_w), 3 = fit (uses

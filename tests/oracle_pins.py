@@ -450,6 +450,60 @@ def pin_moment_gradient_fd(O):
         assert np.abs(J[:, l] - fd).max() <= 1e-6 * np.abs(J).max(), (l, J[:, l], fd)
 
 
+def _growth_r50_bruteforce(I):
+    """r50 by the rule of Sec. 4.1, restated with numpy: rings of integer
+    radius k (k-1 < d <= k) around the brightest pixel (lowest row-major
+    index on ties), summed outward until half the total; linear inside the
+    crossing ring (k = 0: half the total over twice the peak)."""
+    h, w = I.shape
+    p = int(np.argmax(I.ravel()))          # first maximum in row-major order
+    pr, pc = divmod(p, w)
+    yy, xx = np.mgrid[0:h, 0:w]
+    d2 = (yy - pr) ** 2 + (xx - pc) ** 2
+    ring = np.ceil(np.sqrt(d2)).astype(int)
+    sums = np.bincount(ring.ravel(), weights=I.ravel())
+    enclosed = np.cumsum(sums)
+    half = 0.5 * I.sum()
+    k = int(np.argmax(enclosed >= half))
+    if k == 0:
+        return pr, pc, 0.5 * half / enclosed[0]
+    return pr, pc, (k - 1) + (half - enclosed[k - 1]) / (enclosed[k] - enclosed[k - 1])
+
+
+def pin_cutout(O):
+    """The Sec. 4.1 cut-out: r50 equals a brute-force growth curve, the square
+    of side 6 r50 (nearest integer) starts side/2 before the brightest pixel and
+    is cut to the image; on a Gaussian it holds all but ~1e-3 of the flux;
+    sides are clamped; non-finite images are refused."""
+    rng = np.random.default_rng(21)
+    for k in range(6):
+        h, w = int(rng.integers(30, 90)), int(rng.integers(30, 90))
+        yy, xx = np.mgrid[0:h, 0:w].astype(float)
+        # the object inside, and near each corner, so that the square is cut
+        xc, yc = [(rng.uniform(0, w - 1), rng.uniform(0, h - 1)), (w - 1.6, h - 2.2), (1.3, 0.8),
+                  (w - 2.1, 1.4), (0.6, h - 1.3), (rng.uniform(0, w - 1), rng.uniform(0, h - 1))][k]
+        sig = rng.uniform(1.0, 4.0)
+        I = 200.0 * np.exp(-((xx - xc) ** 2 + (yy - yc) ** 2) / (2 * sig * sig)) + rng.normal(0, 0.3, (h, w))
+        pr, pc, r50 = _growth_r50_bruteforce(I)
+        c = O.cutout(I)
+        assert abs(c["r50"] - r50) <= 1e-12 * max(1.0, r50), (k, c, r50)
+        side = min(max(int(np.floor(6.0 * r50 + 0.5)), 8), 128)
+        r0, c0 = pr - side // 2, pc - side // 2
+        want = (max(r0, 0), max(c0, 0), min(r0 + side, h) - max(r0, 0), min(c0 + side, w) - max(c0, 0))
+        assert (c["row0"], c["col0"], c["h"], c["w"]) == want, (k, c, want)
+    # a well-sampled Gaussian: the square keeps all but about 1e-3 of its flux
+    yy, xx = np.mgrid[0:256, 0:256].astype(float)
+    G = np.exp(-((xx - 120.3) ** 2 + (yy - 131.7) ** 2) / (2 * 3.0 ** 2))
+    c = O.cutout(G)
+    inside = G[c["row0"]:c["row0"] + c["h"], c["col0"]:c["col0"] + c["w"]].sum() / G.sum()
+    assert 0.998 <= inside < 1.0 and c["h"] == c["w"] == 21, (c, inside)
+    # clamps and refusal
+    assert O.cutout(G, side_factor=1.0)["h"] == 8 and O.cutout(G, side_factor=100.0)["h"] == 128
+    bad = G.copy()
+    bad[3, 4] = np.inf
+    assert O.cutout(bad)["status"] & 16 and O.cutout(bad)["h"] == 0
+
+
 def pin_edge_cases(O):
     """Status codes: non-finite pixels, empty flux, out-of-range sizes."""
     img = np.ones((8, 8))
@@ -467,4 +521,4 @@ ALL_PINS = [pin_gamma_p_library, pin_sersic_b, pin_sersic_db, pin_flux_closed_fo
             pin_ellipticity_step_newton, pin_matched_sigma_w, pin_stages_chain, pin_fit_noiseless,
             pin_fit_gradient_fd, pin_fit_minimum, pin_fit_chi2_distribution, pin_r50_gaussian,
             pin_chi2_grad_fd, pin_chi2_grad_noiseless, pin_star_gaussian, pin_star_moffat,
-            pin_moment_gradient_closed_forms, pin_moment_gradient_fd, pin_edge_cases]
+            pin_moment_gradient_closed_forms, pin_moment_gradient_fd, pin_cutout, pin_edge_cases]

@@ -83,6 +83,13 @@ MUTATIONS = {
     # implicit gradient: sign of the sigma_w coupling in the VJP
     "mom_grad_kappa_sign": ("for (int k = 0; k < 5; ++k) kappa -= lam[k] * J[k * 5 + 4];",
                             "for (int k = 0; k < 5; ++k) kappa += lam[k] * J[k * 5 + 4];"),
+    # cut-out: the side truncated instead of rounded
+    "cutout_side_round": ("long side = (long)floor(side_factor * r50 + 0.5);", "long side = (long)floor(side_factor * r50);"),
+    # cut-out: the square starts one pixel late
+    "cutout_origin": ("int r0 = pr - (int)(side / 2), c0 = pc - (int)(side / 2);",
+                      "int r0 = pr - (int)(side / 2) + 1, c0 = pc - (int)(side / 2);"),
+    # cut-out: the far edge not cut to the image
+    "cutout_clip": ("if (c1 > W) c1 = W;", "if (c1 > W + 1) c1 = W + 1;"),
     # non-finite input no longer flagged
     "nonfinite_check": ("if (!isfinite(I[p])) { *status |= ORC_NONFINITE; return 0; }", ""),
 }
