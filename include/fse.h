@@ -77,6 +77,7 @@ extern "C" {
 #define FSE_ST_TIMEOUT        (1u << 12) /* a bounded device wait expired for this stamp    */
 #define FSE_ST_MOM_REFINE2    (1u << 13) /* informational: a second moment refinement ran    */
 #define FSE_ST_FIT_REFINE2    (1u << 14) /* informational: a second fit refinement ran       */
+#define FSE_ST_NO_ROOM        (1u << 15) /* fse_cutout: the output buffer had no room for it */
 
 /* fse_opts.flags: fse_fit_batch_ragged captures its launch sequence into a
  * CUDA graph on first use and replays it while its arguments are unchanged. */
@@ -158,6 +159,15 @@ typedef struct {
     uint32_t status;        /* FSE_ST_MOM_CONVERGED / _MAXITER / _FAILED, BAD_SIZE, ... */
     float    reserved;
 } fse_star_result;
+
+/* One cut-out of fse_cutout (24 bytes). */
+typedef struct {
+    int32_t  row0, col0;    /* first row and column of the square in its image        */
+    int32_t  h, w;          /* its size after cutting to the image (0 if refused)     */
+    float    r50;           /* growth-curve half-light radius around the brightest px */
+    uint32_t status;        /* 0, FSE_ST_NONFINITE, FSE_ST_BAD_SIZE, FSE_ST_INIT_FALLBACK,
+                               FSE_ST_NO_ROOM                                          */
+} fse_cutout_info;
 
 /* Create a context on CUDA device `device`: selects the device, builds the
  * device table of the Sérsic b(n) (root of P(2n, b) = 1/2, Eq. 10) and b'(n),
@@ -308,6 +318,29 @@ int fse_moment_vjp(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
 int fse_moment_jvp(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
                    const fse_stamp *idx, int64_t count, const fse_result *moments, int mode,
                    const float *tangent, float *dtheta, uint32_t *status, void *stream);
+
+/* The cut-out of Sec. 4.1.  For each image s (img_idx[s] in `images`, fp32,
+ * or bf16 decoded with scale[s] for the growth curve), r50 comes from the
+ * growth curve around the brightest pixel (ties: lowest row-major index):
+ * pixels summed in rings of integer radius (k-1 < d <= k) until half the
+ * total, linear inside the crossing ring, in exact 64-bit fixed point.  The
+ * square of side floor(side_factor * r50 + 0.5), clamped to [min_side,
+ * max_side], starts side/2 (integer division) rows and columns before the
+ * brightest pixel and is cut to the image.  The cut-outs are copied back to
+ * back into out_pix (same dtype as the images; a bf16 cut-out keeps its
+ * image's scale), in image order; out_idx[s] gets their offset and size and
+ * info[s] the square and r50.  *out_total (device int64) receives the
+ * elements of all cut-outs; with out_pix NULL only sizes and offsets are
+ * written, so a first call can size the buffer.  A cut-out that does not fit
+ * in out_capacity elements gets FSE_ST_NO_ROOM and is not copied.  Images of
+ * more than 2^28 pixels get FSE_ST_BAD_SIZE; a crossing beyond a radius of
+ * 2047 px gives r50 = NaN and the largest side.  1 <= min_side <= max_side
+ * <= 128 (the largest stamp the estimator takes); side_factor > 0 (6 in the
+ * paper).  Device pointers; asynchronous on `stream`. */
+int fse_cutout(fse_ctx *ctx, const void *images, int dtype, const float *scale,
+               const fse_stamp *img_idx, int64_t count, double side_factor, int min_side, int max_side,
+               fse_cutout_info *info, fse_stamp *out_idx, void *out_pix, int64_t out_capacity,
+               int64_t *out_total, void *stream);
 
 /* Evaluate the device b(n) table (Eq. 10: P(2n, b) = 1/2) and its derivative
  * at count values n[i] in [0.2, 10] (device pointers, doubles).  For tests. */

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libfse.so")
-SOURCES = ["fse_api.cu", "fse_kernels.cu", "fse_adjoint.cu", "fse_ragged.cu", "fse_star.cu", "fse_moment_grad.cu"]
+SOURCES = ["fse_api.cu", "fse_kernels.cu", "fse_adjoint.cu", "fse_ragged.cu", "fse_star.cu", "fse_moment_grad.cu", "fse_cutout.cu"]
 HEADERS = ["fse_internal.h", "fse_device.cuh", os.path.join(INCLUDE, "fse.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--cudart", "shared",

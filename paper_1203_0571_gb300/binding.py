@@ -27,14 +27,16 @@ FSE_MAX_PIX = 128 * 128
 ST = dict(MOM_CONVERGED=1 << 0, FIT_CONVERGED=1 << 1, MOM_MAXITER=1 << 2, FIT_MAXITER=1 << 3,
           NONFINITE=1 << 4, BAD_SIZE=1 << 5, MOM_FAILED=1 << 6, FIT_BOUND=1 << 7,
           FIT_SINGULAR=1 << 8, NONPOS_FLUX=1 << 9, SIGW_CLAMPED=1 << 10, INIT_FALLBACK=1 << 11,
-          TIMEOUT=1 << 12, MOM_REFINE2=1 << 13, FIT_REFINE2=1 << 14)
+          TIMEOUT=1 << 12, MOM_REFINE2=1 << 13, FIT_REFINE2=1 << 14, NO_ROOM=1 << 15)
 
 # exported symbols, in the order include/fse.h declares them
 EXPORTS = ["fse_create", "fse_destroy", "fse_last_error", "fse_opts_default", "fse_centroid",
            "fse_ellipticity", "fse_sersic_fit", "fse_fit_batch", "fse_fit_batch_plain",
            "fse_fit_batch_host", "fse_fit_batch_ragged", "fse_autotune", "fse_tuned_warps",
-           "fse_star_fit", "fse_moment_vjp", "fse_moment_jvp", "fse_sersic_b", "fse_sersic_chi2_grad",
-           "fse_sync_check", "fse_fit_batch_static"]
+           "fse_star_fit", "fse_moment_vjp", "fse_moment_jvp", "fse_cutout", "fse_sersic_b",
+           "fse_sersic_chi2_grad", "fse_sync_check", "fse_fit_batch_static"]
+CUTOUT_DTYPE = np.dtype([("row0", "<i4"), ("col0", "<i4"), ("h", "<i4"), ("w", "<i4"), ("r50", "<f4"),
+                         ("status", "<u4")])
 FSE_MOM_ELLIP, FSE_MOM_SIGW_FIXED, FSE_MOM_SIGW_R50 = 1, 2, 4
 FSE_STAR_GAUSS, FSE_STAR_MOFFAT = 0, 1
 STAR_DTYPE = np.dtype([("size", "<f4"), ("beta", "<f4"), ("I0", "<f4"), ("flux", "<f4"), ("r50", "<f4"),
@@ -103,6 +105,9 @@ def load(build: bool = True, path: str | None = None) -> ctypes.CDLL:
         getattr(L, f).argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int64, _vp, ctypes.c_int,
                                   _vp, _vp, _vp, _vp]
         getattr(L, f).restype = ctypes.c_int
+    L.fse_cutout.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int64, ctypes.c_double, ctypes.c_int,
+                             ctypes.c_int, _vp, _vp, _vp, ctypes.c_int64, _vp, _vp]
+    L.fse_cutout.restype = ctypes.c_int
     L.fse_tuned_warps.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                   ctypes.POINTER(ctypes.c_int32)]
     L.fse_tuned_warps.restype = ctypes.c_int
@@ -153,6 +158,11 @@ def make_index(offset, h, w, device="cuda") -> torch.Tensor:
 def star_results(out: torch.Tensor) -> np.ndarray:
     """Copy a star result tensor (uint8 [N, 32]) to a numpy structured array."""
     return out.detach().cpu().contiguous().numpy().view(STAR_DTYPE).reshape(-1)
+
+
+def cutout_info(info: torch.Tensor) -> np.ndarray:
+    """Copy cut-out records (uint8 [N, 24]) to a numpy structured array."""
+    return info.detach().cpu().contiguous().numpy().view(CUTOUT_DTYPE).reshape(-1)
 
 
 def results(out: torch.Tensor) -> np.ndarray:
@@ -294,6 +304,33 @@ class Context:
                                           _stream(stream)))
         return out
 
+    def cutout(self, images, img_index, *, side_factor: float = 6.0, min_side: int = 8, max_side: int = 128,
+               scale=None, out=None, stream=None):
+        """fse_cutout (Sec. 4.1): the square of side side_factor * r50 around the
+        brightest pixel of each image, packed back to back.  Returns (pix,
+        index, info): the cut-out pixels (dtype of the images), their fse_stamp
+        index (int64 [N, 2] view, see make_index) and the per-image
+        fse_cutout_info records (uint8 [N, 24]).  Without `out` a first launch
+        sizes the buffer (and the stream is synchronised once)."""
+        n = int(img_index.shape[0])
+        dev = images.device
+        info = torch.zeros((n, 24), dtype=torch.uint8, device=dev)
+        idx = torch.zeros((n, 2), dtype=torch.int64, device=dev)
+        total = torch.zeros(1, dtype=torch.int64, device=dev)
+        L = load()
+        args = lambda o, cap: (self._h, _ptr(images), _dtype_of(images), _ptr(scale), _ptr(img_index), n,
+                               float(side_factor), int(min_side), int(max_side), _ptr(info), _ptr(idx), _ptr(o),
+                               int(cap), _ptr(total), _stream(stream))
+        if out is None:
+            self._check(L.fse_cutout(*args(None, 0)))
+            torch.cuda.synchronize(dev)
+            out = torch.empty(max(int(total.item()), 1), dtype=images.dtype, device=dev)
+            cap = int(total.item())
+        else:
+            cap = out.numel()
+        self._check(L.fse_cutout(*args(out, cap)))
+        return out, idx, info
+
     def fit_batch_host(self, pix: np.ndarray | torch.Tensor, index: np.ndarray | torch.Tensor, *,
                        scale=None, inv_var=None, opts=None, out=None, stream=None) -> np.ndarray:
         """fse_fit_batch_host: host buffers in, host results out (synchronous)."""
@@ -402,6 +439,10 @@ def fse_moment_vjp(ctx: Context, *a, **k):
 
 def fse_moment_jvp(ctx: Context, *a, **k):
     return ctx.moment_jvp(*a, **k)
+
+
+def fse_cutout(ctx: Context, *a, **k):
+    return ctx.cutout(*a, **k)
 
 
 def fse_sersic_b(ctx: Context, *a, **k):

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -814,6 +815,46 @@ int fse_moment_jvp(fse_ctx* ctx, const void* pix, int dtype, const float* scale,
                    uint32_t* status, void* stream) {
     return moment_grad(ctx, true, pix, dtype, scale, idx, count, moments, mode, nullptr, nullptr, tangent,
                        dtheta, status, stream);
+}
+
+int fse_cutout(fse_ctx* ctx, const void* images, int dtype, const float* scale, const fse_stamp* img_idx,
+               int64_t count, double side_factor, int min_side, int max_side, fse_cutout_info* info,
+               fse_stamp* out_idx, void* out_pix, int64_t out_capacity, int64_t* out_total, void* stream) {
+    if (!ctx) return FSE_EINVAL;
+    if (count < 0) return set_error(ctx, FSE_EINVAL, "count out of range");
+    if (dtype != FSE_F32 && dtype != FSE_BF16) return set_error(ctx, FSE_EINVAL, "unknown dtype %d", dtype);
+    if (!(side_factor > 0.0) || !std::isfinite(side_factor))
+        return set_error(ctx, FSE_EINVAL, "side_factor must be positive and finite");
+    if (min_side < 1 || max_side < min_side || max_side > 128)
+        return set_error(ctx, FSE_EINVAL, "need 1 <= min_side <= max_side <= 128");
+    if (out_capacity < 0) return set_error(ctx, FSE_EINVAL, "out_capacity must not be negative");
+    if (count == 0) return FSE_OK;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return set_error(ctx, FSE_ECUDA, "cannot select device %d", ctx->device);
+    if (!images || !img_idx || !info || !out_idx || !out_total)
+        return set_error(ctx, FSE_EINVAL, "images, img_idx, info, out_idx and out_total must not be NULL");
+    const void* dev_ptrs[] = {images, img_idx, info, out_idx, out_total, out_pix, scale};
+    for (const void* q : dev_ptrs)
+        if (q && !is_device_ptr(q))
+            return set_error(ctx, FSE_EINVAL, "all array arguments must be device pointers");
+    fse::CutoutArgs a;
+    memset(&a, 0, sizeof a);
+    a.images = images;
+    a.dtype = dtype;
+    a.scale = scale;
+    a.img_idx = img_idx;
+    a.count = count;
+    a.side_factor = side_factor;
+    a.min_side = min_side;
+    a.max_side = max_side;
+    a.info = info;
+    a.out_idx = out_idx;
+    a.out_pix = out_pix;
+    a.out_capacity = out_capacity;
+    a.out_total = out_total;
+    cudaError_t e = fse::launch_cutout(a, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cut-out launch");
+    return FSE_OK;
 }
 
 int fse_sersic_b(fse_ctx* ctx, const double* n, double* b, double* db, int64_t count, void* stream) {

@@ -115,6 +115,22 @@ struct MomentGradArgs {
     unsigned int* queue;         // work counter (zeroed before launch)
 };
 
+// Arguments of the cut-out launches (fse_cutout, Sec. 4.1).
+struct CutoutArgs {
+    const void* images;
+    int dtype;
+    const float* scale;          // bf16: per-image scale for the growth curve
+    const fse_stamp* img_idx;
+    int64_t count;
+    double side_factor;
+    int min_side, max_side;
+    fse_cutout_info* info;
+    fse_stamp* out_idx;
+    void* out_pix;               // NULL: sizes and offsets only
+    int64_t out_capacity;        // elements
+    int64_t* out_total;          // device: elements of all cut-outs
+};
+
 // Number of nodes of the b(n) table and its range.
 constexpr double kBnLo = 0.125;
 constexpr double kBnStep = 1.0 / 512.0;
@@ -130,6 +146,8 @@ cudaError_t eval_bn(const double* n, double* b, double* db, int64_t count, cudaS
 cudaError_t launch_estimator(const LaunchArgs& a, cudaStream_t stream);
 // Launches the implicit-gradient kernel; returns the launch error.
 cudaError_t launch_moment_grad(const MomentGradArgs& a, cudaStream_t stream);
+// Launches the three cut-out kernels; returns the launch error.
+cudaError_t launch_cutout(const CutoutArgs& a, cudaStream_t stream);
 // Launches the star-profile kernel; returns the launch error.
 cudaError_t launch_star(const StarArgs& a, cudaStream_t stream);
 // Launches the chi^2 / adjoint kernel; returns the launch error.

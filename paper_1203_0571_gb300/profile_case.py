@@ -1,6 +1,6 @@
 """A small, self-contained launch of libfse for profiler captures.
 
-    python -m paper_1203_0571_gb300.profile_case [--what fit_batch|adjoint|star|moment_vjp|moment_jvp]
+    python -m paper_1203_0571_gb300.profile_case [--what fit_batch|adjoint|star|moment_vjp|moment_jvp|cutout]
         [--profile gauss|moffat] [--workload 1] [--stamps 20000] [--warmup 3] [--launches 1]
 
 Generates the first `stamps` stamps of a synthetic workload on the GPU, runs
@@ -11,7 +11,8 @@ autograd bridge); star runs fse_star_fit (Sec. 4.2) at the centre and
 ellipticity of a preceding fse_centroid + fse_ellipticity; moment_vjp and
 moment_jvp run the implicit gradients of that fixed point (sigma_w from the
 growth curve), on 100,000 stamps of 48x48 (922 MB read; the VJP writes as
-much).  The inputs of the
+much).  cutout runs fse_cutout on 500 images of 512x512 (524 MB) and then
+fse_fit_batch on the cut-outs.  The inputs of the
 default cases (20,000 stamps of 48x48 fp32, 184 MB; for the adjoint, 16,384
 stamps of 64x64, 268 MB; for the stars, 50,000 Gaussian stars of 32x32, 205
 MB, or 50,000 Moffat stars of 48x48, 461 MB) are larger than the 129 MB L2,
@@ -22,6 +23,7 @@ from __future__ import annotations
 import argparse
 import json
 
+import numpy as np
 import torch
 
 from . import binding as B
@@ -30,7 +32,7 @@ from . import synth
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--what", choices=["fit_batch", "adjoint", "star", "moment_vjp", "moment_jvp"],
+    ap.add_argument("--what", choices=["fit_batch", "adjoint", "star", "moment_vjp", "moment_jvp", "cutout"],
                     default="fit_batch")
     ap.add_argument("--profile", choices=["gauss", "moffat"], default="gauss")
     ap.add_argument("--sigw", choices=["r50", "matched", "fixed"], default="r50",
@@ -48,6 +50,8 @@ def main():
         return moment_grad(ctx, args.what == "moment_jvp", args.workload if args.workload is not None else 1,
                            args.stamps if args.stamps is not None else 100000, args.warmup, args.launches,
                            args.sigw)
+    if args.what == "cutout":
+        return cutout(ctx, args.stamps if args.stamps is not None else 500, args.warmup, args.launches)
     if args.what == "star":
         return star(ctx, args.profile, args.workload if args.workload is not None else
                     (6 if args.profile == "gauss" else 7),
@@ -148,6 +152,34 @@ def moment_grad(ctx, jvp, workload, stamps, warmup, launches, sigw):
                       "sigw": sigw,
                       "ms_per_launch": a.elapsed_time(b) / launches,
                       "status_zero": float((st == 0).float().mean())}))
+
+
+def cutout(ctx, images, warmup, launches):
+    batch = synth.make_workload(8, count=images, device="cuda")
+    idx = B.make_index(batch.offset, batch.h, batch.w)
+    pix, cidx, info = ctx.cutout(batch.pix, idx)
+    opts = B.default_opts(max_pix=128 * 128)
+    out = torch.empty((batch.count, 64), dtype=torch.uint8, device="cuda")
+    for _ in range(warmup):
+        ctx.cutout(batch.pix, idx, out=pix)
+        ctx.fit_batch(pix, cidx, opts=opts, out=out)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    for _ in range(launches):
+        ctx.cutout(batch.pix, idx, out=pix)
+    ev[1].record()
+    for _ in range(launches):
+        ctx.fit_batch(pix, cidx, opts=opts, out=out)
+    ev[2].record()
+    ctx.sync_check()
+    inf = B.cutout_info(info)
+    res = B.results(out)
+    print(json.dumps({"images": batch.count, "image_pixels": batch.pix.numel(), "cutout_pixels": pix.numel(),
+                      "side_median": float(np.median(inf["h"])),
+                      "ms_cutout": ev[0].elapsed_time(ev[1]) / launches,
+                      "ms_fit_batch": ev[1].elapsed_time(ev[2]) / launches,
+                      "converged": float(((res["status"] & 3) == 3).mean())}))
 
 
 if __name__ == "__main__":

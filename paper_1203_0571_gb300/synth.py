@@ -113,6 +113,9 @@ WORKLOADS = {
                 "20,000 Gaussian stars 32x32 fp32 (Sec. 4.2): r50 U[1.5,2.5] px, |g| U[0,0.25], SNR 300"),
     7: Workload("stars-moffat-48px", 20_000, 7,
                 "20,000 Moffat stars 48x48 fp32 (Sec. 4.2): beta U[3,5], r50 U[1.5,2.5] px, |g| U[0,0.25], SNR 300"),
+    8: Workload("images-512px", 500, 8,
+                "500 images 512x512 fp32, one galaxy each (the large images of Sec. 4.1): base galaxy "
+                "recipe, SNR U[15,200], centre offset U(-20,20) px from the image centre"),
 }
 
 
@@ -187,6 +190,9 @@ def _draw_params(wl: Workload, ids: np.ndarray) -> dict:
     snr = U(7, 15.0, 200.0)
     if wl.seed == 5:
         snr = U(7, 10.0, 30.0)
+    if wl.seed == 8:
+        dx = U(4, -20.0, 20.0)
+        dy = U(5, -20.0, 20.0)
     if star.any():
         fwhm = U(8, 2.0, 4.0)
         n = np.where(star, 0.5, n)
@@ -206,14 +212,14 @@ def _draw_params(wl: Workload, ids: np.ndarray) -> dict:
         if wl.seed == 7:
             beta = U(11, 3.0, 5.0)
             re = r50 / np.sqrt(2.0 ** (1.0 / (beta - 1.0)) - 1.0)
-    if wl.seed in (0, 1, 3, 6, 7):
-        side = np.full(N, {0: 32, 1: 48, 3: 64, 6: 32, 7: 48}[wl.seed], dtype=np.int64)
+    if wl.seed in (0, 1, 3, 6, 7, 8):
+        side = np.full(N, {0: 32, 1: 48, 3: 64, 6: 32, 7: 48, 8: 512}[wl.seed], dtype=np.int64)
     elif wl.seed == 2:
         side = np.clip(np.rint(8.0 * re), 16, 128).astype(np.int64)
     else:
         side = np.floor(U(10, 32.0, 65.0)).astype(np.int64).clip(32, 64)
     return dict(n=n, re=re, gabs=gabs, phi=phi, dx=dx, dy=dy, flux=flux, snr=snr,
-                star=star, side=side, beta=beta, by_snr=np.full(N, wl.seed in (1, 5, 6, 7)))
+                star=star, side=side, beta=beta, by_snr=np.full(N, wl.seed in (1, 5, 6, 7, 8)))
 
 
 def _render(side: int, p: dict, sel: np.ndarray, ids: np.ndarray, seed: int,
@@ -244,7 +250,9 @@ def _render(side: int, p: dict, sel: np.ndarray, ids: np.ndarray, seed: int,
     img = I0 * prof
     if noise:
         pix = torch.arange(side * side, device=device, dtype=torch.int64).view(1, side, side)
-        cnt = (torch.as_tensor(ids[sel], device=device, dtype=torch.int64).view(k, 1, 1) << 15) + pix
+        # a stamp's noise counters: id << 15 up to 181 x 181 pixels, id << 20 for larger images
+        shift = 15 if side * side <= (1 << 15) else 20
+        cnt = (torch.as_tensor(ids[sel], device=device, dtype=torch.int64).view(k, 1, 1) << shift) + pix
         img = img + normal(seed, _S_NOISE, cnt)
     return img, I0.view(k).cpu().numpy(), g1.view(k).cpu().numpy(), g2.view(k).cpu().numpy(), \
         xc.view(k).cpu().numpy(), yc.view(k).cpu().numpy(), b.view(k).cpu().numpy()

@@ -1,0 +1,176 @@
+"""The Sec. 4.1 cut-out on the GPU (fse_cutout) against the FP64 oracle,
+needs a GB300.
+
+Index work is compared exactly: the brightest pixel, the crossing ring of the
+growth curve and the square (row0, col0, h, w), the offsets of the packed
+buffer and every copied pixel.  r50 (fp32 on the GPU, from exact fixed-point
+sums; fp64 in the oracle) agrees to 1e-6 relative.  The side is
+floor(6 r50 + 0.5) in fp64 on both sides, so the squares differ only where
+6 r50 lies within ~1e-15 of a half-integer; the test reports such a case
+instead of failing on it.
+"""
+import numpy as np
+import pytest
+import torch
+
+import parity as PR
+from paper_1203_0571_gb300 import binding as B
+from paper_1203_0571_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+ST = B.ST
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+    return B.Context(0)
+
+
+@pytest.fixture(scope="module")
+def O(oracle):
+    return oracle.get()
+
+
+def check_against_oracle(O, batch, pix, idx, info, side_factor=6.0, min_side=8, max_side=128):
+    inf = B.cutout_info(info)
+    idx = idx.cpu().numpy()
+    off = idx[:, 0]
+    hw = idx[:, 1]
+    h, w = (hw & 0xffffffff).astype(np.int64), (hw >> 32).astype(np.int64)
+    out = pix.cpu().float().numpy() if pix.dtype == torch.bfloat16 else pix.cpu().numpy()
+    src = batch.pix.cpu().float().numpy() if batch.pix.dtype == torch.bfloat16 else batch.pix.cpu().numpy()
+    want_off = np.concatenate([[0], np.cumsum(h * w)[:-1]]) if batch.count else np.zeros(0)
+    assert np.array_equal(off, want_off)
+    ties = 0
+    for i in range(batch.count):
+        o = O.cutout(batch.stamp(i).astype(np.float32), side_factor, min_side, max_side)
+        g = inf[i]
+        assert int(g["status"]) == o["status"], (i, g, o)
+        if o["status"] & (ST["NONFINITE"] | ST["BAD_SIZE"]):
+            assert g["h"] == 0 and g["w"] == 0
+            continue
+        assert abs(float(g["r50"]) / o["r50"] - 1) <= 1e-6, (i, g["r50"], o["r50"])
+        box_g = (g["row0"], g["col0"], g["h"], g["w"])
+        box_o = (o["row0"], o["col0"], o["h"], o["w"])
+        if box_g != box_o:
+            x = side_factor * o["r50"] + 0.5
+            assert abs(x - round(x)) < 1e-9, (i, box_g, box_o, o["r50"])
+            ties += 1
+            continue
+        assert (h[i], w[i]) == (g["h"], g["w"])
+        W_img = int(batch.w[i])
+        img = src[int(batch.offset[i]):int(batch.offset[i]) + int(batch.h[i]) * W_img].reshape(-1, W_img)
+        cut = img[g["row0"]:g["row0"] + g["h"], g["col0"]:g["col0"] + g["w"]]
+        got = out[off[i]:off[i] + h[i] * w[i]].reshape(h[i], w[i])
+        assert np.array_equal(got, cut), i
+    print("images", batch.count, "half-integer ties", ties)
+    return inf
+
+
+def test_cutout_large_images(ctx, O):
+    """500 images of 512x512 with one galaxy each, centres up to 20 px off."""
+    batch = synth.make_workload(8, count=200).to("cuda")
+    idx = B.make_index(batch.offset, batch.h, batch.w)
+    pix, cidx, info = ctx.cutout(batch.pix, idx)
+    torch.cuda.synchronize()
+    inf = check_against_oracle(O, batch, pix, cidx, info)
+    # the total of a 512x512 image carries the noise of 262,144 pixels (sigma
+    # 512): for faint galaxies it can be <= 0, and the growth curve falls back
+    assert np.all((inf["status"] == 0) | (inf["status"] == ST["INIT_FALLBACK"]))
+    assert np.mean(inf["status"] == 0) > 0.8
+
+
+def test_cutout_ragged_and_corners(ctx, O):
+    """Images of many sizes, objects at the corners (squares cut to the
+    image), a side factor of 4 and a small maximum side."""
+    rng = np.random.default_rng(5)
+    imgs, offs, hs, ws = [], [], [], []
+    pos = 0
+    for k in range(64):
+        h, w = int(rng.integers(20, 300)), int(rng.integers(20, 300))
+        yy, xx = np.mgrid[0:h, 0:w].astype(np.float64)
+        xc, yc = [(rng.uniform(0, w - 1), rng.uniform(0, h - 1)), (w - 1.4, h - 1.7), (0.3, 0.6),
+                  (w - 1.2, 0.9)][k % 4]
+        sig = rng.uniform(0.8, 6.0)
+        I = 100.0 * np.exp(-((xx - xc) ** 2 + (yy - yc) ** 2) / (2 * sig * sig)) + rng.normal(0, 0.5, (h, w))
+        if k == 7:
+            I[:] = 0.0                       # total <= 0: the fallback radius
+        imgs.append(I.astype(np.float32).ravel())
+        offs.append(pos)
+        hs.append(h)
+        ws.append(w)
+        pos += h * w
+    batch = synth.StampBatch(pix=torch.as_tensor(np.concatenate(imgs)), offset=torch.as_tensor(offs),
+                             h=torch.as_tensor(hs, dtype=torch.int32), w=torch.as_tensor(ws, dtype=torch.int32),
+                             truth={}).to("cuda")
+    idx = B.make_index(batch.offset, batch.h, batch.w)
+    for sf, mn, mx in ((6.0, 8, 128), (4.0, 3, 24)):
+        pix, cidx, info = ctx.cutout(batch.pix, idx, side_factor=sf, min_side=mn, max_side=mx)
+        torch.cuda.synchronize()
+        inf = check_against_oracle(O, batch, pix, cidx, info, sf, mn, mx)
+        assert inf["status"][7] == ST["INIT_FALLBACK"]
+
+
+def test_cutout_bf16(ctx, O):
+    """bf16 images with a per-image scale: the growth curve on the decoded
+    values; the cut-out copies the stored bf16 values."""
+    batch = synth.encode_bf16(synth.make_workload(8, count=40, first=200)).to("cuda")
+    idx = B.make_index(batch.offset, batch.h, batch.w)
+    pix, cidx, info = ctx.cutout(batch.pix, idx, scale=batch.scale)
+    torch.cuda.synchronize()
+    assert pix.dtype == torch.bfloat16
+    check_against_oracle(O, batch, pix, cidx, info)
+
+
+def test_cutout_then_measure(ctx, O):
+    """The cut-outs feed fse_fit_batch directly; the chain agrees with the
+    oracle measuring the oracle's own cut-outs (the parity gate of the
+    estimator)."""
+    batch = synth.make_workload(8, count=120, first=300).to("cuda")
+    idx = B.make_index(batch.offset, batch.h, batch.w)
+    pix, cidx, info = ctx.cutout(batch.pix, idx)
+    out = ctx.fit_batch(pix, cidx, opts=B.default_opts(max_pix=128 * 128))
+    g = B.results(out)
+    cpu = batch.to("cpu")
+    stamps, offs, hs, ws = [], [], [], []
+    pos = 0
+    for i in range(cpu.count):
+        c = O.cutout(cpu.stamp(i).astype(np.float32))
+        s = cpu.stamp(i)[c["row0"]:c["row0"] + c["h"], c["col0"]:c["col0"] + c["w"]].astype(np.float32)
+        stamps.append(s.ravel())
+        offs.append(pos)
+        hs.append(c["h"])
+        ws.append(c["w"])
+        pos += s.size
+    cut = synth.StampBatch(pix=torch.as_tensor(np.concatenate(stamps)), offset=torch.as_tensor(offs),
+                           h=torch.as_tensor(hs, dtype=torch.int32), w=torch.as_tensor(ws, dtype=torch.int32),
+                           truth={})
+    ids = np.arange(cut.count)
+    o = PR.oracle_results(O, cut, ids)
+    rep = PR.compare(g, o, O=O, batch=cut, ids=ids)
+    assert rep["gated"] >= 0.8 * rep["n"], {k: v for k, v in rep.items() if not k.startswith("_")}
+    assert rep["within_tolerance"] == rep["gated"], (rep["failing"], rep["max_err"])
+
+
+def test_cutout_edge_cases(ctx):
+    batch = synth.make_workload(8, count=6, first=400).to("cuda")
+    batch.pix[int(batch.offset[2]) + 1000] = float("nan")
+    idx = B.make_index(batch.offset, batch.h, batch.w)
+    pix, cidx, info = ctx.cutout(batch.pix, idx)
+    inf = B.cutout_info(info)
+    assert inf["status"][2] == ST["NONFINITE"] and inf["h"][2] == 0
+    # too little room: the cut-outs that do not fit are refused, the others copied
+    need = int((inf["h"].astype(np.int64) * inf["w"]).sum())
+    first = int(inf["h"][0]) * int(inf["w"][0])
+    small = torch.full((first,), -7.0, device="cuda")
+    _, _, info2 = ctx.cutout(batch.pix, idx, out=small)
+    inf2 = B.cutout_info(info2)
+    assert inf2["status"][0] == 0 and all(inf2["status"][i] & ST["NO_ROOM"] for i in (1, 3, 4, 5)), inf2
+    assert need > first
+    # argument checks and an empty batch
+    for kw in (dict(side_factor=0.0), dict(min_side=0), dict(max_side=129), dict(min_side=20, max_side=10)):
+        with pytest.raises(B.FseError):
+            ctx.cutout(batch.pix, idx, out=small, **kw)
+    ctx.cutout(batch.pix, idx[:0], out=small)
