@@ -37,7 +37,7 @@ class Opts(ctypes.Structure):
                 ("k_gain", ctypes.c_double), ("sigw_mode", ctypes.c_int),
                 ("n_min", ctypes.c_double), ("n_max", ctypes.c_double),
                 ("re_min", ctypes.c_double), ("re_max_frac", ctypes.c_double),
-                ("lm_lambda0", ctypes.c_double)]
+                ("lm_lambda0", ctypes.c_double), ("supersample", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -100,6 +100,8 @@ class Oracle:
                                      [ctypes.c_int, _dp]
         L.orc_fit_eval.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + \
                                   [_dp, _dp]
+        L.orc_fit_eval_ss.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + \
+                                     [_dp, ctypes.c_int, _dp]
         L.orc_star.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Opts), ctypes.c_int] + \
             [ctypes.c_double] * 5 + [ctypes.POINTER(StarResult)]
         L.orc_star.restype = None
@@ -181,14 +183,15 @@ class Oracle:
         return dict(dx=out[0], dy=out[1], dg1=out[2], dg2=out[3], e1=out[4], e2=out[5],
                     sigw_new=out[6], ok=bool(out[7]))
 
-    def fit_eval(self, I, xc, yc, g1, g2, p, ivar=None):
-        """chi^2, J^T r and J^T J at p = (I0, r_e, n) with centre and g fixed."""
+    def fit_eval(self, I, xc, yc, g1, g2, p, ivar=None, supersample: int = 1):
+        """chi^2, J^T r and J^T J at p = (I0, r_e, n) with centre and g fixed;
+        with supersample S the model of a pixel is the mean of S x S samples."""
         I = _img(I)
         iv = None if ivar is None else _img(ivar)
         pp = np.ascontiguousarray(p, dtype=np.float64)
         out = np.zeros(13)
-        self.L.orc_fit_eval(_as_dp(I), None if iv is None else _as_dp(iv), I.shape[0], I.shape[1],
-                            xc, yc, g1, g2, _as_dp(pp), _as_dp(out))
+        self.L.orc_fit_eval_ss(_as_dp(I), None if iv is None else _as_dp(iv), I.shape[0], I.shape[1],
+                               xc, yc, g1, g2, _as_dp(pp), int(supersample), _as_dp(out))
         return out[0], out[1:4].copy(), out[4:].reshape(3, 3).copy()
 
     def star(self, I, xc, yc, g1, g2, size0, profile: str = "gauss", opts: Opts | None = None) -> dict:

@@ -83,6 +83,8 @@ typedef struct {
     double re_min;       /* lower bound on r_e, px                       */
     double re_max_frac;  /* upper bound on r_e = re_max_frac * max(h,w)  */
     double lm_lambda0;
+    int    supersample;  /* S: the model of a pixel is the mean of S x S point
+                            samples on a regular sub-grid (1: the pixel centre) */
 } orc_opts;
 
 typedef struct {
@@ -123,6 +125,7 @@ void orc_default_opts(orc_opts *o)
     o->re_min = 0.2;
     o->re_max_frac = 2.0;
     o->lm_lambda0 = 1e-3;
+    o->supersample = 1;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -438,12 +441,34 @@ static void moment_iterate(const double *I, int h, int w, const orc_opts *o, int
 /* ------------------------------------------------------------------------ */
 typedef struct {
     const double *I, *ivar;
-    const double *r;      /* Sérsic radius of each pixel, R(g)/(1-|g|) */
-    int npix;
+    const double *r;      /* Sérsic radius R(g)/(1-|g|) of each point sample,
+                             ns per pixel (pixel i: r[i*ns ... i*ns + ns-1]) */
+    int npix, ns;
 } fit_data;
 
+/* Sérsic radii of the point samples of every pixel: with supersample S the
+ * S x S sub-grid points (j + (a + 1/2)/S - 1/2, i + (c + 1/2)/S - 1/2) of
+ * pixel (i, j), S = 1 the pixel centre (Sec. 4.1 samples the profile at the
+ * pixels; the mean over a finer grid approaches the pixel integral that
+ * pixelation calls for, Sec. 4.2). */
+static double *sample_radii(int h, int w, int S, double xc, double yc, double g1, double g2)
+{
+    double gabs = sqrt(g1 * g1 + g2 * g2);
+    double *r = (double *)malloc(sizeof(double) * h * w * S * S);
+    for (int i = 0; i < h; ++i)
+        for (int j = 0; j < w; ++j)
+            for (int c = 0; c < S; ++c)
+                for (int a = 0; a < S; ++a) {
+                    double oy = (c + 0.5) / S - 0.5, ox = (a + 0.5) / S - 0.5;
+                    double R2 = ellip_R2(j + ox - xc, i + oy - yc, g1, g2);
+                    r[((i * w + j) * S + c) * S + a] = sqrt(R2 > 0.0 ? R2 : 0.0) / (1.0 - gabs);
+                }
+    return r;
+}
+
 /* chi^2 (Eq. 11) and, if H != NULL, the normal equations J^T W J, J^T W r
- * of the model m = I0 exp(-b (r/r_e)^(1/n)) with respect to (I0, r_e, n). */
+ * of the model m = I0 exp(-b (r/r_e)^(1/n)) with respect to (I0, r_e, n).
+ * A pixel's model and derivatives are the means over its point samples. */
 static double fit_eval(const fit_data *d, const double p[3], double H[3][3], double g[3])
 {
     double I0 = p[0], re = p[1], n = p[2];
@@ -452,17 +477,23 @@ static double fit_eval(const fit_data *d, const double p[3], double H[3][3], dou
     if (H) { memset(H, 0, 9 * sizeof(double)); memset(g, 0, 3 * sizeof(double)); }
     for (int i = 0; i < d->npix; ++i) {
         double wgt = d->ivar ? d->ivar[i] : 1.0;
-        double x = d->r[i] / re;
-        double u = x > 0.0 ? pow(x, 1.0 / n) : 0.0;
-        double E = exp(-b * u);
+        double E = 0.0, J[3] = { 0.0, 0.0, 0.0 };
+        for (int k = 0; k < d->ns; ++k) {
+            double x = d->r[i * d->ns + k] / re;
+            double u = x > 0.0 ? pow(x, 1.0 / n) : 0.0;
+            double Ek = exp(-b * u);
+            E += Ek;
+            J[1] += I0 * Ek * b * u / (n * re);                              /* dm/dr_e */
+            if (x > 0.0) J[2] += I0 * Ek * u * (b * log(x) / (n * n) - db);   /* dm/dn */
+        }
+        E /= d->ns;
+        J[0] = E;                                                             /* dm/dI0 */
+        J[1] /= d->ns;
+        J[2] /= d->ns;
         double m = I0 * E;
         double res = m - d->I[i];
         chi2 += wgt * res * res;
         if (!H) continue;
-        double J[3];
-        J[0] = E;                                           /* dm/dI0 */
-        J[1] = m * b * u / (n * re);                         /* dm/dr_e */
-        J[2] = x > 0.0 ? m * u * (b * log(x) / (n * n) - db) : 0.0;   /* dm/dn */
         for (int a = 0; a < 3; ++a) {
             g[a] += wgt * J[a] * res;
             for (int c = 0; c < 3; ++c) H[a][c] += wgt * J[a] * J[c];
@@ -485,8 +516,12 @@ static double profiled_eval(const fit_data *d, double re, double n, double *I0_o
     double sIf = 0.0, sff = 0.0;
     for (int i = 0; i < d->npix; ++i) {
         double wgt = d->ivar ? d->ivar[i] : 1.0;
-        double x = d->r[i] / re;
-        double f = exp(-b * (x > 0.0 ? pow(x, 1.0 / n) : 0.0));
+        double f = 0.0;
+        for (int k = 0; k < d->ns; ++k) {
+            double x = d->r[i * d->ns + k] / re;
+            f += exp(-b * (x > 0.0 ? pow(x, 1.0 / n) : 0.0));
+        }
+        f /= d->ns;
         sIf += wgt * d->I[i] * f;
         sff += wgt * f * f;
     }
@@ -534,13 +569,9 @@ static void fit_stamp(const double *I, const double *ivar, int h, int w, const o
 {
     int npix = h * w;
     double gabs = sqrt(g1 * g1 + g2 * g2);
-    double *r = (double *)malloc(sizeof(double) * npix);
-    for (int i = 0; i < h; ++i)
-        for (int j = 0; j < w; ++j) {
-            double R2 = ellip_R2(j - xc, i - yc, g1, g2);
-            r[i * w + j] = sqrt(R2 > 0.0 ? R2 : 0.0) / (1.0 - gabs);
-        }
-    fit_data d = { I, ivar, r, npix };
+    int S = o->supersample > 1 ? o->supersample : 1;
+    double *r = sample_radii(h, w, S, xc, yc, g1, g2);
+    fit_data d = { I, ivar, r, npix, S * S };
     double re_max = o->re_max_frac * (h > w ? h : w);
     /* Start: r_e from the weight size, n the best of {0.5, 1, 2, 4}. */
     double re0 = SQRT_2LN2 * sw / (1.0 - gabs);
@@ -686,23 +717,24 @@ void orc_moment_step(const double *I, int h, int w, double xc, double yc, double
 
 /* chi^2 and normal equations at given (I0, r_e, n) with the centre and
  * ellipticity fixed; out = {chi2, g[3], H[9]}. */
-void orc_fit_eval(const double *I, const double *ivar, int h, int w, double xc, double yc,
-                  double g1, double g2, const double p[3], double out[13])
+void orc_fit_eval_ss(const double *I, const double *ivar, int h, int w, double xc, double yc,
+                     double g1, double g2, const double p[3], int supersample, double out[13])
 {
     int npix = h * w;
-    double gabs = sqrt(g1 * g1 + g2 * g2);
-    double *r = (double *)malloc(sizeof(double) * npix);
-    for (int i = 0; i < h; ++i)
-        for (int j = 0; j < w; ++j) {
-            double R2 = ellip_R2(j - xc, i - yc, g1, g2);
-            r[i * w + j] = sqrt(R2 > 0.0 ? R2 : 0.0) / (1.0 - gabs);
-        }
-    fit_data d = { I, ivar, r, npix };
+    int S = supersample > 1 ? supersample : 1;
+    double *r = sample_radii(h, w, S, xc, yc, g1, g2);
+    fit_data d = { I, ivar, r, npix, S * S };
     double H[3][3], g[3];
     out[0] = fit_eval(&d, p, H, g);
     for (int a = 0; a < 3; ++a) out[1 + a] = g[a];
     for (int a = 0; a < 3; ++a) for (int c = 0; c < 3; ++c) out[4 + 3 * a + c] = H[a][c];
     free(r);
+}
+
+void orc_fit_eval(const double *I, const double *ivar, int h, int w, double xc, double yc,
+                  double g1, double g2, const double p[3], double out[13])
+{
+    orc_fit_eval_ss(I, ivar, h, w, xc, yc, g1, g2, p, 1, out);
 }
 
 /* Gradient of chi^2 (Eq. 11) for the elliptical Sérsic model of Eq. 10 with

@@ -37,10 +37,10 @@ MUTATIONS = {
     # flux closed form: axis ratio without the (1+|g|)
     "flux_q": ("double q = (1.0 - gabs) / (1.0 + gabs);\n    return", "double q = (1.0 - gabs);\n    return"),
     # Sérsic radius not divided by (1 - |g|)
-    "sersic_radius": ("r[i * w + j] = sqrt(R2 > 0.0 ? R2 : 0.0) / (1.0 - gabs);",
-                      "r[i * w + j] = sqrt(R2 > 0.0 ? R2 : 0.0);"),
+    "sersic_radius": ("r[((i * w + j) * S + c) * S + a] = sqrt(R2 > 0.0 ? R2 : 0.0) / (1.0 - gabs);",
+                      "r[((i * w + j) * S + c) * S + a] = sqrt(R2 > 0.0 ? R2 : 0.0);"),
     # dm/dr_e loses the 1/n
-    "jac_re": ("J[1] = m * b * u / (n * re);", "J[1] = m * b * u / re;"),
+    "jac_re": ("J[1] += I0 * Ek * b * u / (n * re);", "J[1] += I0 * Ek * b * u / re;"),
     # dm/dn: sign of the b' term
     "jac_n_sign": ("(b * log(x) / (n * n) - db)", "(b * log(x) / (n * n) + db)"),
     # Eq. 13: amplitude normalised by sqrt
@@ -90,6 +90,13 @@ MUTATIONS = {
                       "int r0 = pr - (int)(side / 2) + 1, c0 = pc - (int)(side / 2);"),
     # cut-out: the far edge not cut to the image
     "cutout_clip": ("if (c1 > W) c1 = W;", "if (c1 > W + 1) c1 = W + 1;"),
+    # pixel-integrated model: the sub-grid not centred on the pixel
+    "ss_subgrid": ("double oy = (c + 0.5) / S - 0.5, ox = (a + 0.5) / S - 0.5;",
+                   "double oy = (c + 0.5) / S - 0.5, ox = (a + 0.5) / S;"),
+    # pixel-integrated model: the amplitude's template averaged over one sample too few
+    "ss_template_mean": ("        f /= d->ns;", "        f /= (d->ns > 1 ? d->ns - 1 : 1);"),
+    # pixel-integrated model: dm/dn summed instead of averaged
+    "ss_jac_n_mean": ("        J[2] /= d->ns;", ""),
     # non-finite input no longer flagged
     "nonfinite_check": ("if (!isfinite(I[p])) { *status |= ORC_NONFINITE; return 0; }", ""),
 }
