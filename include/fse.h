@@ -129,6 +129,11 @@ typedef struct {
     int32_t warps_per_stamp;/* warps sharing one stamp (whole chain only): 0 (library
                                choice: 1 up to 48x48 tiles, then 2, 4, 8 up to 128x128),
                                1, 2, 4 or 8; warps_per_cta must be a multiple     (0)  */
+    int32_t supersample;    /* S in [1, 8]: the fit's Sersic model of a pixel is the mean
+                               of S x S point samples on a regular sub-grid, the pixel
+                               integral to O(1/S^2) (pixelation, Sec. 4.2); 0 or 1: the
+                               pixel centre (Sec. 4.1).  S > 1 runs one warp per stamp
+                               and costs about S^2 times the fit.              (1)       */
 } fse_opts;
 
 /* Per-stamp result (64 bytes). */

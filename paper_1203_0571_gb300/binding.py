@@ -51,7 +51,8 @@ class Opts(ctypes.Structure):
                 ("max_pix", ctypes.c_int32), ("n_min", ctypes.c_double), ("n_max", ctypes.c_double),
                 ("re_min", ctypes.c_double), ("re_max_frac", ctypes.c_double),
                 ("lm_lambda0", ctypes.c_double), ("flags", ctypes.c_uint32),
-                ("warps_per_cta", ctypes.c_int32), ("warps_per_stamp", ctypes.c_int32)]
+                ("warps_per_cta", ctypes.c_int32), ("warps_per_stamp", ctypes.c_int32),
+                ("supersample", ctypes.c_int32)]
 
 
 RESULT_DTYPE = np.dtype([("x0", "<f4"), ("y0", "<f4"), ("e1", "<f4"), ("e2", "<f4"), ("I0", "<f4"),

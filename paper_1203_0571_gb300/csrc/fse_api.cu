@@ -117,6 +117,9 @@ int check_opts(fse_ctx* ctx, const fse_opts* o) {
         return set_error(ctx, FSE_EINVAL, "warps_per_cta must be a multiple of warps_per_stamp");
     if (o->flags & ~static_cast<uint32_t>(FSE_FLAG_GRAPH))
         return set_error(ctx, FSE_EINVAL, "unknown bits in flags");
+    if (o->supersample < 0 || o->supersample > 8) return set_error(ctx, FSE_EINVAL, "supersample must be in [0, 8]");
+    if (o->supersample > 1 && ws > 1)
+        return set_error(ctx, FSE_EINVAL, "supersample > 1 runs one warp per stamp (warps_per_stamp 0 or 1)");
     return FSE_OK;
 }
 
@@ -136,6 +139,7 @@ fse::DevOpts dev_opts(const fse_opts& o) {
     d.re_min = static_cast<float>(o.re_min);
     d.re_max_frac = static_cast<float>(o.re_max_frac);
     d.lm_lambda0 = static_cast<float>(o.lm_lambda0);
+    d.supersample = o.supersample > 1 ? o.supersample : 1;
     return d;
 }
 
@@ -146,7 +150,7 @@ void launch_shape(const fse_opts& o, int max_pix, int stage, int* wpc, int* nw) 
     int dw = 0, dn = 0;
     fse::choose_launch(max_pix, &dw, &dn);
     int n = o.warps_per_stamp > 0 ? o.warps_per_stamp : (o.warps_per_cta > 0 ? 1 : dn);
-    if (stage != fse::kStageAll) n = 1;
+    if (stage != fse::kStageAll || o.supersample > 1) n = 1;
     int w = o.warps_per_cta > 0 ? o.warps_per_cta : (n == dn ? dw : n);
     if (n == 1 && o.warps_per_cta <= 0 && dn != 1) {
         // one warp per stamp on a large tile: as many as fit, up to four
@@ -253,7 +257,7 @@ int ragged_workspace(fse_ctx* ctx, int64_t count) {
 // autotuner's choice, else the library default for the class's tile.
 void class_shape(const fse_ctx* ctx, const fse::LaunchArgs& a, const fse_opts& o, int k, int* wpc,
                  int* nw) {
-    if (o.warps_per_cta > 0 || o.warps_per_stamp > 0) {
+    if (o.warps_per_cta > 0 || o.warps_per_stamp > 0 || o.supersample > 1) {
         launch_shape(o, fse::kClassPix[k], fse::kStageAll, wpc, nw);
         return;
     }
@@ -357,6 +361,7 @@ void fse_opts_default(fse_opts* o) {
     o->flags = 0;
     o->warps_per_cta = 0;
     o->warps_per_stamp = 0;
+    o->supersample = 1;
 }
 
 int fse_create(fse_ctx** out, int device) {
@@ -663,6 +668,7 @@ int fse_autotune(fse_ctx* ctx, const void* pix, int dtype, const float* scale,
             static const int kNw[10] = {1, 1, 1, 1, 2, 2, 2, 4, 4, 8};
             static const int kGr[10] = {1, 2, 4, 8, 1, 2, 4, 1, 2, 1};
             const int nw = kNw[cand], groups = kGr[cand];
+            if (nw > 1 && a.opts.supersample > 1) continue;
             if (fse::smem_per_group(fse::kClassPix[k], iv != 0, nw) * groups > 227 * 1024) continue;
             const int wpc = nw * groups;
             float t_min = 1e30f;

@@ -26,6 +26,7 @@ struct DevOpts {
     int max_pix;
     float n_min, n_max, re_min, re_max_frac;
     float lm_lambda0;
+    int supersample;     // S > 1: the fit's model is the mean of S x S samples per pixel
 };
 
 struct LaunchArgs {

@@ -931,6 +931,43 @@ __device__ InitOut stamp_init(const float* s, int h, int w, int npix, const Grp<
 // of (I0, r_e, n) and, after eliminating I0 at its closed form (Eq. 13), the
 // reduced 2x2 problem in (r_e, n):
 //   dm/dr_e = I0 b v / (n r_e),  dm/dn = I0 (b ln2 / n^2) v a - I0 b'(n) v.
+// Pixel-integrated model (fse_opts.supersample = S > 1): a pixel's model and
+// its derivatives are the means over the S x S sub-grid points
+// (t1 + (a + 1/2)/S - 1/2, t2 + (c + 1/2)/S - 1/2) of the pixel.  Everything the
+// fit sums is linear in those means, so the sums and the solves are those of
+// the pixel-centre model with each per-pixel factor replaced by its mean.
+struct SubGeom {
+    float A, B, G4;    // R^2 = A t1^2 + B t2^2 - G4 t1 t2 (Eq. A1)
+    int S;
+    float invS, invS2;
+};
+
+__device__ __forceinline__ SubGeom sub_geom(const MomState& st, int S) {
+    const float gg = st.g1 * st.g1 + st.g2 * st.g2;
+    SubGeom q;
+    q.A = 1.f + gg - 2.f * st.g1;
+    q.B = 1.f + gg + 2.f * st.g1;
+    q.G4 = 4.f * st.g2;
+    q.S = S;
+    q.invS = 1.f / static_cast<float>(S);
+    q.invS2 = q.invS * q.invS;
+    return q;
+}
+
+// a = log2(r / r_e) of one sub-grid point (r = R / (1 - |g|); c0 = log2 r_e + log2(1 - |g|)).
+__device__ __forceinline__ float sub_a(const SubGeom& q, float t1, float t2, int a, int c, float c0) {
+    const float u1 = t1 + (static_cast<float>(a) + 0.5f) * q.invS - 0.5f;
+    const float u2 = t2 + (static_cast<float>(c) + 0.5f) * q.invS - 0.5f;
+    const float R2 = fmaf(q.A, u1 * u1, fmaf(q.B, u2 * u2, -q.G4 * (u1 * u2)));
+    return (R2 > 0.f ? 0.5f * log2f(R2) : -1000.f) - c0;
+}
+
+// Offsets of a pixel from the fixed centre.
+__device__ __forceinline__ void pix_t(const PixelWalk& pw, const MomState& st, float* t1, float* t2) {
+    *t1 = static_cast<float>(pw.col - st.xi) - st.xf;
+    *t2 = static_cast<float>(pw.row - st.yi) - st.yf;
+}
+
 struct FitEval {
     float I0;       // Eq. 13 at (r_e, n)
     float chi2;     // Eq. 11 at that I0
@@ -939,10 +976,11 @@ struct FitEval {
     float corr;     // (I0 - I0g)^2 sum E^2 / chi2: cancellation in chi2 when large
 };
 
-template <bool IVAR, int NW>
+template <bool IVAR, int NW, bool SUP = false>
 __device__ FitEval fit_eval(const float* __restrict__ s, const float* __restrict__ L,
                             const float* __restrict__ sq, int npix, const Grp<NW>& g, float I0g,
-                            float re, float n, float lq) {
+                            float re, float n, float lq, int w = 0, const MomState* st = nullptr,
+                            int S = 1) {
     float b, db;
     bn_eval_f(n, &b, &db);
     const float inv_n = 1.f / n;
@@ -951,18 +989,48 @@ __device__ FitEval fit_eval(const float* __restrict__ s, const float* __restrict
     float acc[10];
 #pragma unroll
     for (int i = 0; i < 10; ++i) acc[i] = 0.f;
+    SubGeom sg;
+    if constexpr (SUP) sg = sub_geom(*st, S);
+    PixelWalk pw(g.t, SUP ? w : 1, Grp<NW>::NT);
 #pragma unroll 2
     for (int p = g.t; p < npix; p += Grp<NW>::NT) {
-        const float a = L[p] - c0;
-        const float u = ex2(a * inv_n);
-        float E = ex2(u * nbl);
+        float E, v = 0.f, va = 0.f, u = 0.f, a = 0.f;
+        if constexpr (SUP) {
+            float t1, t2;
+            pix_t(pw, *st, &t1, &t2);
+            pw.next();
+            E = 0.f;
+            for (int ic = 0; ic < sg.S; ++ic)
+                for (int ia = 0; ia < sg.S; ++ia) {
+                    const float as = sub_a(sg, t1, t2, ia, ic, c0);
+                    const float us = ex2(as * inv_n);
+                    const float es = ex2(us * nbl);
+                    E += es;
+                    v = fmaf(es, us, v);
+                    va = fmaf(es * us, as, va);
+                }
+            E *= sg.invS2;
+            v *= sg.invS2;
+            va *= sg.invS2;
+        } else {
+            a = L[p] - c0;
+            u = ex2(a * inv_n);
+            E = ex2(u * nbl);
+        }
         float r = fmaf(I0g, E, -s[p]);
         if (IVAR) {
             const float q = sq[p];
             E *= q;
             r *= q;
+            if constexpr (SUP) {
+                v *= q;
+                va *= q;
+            }
         }
-        const float v = E * u, va = v * a;
+        if constexpr (!SUP) {
+            v = E * u;
+            va = v * a;
+        }
         acc[0] = fmaf(E, E, acc[0]);
         acc[1] = fmaf(E, v, acc[1]);
         acc[2] = fmaf(E, va, acc[2]);
@@ -1000,10 +1068,11 @@ __device__ FitEval fit_eval(const float* __restrict__ s, const float* __restrict
 
 // Start: r_e from the weight size, n the candidate of {0.5, 1, 2, 4} with the
 // lowest chi^2 at its closed-form I0 (chi^2 = sum I^2 - (sum I E)^2 / sum E^2).
-template <bool IVAR, int NW>
+template <bool IVAR, int NW, bool SUP = false>
 __device__ void fit_start(const float* __restrict__ s, const float* __restrict__ L,
                           const float* __restrict__ sq, int npix, const Grp<NW>& g, float re0,
-                          float lq, float* n0, float* I00) {
+                          float lq, float* n0, float* I00, int w = 0, const MomState* st = nullptr,
+                          int S = 1) {
     const float nc[4] = {0.5f, 1.f, 2.f, 4.f};
     float inv_n[4], nbl[4];
 #pragma unroll
@@ -1017,18 +1086,41 @@ __device__ void fit_start(const float* __restrict__ s, const float* __restrict__
     float acc[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) acc[i] = 0.f;
+    SubGeom sg;
+    if constexpr (SUP) sg = sub_geom(*st, S);
+    PixelWalk pw(g.t, SUP ? w : 1, Grp<NW>::NT);
     for (int p = g.t; p < npix; p += Grp<NW>::NT) {
-        const float a = L[p] - c0;
         float I = s[p];
         const float q = IVAR ? sq[p] : 1.f;
         if (IVAR) I *= q;
         acc[8] = fmaf(I, I, acc[8]);
+        if constexpr (SUP) {
+            float t1, t2;
+            pix_t(pw, *st, &t1, &t2);
+            pw.next();
+            float Em[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int ic = 0; ic < sg.S; ++ic)
+                for (int ia = 0; ia < sg.S; ++ia) {
+                    const float as = sub_a(sg, t1, t2, ia, ic, c0);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            float E = ex2(ex2(a * inv_n[c]) * nbl[c]);
-            if (IVAR) E *= q;
-            acc[2 * c] = fmaf(E, E, acc[2 * c]);
-            acc[2 * c + 1] = fmaf(E, I, acc[2 * c + 1]);
+                    for (int c = 0; c < 4; ++c) Em[c] += ex2(ex2(as * inv_n[c]) * nbl[c]);
+                }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float E = Em[c] * sg.invS2;
+                if (IVAR) E *= q;
+                acc[2 * c] = fmaf(E, E, acc[2 * c]);
+                acc[2 * c + 1] = fmaf(E, I, acc[2 * c + 1]);
+            }
+        } else {
+            const float a = L[p] - c0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float E = ex2(ex2(a * inv_n[c]) * nbl[c]);
+                if (IVAR) E *= q;
+                acc[2 * c] = fmaf(E, E, acc[2 * c]);
+                acc[2 * c + 1] = fmaf(E, I, acc[2 * c + 1]);
+            }
         }
     }
     g.allsum(acc);
@@ -1079,6 +1171,21 @@ __device__ __noinline__ double bright_r2(const BrightModel& bm, double t1, doubl
     const double R2 = bm.A * t1 * t1 + bm.B * t2 * t2 - bm.G4 * t1 * t2;
     const double u = exp((0.5 * log(R2) - bm.ln1g - bm.lnre) * bm.inv_n);
     const double r = (bm.I0 * exp(-bm.b * u) - pix) * q;
+    return r * r;
+}
+
+// The same for the pixel-integrated model: the mean over the S x S sub-grid.
+__device__ __noinline__ double bright_r2_sub(const BrightModel& bm, double t1, double t2, float pix,
+                                             float q, int S) {
+    double m = 0.0;
+    for (int c = 0; c < S; ++c)
+        for (int a = 0; a < S; ++a) {
+            const double u1 = t1 + (a + 0.5) / S - 0.5, u2 = t2 + (c + 0.5) / S - 0.5;
+            const double R2 = bm.A * u1 * u1 + bm.B * u2 * u2 - bm.G4 * u1 * u2;
+            const double u = exp((0.5 * log(R2) - bm.ln1g - bm.lnre) * bm.inv_n);
+            m += exp(-bm.b * u);
+        }
+    const double r = (bm.I0 * m / (static_cast<double>(S) * S) - pix) * q;
     return r * r;
 }
 
@@ -1159,11 +1266,11 @@ __device__ Precise refine_tail(const float (&rh)[10], const float (&rl)[10], con
     return o;
 }
 
-template <bool IVAR, int NW>
+template <bool IVAR, int NW, bool SUP = false>
 __device__ Precise fit_refine(const float* __restrict__ s, const float* __restrict__ L,
                               const float* __restrict__ sq, int w, int npix, const Grp<NW>& g,
                               float I0g,
-                              float re, float n, float lq, const MomState& st) {
+                              float re, float n, float lq, const MomState& st, int S = 1) {
     float bf, dbf;
     bn_eval_f(n, &bf, &dbf);
     const float inv_n = 1.f / n;
@@ -1191,6 +1298,77 @@ __device__ Precise fit_refine(const float* __restrict__ s, const float* __restri
 #pragma unroll
     for (int i = 0; i < 4; ++i) T[i] = 0.f;
     PixelWalk pw(g.t, w, Grp<NW>::NT);
+    if constexpr (SUP) {
+        // the pixel-integrated model: every factor below is a mean over the sub-grid
+        const SubGeom sg = sub_geom(st, S);
+        for (int p = g.t; p < npix; p += Grp<NW>::NT) {
+            float t1, t2;
+            pix_t(pw, st, &t1, &t2);
+            float E = 0.f, v = 0.f, va = 0.f, m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
+            for (int ic = 0; ic < sg.S; ++ic)
+                for (int ia = 0; ia < sg.S; ++ia) {
+                    const float as = sub_a(sg, t1, t2, ia, ic, c0);
+                    const float us = exp2_acc(as * inv_n);
+                    const float es = exp2_acc(us * nbl);
+                    const float eu = es * us, eua = eu * as, euu = eu * us;
+                    E += es;
+                    v += eu;
+                    va += eua;
+                    m0 = fmaf(eua, as, m0);        // E u a^2
+                    m1 += euu;                     // E u^2
+                    m2 = fmaf(euu, as, m2);        // E u^2 a
+                    m3 = fmaf(euu * as, as, m3);   // E u^2 a^2
+                }
+            E *= sg.invS2;
+            v *= sg.invS2;
+            va *= sg.invS2;
+            m0 *= sg.invS2;
+            m1 *= sg.invS2;
+            m2 *= sg.invS2;
+            m3 *= sg.invS2;
+            float r = fmaf(I0g, E, -s[p]);
+            float rr_hi = 0.f, rr_lo = 0.f;
+            bool bright = false;
+            const float q = IVAR ? sq[p] : 1.f;
+            if (check_bright && fabsf(I0g * E) * q > kBrightSigma) {
+                const double rrd = bright_r2_sub(bm, static_cast<double>(pw.col - st.xi) - st.xf,
+                                                 static_cast<double>(pw.row - st.yi) - st.yf, s[p], q, sg.S);
+                rr_hi = static_cast<float>(rrd);
+                rr_lo = static_cast<float>(rrd - rr_hi);
+                bright = true;
+            }
+            pw.next();
+            if (IVAR) {
+                E *= q;
+                r *= q;
+                v *= q;
+                va *= q;
+                m0 *= q;
+                m1 *= q;
+                m2 *= q;
+                m3 *= q;
+            }
+            df_add(rh[0], rl[0], E * E);
+            df_add(rh[1], rl[1], E * v);
+            df_add(rh[2], rl[2], E * va);
+            df_add(rh[3], rl[3], v * v);
+            df_add(rh[4], rl[4], v * va);
+            df_add(rh[5], rl[5], va * va);
+            df_add(rh[6], rl[6], E * r);
+            df_add(rh[7], rl[7], v * r);
+            df_add(rh[8], rl[8], va * r);
+            T[0] = fmaf(r, m0, T[0]);
+            T[1] = fmaf(r, m1, T[1]);
+            T[2] = fmaf(r, m2, T[2]);
+            T[3] = fmaf(r, m3, T[3]);
+            if (bright) {
+                df_add(rh[9], rl[9], rr_hi);
+                rl[9] += rr_lo;
+            } else {
+                df_add(rh[9], rl[9], r * r);
+            }
+        }
+    } else
     for (int p = g.t; p < npix; p += Grp<NW>::NT) {
         const float a = L[p] - c0;
         const float u = exp2_acc(a * inv_n);
@@ -1259,15 +1437,17 @@ struct FitOut {
 
 // Levenberg-Marquardt over theta = (r_e, n) with I0 at its closed form after
 // every pass; damping by the gain ratio rho (Nielsen 1999).
-template <bool IVAR, int NW>
+template <bool IVAR, int NW, bool SUP = false>
 __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, int w, int npix,
                              const Grp<NW>& g, const DevOpts& o, const MomState& st,
                              uint32_t& status) {
     // per-pixel 0.5 log2 R^2 about the fixed centre with the fixed ellipticity
+    // (the pixel-integrated model evaluates its sub-grid points as it goes)
     const float g1 = st.g1, g2 = st.g2;
     const float gg = g1 * g1 + g2 * g2;
     const float A = 1.f + gg - 2.f * g1, B = 1.f + gg + 2.f * g1, G4 = 4.f * g2;
-    {
+    const int S = SUP ? o.supersample : 1;
+    if constexpr (!SUP) {
         PixelWalk pw(g.t, w, Grp<NW>::NT);
         for (int p = g.t; p < npix; p += Grp<NW>::NT) {
             const float t1 = static_cast<float>(pw.col - st.xi) - st.xf;
@@ -1285,7 +1465,7 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
     float re = static_cast<float>(kSqrt2Ln2) * st.sw / (1.f - gabs);
     re = re < re_min ? re_min : (re > re_max ? re_max : re);
     float n, I0g;
-    fit_start<IVAR>(s, L, sq, npix, g, re, lq, &n, &I0g);
+    fit_start<IVAR, NW, SUP>(s, L, sq, npix, g, re, lq, &n, &I0g, w, &st, S);
     // One evaluation site: every pass of the profile goes through the single
     // fit_eval call at the top of this loop (first the start, then each trial
     // step, and a repeat at I0* when the amplitude jumped).
@@ -1297,7 +1477,7 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
     int evals = 0, band_accepts = 0, it = 0;
 #pragma unroll 1
     for (;;) {
-        const FitEval ev = fit_eval<IVAR>(s, L, sq, npix, g, I0t, ret, nt, lq);
+        const FitEval ev = fit_eval<IVAR, NW, SUP>(s, L, sq, npix, g, I0t, ret, nt, lq, w, &st, S);
         ++evals;
         if (ev.corr > 0.5f && !retried) {
             // the amplitude moved so far that chi^2 lost precision: evaluate again at I0*
@@ -1392,7 +1572,7 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
         int passes = 0;
 #pragma unroll 1
         for (;;) {
-            const Precise E = fit_refine<IVAR>(s, L, sq, w, npix, g, tI0, te, tn, lq, st);
+            const Precise E = fit_refine<IVAR, NW, SUP>(s, L, sq, w, npix, g, tI0, te, tn, lq, st, S);
             ++passes;
             // a step within 1e-2 is taken on the Newton model alone: its chi^2
             // decrease can be below the rounding of the fp32 model values
@@ -1453,7 +1633,7 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
 // ------------------------------------------------------------------ kernel
 // NW warps share each stamp (a stamp group); a CTA holds blockDim.x / (32 NW)
 // groups, each with its own tile and, for NW > 1, named barrier 1 + group.
-template <int STAGE, int DT, bool IVAR, int NW>
+template <int STAGE, int DT, bool IVAR, int NW, bool SUP = false>
 // 168 registers per thread let three CTAs of four warps share an SM (the
 // launch shape of 48x48 and smaller tiles); more would leave two.
 __global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
@@ -1602,7 +1782,7 @@ __global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
             if (!(status & FSE_ST_MOM_CONVERGED)) skip = true;
         }
         if (!skip && (STAGE == kStageFit || STAGE == kStageAll)) {
-            const FitOut f = sersic_fit<IVAR>(s, aux, ivbuf, h, w, npix, g, o, st, status);
+            const FitOut f = sersic_fit<IVAR, NW, SUP>(s, aux, ivbuf, h, w, npix, g, o, st, status);
             res.I0 = static_cast<float>(f.I0);
             res.re = static_cast<float>(f.re);
             res.n = static_cast<float>(f.n);
@@ -1616,12 +1796,12 @@ __global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
     }
 }
 
-template <int STAGE, int DT, bool IVAR, int NW>
+template <int STAGE, int DT, bool IVAR, int NW, bool SUP = false>
 cudaError_t launch_t(const LaunchArgs& a, cudaStream_t stream) {
     const int groups = a.warps_per_cta / NW;
     if (groups < 1 || groups * NW != a.warps_per_cta || groups > 15) return cudaErrorInvalidValue;
     const size_t smem = group_bytes(a.opts.max_pix, IVAR, NW) * groups;
-    auto kern = estimator_kernel<STAGE, DT, IVAR, NW>;
+    auto kern = estimator_kernel<STAGE, DT, IVAR, NW, SUP>;
     // the shared-memory opt-in is raised once per instantiation and size (per device)
     static size_t opted[64] = {0};
     int dev = 0;
@@ -1654,6 +1834,13 @@ cudaError_t launch_t(const LaunchArgs& a, cudaStream_t stream) {
 template <int STAGE, int DT, bool IVAR>
 cudaError_t launch_nw(const LaunchArgs& a, cudaStream_t stream) {
     const int nw = a.warps_per_stamp > 1 ? a.warps_per_stamp : 1;
+    if constexpr (STAGE == kStageAll || STAGE == kStageFit) {
+        // the pixel-integrated model: one warp per stamp
+        if (a.opts.supersample > 1) {
+            if (nw != 1) return cudaErrorInvalidValue;
+            return launch_t<STAGE, DT, IVAR, 1, true>(a, stream);
+        }
+    }
     if constexpr (STAGE == kStageAll) {
         switch (nw) {
             case 1: return launch_t<STAGE, DT, IVAR, 1>(a, stream);

@@ -43,9 +43,10 @@ def oracle_results(O, batch, ids, stage="measure", init=None, ivar=None, threads
     return res
 
 
-def jtj_condition(O, stamp, r, ivar=None):
+def jtj_condition(O, stamp, r, ivar=None, supersample=1):
     """Condition number of the Jacobi-scaled J^T J at the oracle's optimum."""
-    _, _, H = O.fit_eval(stamp, r["x0"], r["y0"], r["e1"], r["e2"], [r["I0"], r["re"], r["n"]], ivar=ivar)
+    _, _, H = O.fit_eval(stamp, r["x0"], r["y0"], r["e1"], r["e2"], [r["I0"], r["re"], r["n"]], ivar=ivar,
+                         supersample=supersample)
     d = np.sqrt(np.abs(np.diag(H)))
     if not np.all(d > 0):
         return np.inf
@@ -55,7 +56,7 @@ def jtj_condition(O, stamp, r, ivar=None):
 
 
 def compare(gpu, orc, keys=("x0", "y0", "e1", "e2", "re", "n", "flux", "chi2"), fit=True,
-            O=None, batch=None, ids=None, ivar=None):
+            O=None, batch=None, ids=None, ivar=None, supersample=1):
     """Per-stamp errors and the gate verdict.  Returns a report dict."""
     gs, os_ = gpu["status"].astype(np.int64), orc["status"].astype(np.int64)
     conv = (gs & MOM_CONVERGED).astype(bool) & (os_ & MOM_CONVERGED).astype(bool)
@@ -81,7 +82,7 @@ def compare(gpu, orc, keys=("x0", "y0", "e1", "e2", "re", "n", "flux", "chi2"), 
                 if ivar is not None:
                     o = int(batch.offset[i])
                     iv = ivar[o:o + int(batch.h[i]) * int(batch.w[i])].reshape(batch.h[i], batch.w[i])
-                excluded_cond[j] = jtj_condition(O, batch.stamp(i), orc[j], iv) > 1e10
+                excluded_cond[j] = jtj_condition(O, batch.stamp(i), orc[j], iv, supersample) > 1e10
     gate = conv & ~excluded_cond & ~excluded_basin
     ok = np.ones(len(gs), bool)
     for k in keys:
