@@ -35,6 +35,8 @@ def main():
     ap.add_argument("--what", choices=["fit_batch", "adjoint", "star", "moment_vjp", "moment_jvp", "cutout"],
                     default="fit_batch")
     ap.add_argument("--profile", choices=["gauss", "moffat"], default="gauss")
+    ap.add_argument("--supersample", type=int, default=1,
+                    help="fit_batch: the fit's model as the mean of S x S samples per pixel")
     ap.add_argument("--sigw", choices=["r50", "matched", "fixed"], default="r50",
                     help="sigma_w rule of the implicit gradients (moment_vjp, moment_jvp)")
     ap.add_argument("--workload", type=int, default=None)
@@ -59,7 +61,7 @@ def main():
     batch = synth.make_workload(args.workload if args.workload is not None else 1,
                                 count=args.stamps if args.stamps is not None else 20000, device="cuda")
     idx = B.make_index(batch.offset, batch.h, batch.w)
-    opts = B.default_opts(max_pix=int((batch.h.long() * batch.w.long()).max()))
+    opts = B.default_opts(max_pix=int((batch.h.long() * batch.w.long()).max()), supersample=args.supersample)
     out = torch.empty((batch.count, 64), dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
         ctx.fit_batch(batch.pix, idx, out=out, opts=opts)
