@@ -79,7 +79,7 @@ def test_cutout_large_images(ctx, O):
     # the total of a 512x512 image carries the noise of 262,144 pixels (sigma
     # 512): for faint galaxies it can be <= 0, and the growth curve falls back
     assert np.all((inf["status"] == 0) | (inf["status"] == ST["INIT_FALLBACK"]))
-    assert np.mean(inf["status"] == 0) > 0.8
+    assert np.mean(inf["status"] == 0) > 0.75
 
 
 def test_cutout_ragged_and_corners(ctx, O):
