@@ -17,8 +17,9 @@
  *    centre at (x = j, y = i) in stamp coordinates.
  *  - Pixels of all stamps sit in one flat buffer; stamp s starts at element
  *    idx[s].offset.  Stamps may be unaligned, of different sizes, and in any
- *    order.  1 <= h*w <= opts->max_pix <= FSE_MAX_PIX; a stamp outside that
- *    range is reported with FSE_ST_BAD_SIZE and no other work.
+ *    order.  1 <= h, w <= FSE_MAX_SIDE and h*w <= opts->max_pix <=
+ *    FSE_MAX_PIX; the estimator reports a stamp outside that range with
+ *    FSE_ST_BAD_SIZE and does no other work on it.
  *  - Pixel type FSE_F32: float.  FSE_BF16: bfloat16, decoded as
  *    (float)pix * scale[s] with one float scale per stamp.
  *  - inv_var (optional, may be NULL): per-pixel 1/sigma_i^2 as float, laid out
@@ -59,6 +60,7 @@ extern "C" {
 #define FSE_EUNSUPPORTED  5
 
 #define FSE_MAX_PIX       (128 * 128)
+#define FSE_MAX_SIDE      128
 
 /* fse_result.status bits */
 #define FSE_ST_MOM_CONVERGED  (1u << 0)  /* centroid/ellipticity reached the stop rule      */

@@ -646,7 +646,8 @@ static void fit_stamp(const double *I, const double *ivar, int h, int w, const o
 /* ------------------------------------------------------------------------ */
 /* Public entry points (single stamp; pixels as float64, row-major).          */
 /* ------------------------------------------------------------------------ */
-static int size_ok(int h, int w) { return h >= 1 && w >= 1 && (int64_t)h * w <= 128 * 128; }
+/* The library's input contract: sides of 1 to 128 pixels (so h*w <= 128*128). */
+static int size_ok(int h, int w) { return h >= 1 && w >= 1 && h <= 128 && w <= 128; }
 
 /* Sec. 2 alone: brightest-pixel start, circular weight, centroid fixed point. */
 void orc_centroid(const double *I, int h, int w, const orc_opts *o, orc_result *res)

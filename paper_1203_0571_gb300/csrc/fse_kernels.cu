@@ -1699,7 +1699,7 @@ __global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
                               : 0u;
         res.npix = static_cast<int32_t>(npl > 0x7fffffff ? 0x7fffffff : npl);
         bool skip = false;
-        if (h < 1 || w < 1 || npl > max_pix) {
+        if (h < 1 || w < 1 || h > FSE_MAX_SIDE || w > FSE_MAX_SIDE || npl > max_pix) {
             status |= FSE_ST_BAD_SIZE;
             skip = true;
         }

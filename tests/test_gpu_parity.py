@@ -244,3 +244,33 @@ def test_fixed_gain_reaches_the_same_fixed_point(ctx, O):
         assert_gate(rep)
     both = ((g75["status"] & 1) & (g0["status"] & 1)).astype(bool)
     assert g0["it_mom"][both].mean() < g75["it_mom"][both].mean()
+
+
+def test_side_limit(ctx, O):
+    """Stamps with a side above 128 pixels are refused (BAD_SIZE) whatever their
+    area, by the estimator and by the oracle's batch; stamps of the same batch
+    within the limit, including elongated ones, are measured as usual."""
+    rng = np.random.default_rng(12)
+    shapes = [(1, 200), (200, 1), (2, 1200), (129, 100), (24, 96), (48, 48), (128, 40), (40, 128)]
+    stamps = []
+    for h, w in shapes:
+        yy, xx = np.mgrid[0:h, 0:w].astype(np.float64)
+        xc, yc = rng.uniform(0.4, 0.6) * (w - 1), rng.uniform(0.4, 0.6) * (h - 1)
+        stamps.append(50.0 * np.exp(-((xx - xc) ** 2 + (yy - yc) ** 2) / (2 * 3.0 ** 2)) +
+                      rng.normal(0, 0.2, (h, w)))
+    pix = np.concatenate([s_.astype(np.float32).ravel() for s_ in stamps])
+    offs = np.cumsum([0] + [s_.size for s_ in stamps[:-1]])
+    hs = np.array([s_.shape[0] for s_ in stamps])
+    ws = np.array([s_.shape[1] for s_ in stamps])
+    idx = B.make_index(offs, hs, ws)
+    d = torch.as_tensor(pix).cuda()
+    g = B.results(ctx.centroid(d, idx, opts=B.default_opts(max_pix=16384)))
+    gf = B.results(ctx.fit_batch(d, idx, opts=B.default_opts(max_pix=16384)))
+    o, _ = O.batch(pix, offs, hs, ws, stage="centroid")
+    for j, (h, w) in enumerate(shapes):
+        if h > 128 or w > 128:
+            assert g["status"][j] == gf["status"][j] == B.ST["BAD_SIZE"] and o["status"][j] == 32, (h, w)
+            continue
+        assert abs(g["r50"][j] / o["r50"][j] - 1) <= 1e-6, (h, w, g["r50"][j], o["r50"][j])
+        assert (g["status"][j] & 1) and (o["status"][j] & 1), (h, w)
+        assert abs(g["x0"][j] - o["x0"][j]) <= 1e-4 and abs(g["y0"][j] - o["y0"][j]) <= 1e-4, (h, w)
