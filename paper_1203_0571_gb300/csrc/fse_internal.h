@@ -14,7 +14,8 @@ enum Stage : int {
     kStageCentroid = 1,     // start-up + Sec. 2 centroid (circular weight)
     kStageEllipticity = 2,  // Secs. 2-3 from a given centre and sigma_w
     kStageFit = 3,          // Sec. 4.1 fit with centre and g fixed
-    kStageAll = 4,          // whole chain
+    kStageAll = 4,          // whole chain: runs as kStageMoments, then kStageFit with chain_fit
+    kStageMoments = 5,      // start-up + Secs. 2-3 (the first launch of the chain)
 };
 
 // Options as the kernels see them (fp32 where the per-pixel code uses them).
@@ -45,6 +46,8 @@ struct LaunchArgs {
     int warps_per_stamp;     // 1, 2, 4 or 8 warps share a stamp (whole chain only)
     int num_ctas;            // 0 = library choice
     int static_assign;       // 1: warp w of the grid takes stamp w only (no counter)
+    int chain_fit;           // kStageFit as the second launch of the chain: keeps every
+                             // status bit of the record and fits only converged moments
     // Size-class launches of the ragged path: the launch takes the stamps
     // perm[range[0] .. range[0] + range[1]) (range in device memory, written by
     // the classification kernels earlier on the stream).  NULL: stamps 0..count.

