@@ -319,6 +319,30 @@ __host__ __device__ inline size_t group_bytes(int max_pix, bool ivar, int nw) {
     return warp_bytes(max_pix, ivar) + (nw > 1 ? static_cast<size_t>(nw) * 128 + 16 : 0);
 }
 
+// The moment stages keep a smaller tile: the pixels, and an auxiliary area
+// only for the start-up's ring histogram (at most 182 rings for sides up to
+// 128) or the raw bf16 staging; no inverse variance (the moments do not use
+// it).  For 48x48 that is 10.7 KB per warp instead of 18.5 KB, so more warps
+// share an SM.
+constexpr size_t kHistBytes = 182 * 8;
+__host__ __device__ inline size_t aux_bytes_moments(int max_pix, bool bf16) {
+    const size_t raw = bf16 ? static_cast<size_t>(max_pix + 8) * 2 : 0;
+    return align16(raw > kHistBytes ? raw : kHistBytes);
+}
+__host__ __device__ inline constexpr bool moment_stage(int stage) {
+    return stage == kStageCentroid || stage == kStageEllipticity || stage == kStageMoments;
+}
+__host__ __device__ inline size_t stage_aux_bytes(int stage, int max_pix, bool bf16) {
+    return moment_stage(stage) ? aux_bytes_moments(max_pix, bf16) : aux_bytes(max_pix);
+}
+__host__ __device__ inline size_t stage_warp_bytes(int stage, int max_pix, bool bf16, bool ivar) {
+    return pix_bytes(max_pix) + stage_aux_bytes(stage, max_pix, bf16) +
+           (ivar && !moment_stage(stage) ? pix_bytes(max_pix) : 0) + 16;
+}
+__host__ __device__ inline size_t stage_group_bytes(int stage, int max_pix, bool bf16, bool ivar, int nw) {
+    return stage_warp_bytes(stage, max_pix, bf16, ivar) + (nw > 1 ? static_cast<size_t>(nw) * 128 + 16 : 0);
+}
+
 // Stage a stamp (npix elements at gsrc) into shared memory.  The 16-byte
 // aligned body moves with one bulk TMA copy completing on `bar`; the head
 // and tail are loaded by lanes.  Returns false if the bounded wait expired.
@@ -405,27 +429,12 @@ struct MomState {
     int xr, yr;      // reference pixel of the stored per-pixel offsets
 };
 
-// Offsets (column - xr, row - yr) of every pixel as half2 (integers below
-// 2048 are exact in fp16), stored in the auxiliary buffer for the moment
-// passes.
-template <int NW>
-__device__ __forceinline__ void store_offsets(__half2* C, int w, int npix, const Grp<NW>& g,
-                                              int xr, int yr) {
-    PixelWalk pw(g.t, w, Grp<NW>::NT);
-    for (int p = g.t; p < npix; p += Grp<NW>::NT) {
-        C[p] = __floats2half2_rn(static_cast<float>(pw.col - xr), static_cast<float>(pw.row - yr));
-        pw.next();
-    }
-    g.sync();
-}
-
 // One weighted pass: S0 = sum f W, S1 = sum f W theta, the three second and
 // five fourth moments of f W (f = pixel value).  Everything the centroid step
 // (Eqs. 5-6) and the ellipticity step (Eqs. 8-9 with A5-A6, B7-B14) needs is a
 // linear combination of these eleven sums.
 template <int NW>
-__device__ __forceinline__ void moment_pass(const float* __restrict__ s,
-                                            const __half2* __restrict__ C, int npix,
+__device__ __forceinline__ void moment_pass(const float* __restrict__ s, int w, int npix,
                                             const Grp<NW>& g, const MomState& st,
                                             float (&acc)[11]) {
     const float gg = st.g1 * st.g1 + st.g2 * st.g2;
@@ -440,11 +449,13 @@ __device__ __forceinline__ void moment_pass(const float* __restrict__ s,
     // use exact offsets)
     const float cx = static_cast<float>(st.xi - st.xr) + st.xf;
     const float cy = static_cast<float>(st.yi - st.yr) + st.yf;
+    // pixel offsets from the reference pixel, exact integers in fp32
+    PixelWalk pw(g.t, w, Grp<NW>::NT);
 #pragma unroll 2
     for (int p = g.t; p < npix; p += Grp<NW>::NT) {
-        const float2 X = __half22float2(C[p]);
-        const float t1 = X.x - cx;
-        const float t2 = X.y - cy;
+        const float t1 = static_cast<float>(pw.col - st.xr) - cx;
+        const float t2 = static_cast<float>(pw.row - st.yr) - cy;
+        pw.next();
         const float t11 = t1 * t1, t22 = t2 * t2, t12 = t1 * t2;
         const float R2 = fmaf(A, t11, fmaf(B, t22, -G4 * t12));
         const float f = s[p] * ex2(R2 * cw);
@@ -700,11 +711,10 @@ constexpr float kMomRefineSkip = 1e-7f;
 
 // Iterate to the stop rule.  Returns the number of passes; sets status bits.
 template <int NW>
-__device__ int moment_iterate(const float* s, __half2* C, int h, int w, int npix, const Grp<NW>& g,
+__device__ int moment_iterate(const float* s, int h, int w, int npix, const Grp<NW>& g,
                               const DevOpts& o, bool ellip, MomState& st, uint32_t& status) {
     st.xr = st.xi;
     st.yr = st.yi;
-    store_offsets(C, w, npix, g, st.xr, st.yr);
     const float sw_max = 0.5f * static_cast<float>(h < w ? h : w);
     float prev = 0.f;   // size of the previous step, for the contraction estimate
     // with the determined gain (k_gain = 0): a centre step that does not shrink
@@ -713,7 +723,7 @@ __device__ int moment_iterate(const float* s, __half2* C, int h, int w, int npix
     int it;
     for (it = 1; it <= o.max_iter_mom; ++it) {
         float m[11];
-        moment_pass(s, C, npix, g, st, m);
+        moment_pass(s, w, npix, g, st, m);
         const MomStep d = moment_step(m, st, k_use, ellip);
         if (k_use <= 0.f) {
             const float dc = fmaxf(fabsf(d.dx), fabsf(d.dy));
@@ -1647,14 +1657,18 @@ __global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
     g.t = g.wi * 32 + lane;
     g.bar = 1 + grp;
     const int max_pix = a.opts.max_pix;
-    unsigned char* wbase = smem + static_cast<size_t>(grp) * group_bytes(max_pix, IVAR, NW);
+    constexpr bool kBf16 = DT == FSE_BF16;
+    constexpr bool kIv = IVAR && !moment_stage(STAGE);   // the moments do not use inverse variance
+    const size_t wb = stage_warp_bytes(STAGE, max_pix, kBf16, IVAR);
+    unsigned char* wbase = smem + static_cast<size_t>(grp) * stage_group_bytes(STAGE, max_pix, kBf16, IVAR, NW);
     float* pixbuf = reinterpret_cast<float*>(wbase);
     float* aux = reinterpret_cast<float*>(wbase + pix_bytes(max_pix));
-    float* ivbuf = IVAR ? reinterpret_cast<float*>(wbase + pix_bytes(max_pix) + aux_bytes(max_pix))
-                        : nullptr;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(wbase + warp_bytes(max_pix, IVAR) - 16);
-    g.red = reinterpret_cast<float*>(wbase + warp_bytes(max_pix, IVAR));   // used when NW > 1
-    unsigned* slot = reinterpret_cast<unsigned*>(wbase + warp_bytes(max_pix, IVAR) + NW * 128);
+    float* ivbuf = kIv ? reinterpret_cast<float*>(wbase + pix_bytes(max_pix) +
+                                                  stage_aux_bytes(STAGE, max_pix, kBf16))
+                       : nullptr;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(wbase + wb - 16);
+    g.red = reinterpret_cast<float*>(wbase + wb);   // used when NW > 1
+    unsigned* slot = reinterpret_cast<unsigned*>(wbase + wb + NW * 128);
     if (g.t == 0) mbar_init(bar);
     g.sync();
     if (g.t == 0) fence_proxy_async();
@@ -1730,7 +1744,7 @@ __global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
             const float scale = (DT == FSE_BF16 && a.scale) ? a.scale[si] : 1.f;
             const bool ok = stage_stamp<DT>(pixbuf, &s, aux, gsrc, static_cast<int>(npl), scale, bar,
                                             &phase, g);
-            if (IVAR && ok) {
+            if (kIv && ok) {
                 const float* gv = a.inv_var + ix.offset;
                 for (int p = g.t; p < npl; p += Grp<NW>::NT) ivbuf[p] = sqrtf(fmaxf(__ldg(gv + p), 0.f));
                 g.sync();
@@ -1797,7 +1811,7 @@ __global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
         }
         if (!skip && STAGE != kStageFit) {
             const bool ellip = STAGE != kStageCentroid;
-            res.it_mom = moment_iterate(s, reinterpret_cast<__half2*>(aux), h, w, npix, g, o,
+            res.it_mom = moment_iterate(s, h, w, npix, g, o,
                                         ellip, st, status);
             res.x0 = static_cast<float>(st.xi) + st.xf;
             res.y0 = static_cast<float>(st.yi) + st.yf;
@@ -1834,7 +1848,7 @@ template <int STAGE, int DT, bool IVAR, int NW, bool SUP = false>
 cudaError_t launch_t(const LaunchArgs& a, cudaStream_t stream) {
     const int groups = a.warps_per_cta / NW;
     if (groups < 1 || groups * NW != a.warps_per_cta || groups > 15) return cudaErrorInvalidValue;
-    const size_t smem = group_bytes(a.opts.max_pix, IVAR, NW) * groups;
+    const size_t smem = stage_group_bytes(STAGE, a.opts.max_pix, DT == FSE_BF16, IVAR, NW) * groups;
     auto kern = estimator_kernel<STAGE, DT, IVAR, NW, SUP>;
     // the shared-memory opt-in is raised once per instantiation and size (per device)
     static size_t opted[64] = {0};
