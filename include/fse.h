@@ -231,9 +231,15 @@ int fse_fit_batch_plain(fse_ctx *ctx, const void *pix, int dtype, const float *s
 /* fse_fit_batch on HOST buffers: pix (npix_total elements of dtype), scale
  * (count floats or NULL), idx, inv_var (or NULL) and out are host pointers
  * (page-locked memory lets the copies overlap the kernels).  The call copies
- * the inputs to context-owned device buffers in chunks, runs the chain, copies
- * the results back and returns when out[] is complete.  npix_total bounds
- * every idx[s].offset + h*w. */
+ * the inputs to context-owned device buffers in chunks (from 8192 stamps up,
+ * 5 chunks of 2, 4, 8, 16 and 34 64ths of the batch, else one) on a context
+ * copy stream,
+ * runs each chunk's chain on `stream` or a second context stream as soon as
+ * its copy is done, copies the results back and returns when out[] is
+ * complete.  npix_total bounds every idx[s].offset + h*w; a stamp outside it
+ * returns FSE_EINVAL before anything is copied.  Results equal those of
+ * fse_fit_batch byte for byte.  One host-buffer call at a time per context
+ * (the device buffers and events are the context's). */
 int fse_fit_batch_host(fse_ctx *ctx, const void *pix, int64_t npix_total, int dtype,
                        const float *scale, const fse_stamp *idx, int64_t count,
                        const float *inv_var, const fse_opts *opts, fse_result *out,

@@ -1644,9 +1644,11 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
 // NW warps share each stamp (a stamp group); a CTA holds blockDim.x / (32 NW)
 // groups, each with its own tile and, for NW > 1, named barrier 1 + group.
 template <int STAGE, int DT, bool IVAR, int NW, bool SUP = false>
-// 168 registers per thread let three CTAs of four warps share an SM (the
-// launch shape of 48x48 and smaller tiles); more would leave two.
-__global__ void __maxnreg__(168) estimator_kernel(LaunchArgs a) {
+// Fit stages: 168 registers per thread let three CTAs of four warps share an
+// SM (the launch shape of 48x48 and smaller tiles); more would leave two.
+// Moment stages: 96 registers (they need 102 uncapped, and spill nothing at
+// 96) let five CTAs of four warps share an SM with their compact tile.
+__global__ void __maxnreg__(moment_stage(STAGE) ? 96 : 168) estimator_kernel(LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;

@@ -231,6 +231,28 @@ def test_host_buffers_equal_device(ctx):
     assert host.tobytes() == dev.tobytes()
 
 
+def test_host_buffers_ragged_bf16_inverse_variance(ctx):
+    """The chunked host-buffer pipeline on 9,001 stamps of 32-64 px (bf16 with a
+    per-stamp scale, a per-pixel inverse variance, two stamps of a refused
+    size): its results equal fse_fit_batch on device buffers, byte for byte."""
+    batch = synth.encode_bf16(synth.make_workload(4, count=9001))
+    opts = opts_for(batch)
+    batch.h[17] = 0                     # empty: BAD_SIZE
+    batch.h[5000], batch.w[5000] = 1, 129   # a side above the limit: BAD_SIZE
+    rng = np.random.default_rng(11)
+    ivar = torch.as_tensor(rng.uniform(0.5, 2.0, batch.pix.numel()).astype(np.float32))
+    b = batch.to("cuda")
+    idx = B.make_index(b.offset, b.h, b.w)
+    dev = B.results(ctx.fit_batch(b.pix, idx, scale=b.scale, inv_var=ivar.cuda(), opts=opts))
+    host_idx = B.make_index(batch.offset, batch.h, batch.w, device="cpu").pin_memory()
+    out = torch.zeros((batch.count, 64), dtype=torch.uint8).pin_memory()
+    ctx.fit_batch_host(batch.pix.pin_memory(), host_idx, scale=batch.scale.pin_memory(),
+                       inv_var=ivar.pin_memory(), opts=opts, out=out)
+    host = out.numpy().view(B.RESULT_DTYPE).reshape(-1)
+    assert host["status"][17] & B.ST["BAD_SIZE"] and host["status"][5000] & B.ST["BAD_SIZE"]
+    assert host.tobytes() == dev.tobytes()
+
+
 def test_fixed_gain_reaches_the_same_fixed_point(ctx, O):
     """k = 0.75 (the fixed gain of Sec. 2) and the default determined gain both
     reach the oracle's fixed point; only the number of passes differs."""
