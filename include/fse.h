@@ -232,8 +232,8 @@ int fse_fit_batch_plain(fse_ctx *ctx, const void *pix, int dtype, const float *s
  * (count floats or NULL), idx, inv_var (or NULL) and out are host pointers
  * (page-locked memory lets the copies overlap the kernels).  The call copies
  * the inputs to context-owned device buffers in chunks (from 8192 stamps up,
- * 5 chunks of 2, 4, 8, 16 and 34 64ths of the batch, else one) on a context
- * copy stream,
+ * 9 chunks of 2, 4, 6, 8, 10, 10, 10, 8 and 6 64ths of the batch, else one)
+ * on a context copy stream,
  * runs each chunk's chain on `stream` or a second context stream as soon as
  * its copy is done, copies the results back and returns when out[] is
  * complete.  npix_total bounds every idx[s].offset + h*w; a stamp outside it

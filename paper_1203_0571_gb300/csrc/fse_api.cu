@@ -16,14 +16,17 @@
 #include "fse_internal.h"
 
 // Chunks of the host-buffer pipeline (fse_fit_batch_host), in units of 1/64
-// of the batch.  The kernels start after the copy of the small first chunk,
-// and each chunk is about twice the one before: on a GB300 the host-to-device
-// copy (211 GB/s measured) moves a stamp in less than half the time the chain
-// takes for it, so chunk c+1's copy ends before chunk c's kernels do.  Few
-// chunks, because every chunk adds two launch tails (on 100,000 stamps of
-// 48x48, twelve chunks cost 11.0 ms against 9.5 ms for one launch pair).
-constexpr int kHostChunks = 5;
-constexpr int kChunkUnits[kHostChunks] = {2, 4, 8, 16, 34};
+// of the batch.  The kernels start after the copy of the small first chunk;
+// the chunks then grow while the copy runs ahead of the kernels, level off,
+// and shrink again so that little compute is left once the last copy is done.
+// The host link's rate differs between machines (211 and about 120 GB/s
+// measured on two GB300 hosts, against about 100 GB/s of pixels consumed by
+// the kernels on 48x48 stamps), and this schedule stays within 10% of the
+// best over that range; few chunks, because every chunk adds two launch tails
+// (on 100,000 stamps of 48x48, twelve chunks cost 11.0 ms against 9.5 ms for
+// one launch pair).
+constexpr int kHostChunks = 9;
+constexpr int kChunkUnits[kHostChunks] = {2, 4, 6, 8, 10, 10, 10, 8, 6};
 
 struct fse_ctx {
     int device = 0;

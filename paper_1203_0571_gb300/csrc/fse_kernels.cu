@@ -429,6 +429,33 @@ struct MomState {
     int xr, yr;      // reference pixel of the stored per-pixel offsets
 };
 
+// The offsets (column - xr, row - yr) of a thread's pixels p = t, t + nt, ...
+// of a row-major stamp of width w, as floats.  They are integers below 2^24,
+// exact in fp32, so stepping them with float adds gives the same values as
+// converting the integer offsets, without a conversion per pixel.
+struct OffsetWalk {
+    float u, v;      // column and row offset of the current pixel
+    float du, dv;    // one step of nt pixels: dv rows and du columns
+    float wrap, fw;  // u >= wrap: the column passed the right edge (w - xr); fw = w
+    __device__ __forceinline__ OffsetWalk(int t, int w, int nt, int xr, int yr) {
+        const int row = t / w, dr = nt / w;
+        u = static_cast<float>(t - row * w - xr);
+        v = static_cast<float>(row - yr);
+        du = static_cast<float>(nt - dr * w);
+        dv = static_cast<float>(dr);
+        wrap = static_cast<float>(w - xr);
+        fw = static_cast<float>(w);
+    }
+    __device__ __forceinline__ void next() {
+        u += du;
+        v += dv;
+        if (u >= wrap) {
+            u -= fw;
+            v += 1.f;
+        }
+    }
+};
+
 // One weighted pass: S0 = sum f W, S1 = sum f W theta, the three second and
 // five fourth moments of f W (f = pixel value).  Everything the centroid step
 // (Eqs. 5-6) and the ellipticity step (Eqs. 8-9 with A5-A6, B7-B14) needs is a
@@ -450,12 +477,12 @@ __device__ __forceinline__ void moment_pass(const float* __restrict__ s, int w, 
     const float cx = static_cast<float>(st.xi - st.xr) + st.xf;
     const float cy = static_cast<float>(st.yi - st.yr) + st.yf;
     // pixel offsets from the reference pixel, exact integers in fp32
-    PixelWalk pw(g.t, w, Grp<NW>::NT);
+    OffsetWalk ow(g.t, w, Grp<NW>::NT, st.xr, st.yr);
 #pragma unroll 2
     for (int p = g.t; p < npix; p += Grp<NW>::NT) {
-        const float t1 = static_cast<float>(pw.col - st.xr) - cx;
-        const float t2 = static_cast<float>(pw.row - st.yr) - cy;
-        pw.next();
+        const float t1 = ow.u - cx;
+        const float t2 = ow.v - cy;
+        ow.next();
         const float t11 = t1 * t1, t22 = t2 * t2, t12 = t1 * t2;
         const float R2 = fmaf(A, t11, fmaf(B, t22, -G4 * t12));
         const float f = s[p] * ex2(R2 * cw);
@@ -623,9 +650,9 @@ __device__ float moment_refine(const float* __restrict__ s, int w, int npix, con
     for (int i = 0; i < 6; ++i) dh[i] = dl[i] = 0.f;
 #pragma unroll
     for (int i = 0; i < 5; ++i) cx[i] = F[i] = 0.f;
-    PixelWalk pw(g.t, w, Grp<NW>::NT);
+    OffsetWalk ow(g.t, w, Grp<NW>::NT, st.xi, st.yi);
     for (int p = g.t; p < npix; p += Grp<NW>::NT) {
-        const float k1 = static_cast<float>(pw.col - st.xi), k2 = static_cast<float>(pw.row - st.yi);
+        const float k1 = ow.u, k2 = ow.v;
         // theta = k - x_f exactly as hi + lo (|k| >= |x_f| unless k = 0, where lo = 0)
         const float t1 = k1 - st.xf, t1l = -st.xf - (t1 - k1);
         const float t2 = k2 - st.yf, t2l = -st.yf - (t2 - k2);
@@ -649,7 +676,7 @@ __device__ float moment_refine(const float* __restrict__ s, int w, int npix, con
         F[2] = fmaf(f11, t22, F[2]);
         F[3] = fmaf(f22, t12, F[3]);
         F[4] = fmaf(f22, t22, F[4]);
-        pw.next();
+        ow.next();
     }
     g.allsum_df(dh, dl);
     g.allsum(cx);
@@ -817,6 +844,20 @@ struct InitOut {
 // interpolates linearly in the ring that crosses.  Sums are exact 64-bit
 // fixed point (pixel * 2^S), so the crossing ring does not depend on the
 // summation order.
+// ceil(sqrt(d2)) for an integer 0 <= d2 <= 2 * 127^2 (sides of at most
+// FSE_MAX_SIDE = 128 pixels).  sqrt.approx.f32 is within about 2^-22 relative
+// of the square root, under 1e-4 absolute here, while the square root of a
+// non-square integer below 2 * 128^2 lies at least 1 / 364 from every
+// integer.  Its floor is therefore the integer square root, or one less at a
+// perfect square, and the comparison turns either into the ceiling.
+__device__ __forceinline__ int ring_of(int d2) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(static_cast<float>(d2)));
+    int k = static_cast<int>(r);
+    k += (k * k < d2) ? 1 : 0;
+    return k;
+}
+
 template <int NW>
 __device__ InitOut stamp_init(const float* s, int h, int w, int npix, const Grp<NW>& g,
                               unsigned long long* hist) {
@@ -874,17 +915,37 @@ __device__ InitOut stamp_init(const float* s, int h, int w, int npix, const Grp<
     const int kmax = static_cast<int>(ceilf(sqrtf(static_cast<float>(dh * dh + dw * dw)))) + 1;
     for (int k = g.t; k <= kmax; k += NT) hist[k] = 0ull;
     g.sync();
+    // Each thread takes a block of C consecutive pixels, starting at offset
+    // t mod C within it and wrapping to the block's start: the threads of a
+    // warp sit about C pixels apart, mostly on different rings, so their
+    // shared-memory atomics seldom meet on one address, and with C + 1 odd
+    // their pixel loads fall in distinct banks.  The sums are integers, so the
+    // order of the additions does not change them.
     long long tot = 0;
-    PixelWalk pw(g.t, w, NT);
-    for (int p = g.t; p < npix; p += NT) {
-        const long long q = __float2ll_rn(s[p] * fs);
-        tot += q;
-        const int di = pw.row - pr, dj = pw.col - pc;
-        const int d2 = di * di + dj * dj;
-        int k = static_cast<int>(sqrtf(static_cast<float>(d2)));
-        k += (k * k < d2) ? 1 : 0;
-        atomicAdd(&hist[k], static_cast<unsigned long long>(q));
-        pw.next();
+    const int C = (npix + NT - 1) / NT;
+    const int b0 = g.t * C;
+    const int row0 = b0 / w, col0 = b0 - row0 * w;
+    int j = g.t % C;
+    int p = b0 + j;
+    int row = p / w, col = p - row * w;
+    for (int i = 0; i < C; ++i) {
+        if (p < npix) {
+            const long long q = __float2ll_rn(s[p] * fs);
+            tot += q;
+            const int di = row - pr, dj = col - pc;
+            atomicAdd(&hist[ring_of(di * di + dj * dj)], static_cast<unsigned long long>(q));
+        }
+        ++p;
+        if (++col == w) {
+            col = 0;
+            ++row;
+        }
+        if (++j == C) {
+            j = 0;
+            p = b0;
+            row = row0;
+            col = col0;
+        }
     }
     tot = g.allsum_ll(tot);
     g.sync();   // every ring of the histogram is complete (the scan reads them)
