@@ -298,7 +298,7 @@ def main():
            "d2h_bytes_per_step": int(n * 64), "entry": "fse_fit_batch_host", "ms_per_step": 1e3 * e2e_s}
     same = bool(np.array_equal(host_out.numpy(), out.cpu().numpy()))
 
-    # the plain form: one launch per stamp, on the first stamps of the workload
+    # the plain form: one launch pair per stamp, on the first stamps of the workload
     pn = min(args.plain_stamps, n)
     pout = torch.empty((pn, 64), dtype=torch.uint8, device=f"cuda:{local}")
     ctx.fit_batch_plain(batch.pix, idx[:pn], out=pout, opts=opts)

@@ -217,13 +217,16 @@ int fse_sersic_fit(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
                    const fse_opts *opts, fse_result *inout, void *stream);
 
 /* The whole chain of Sec. 4.1 (start-up, centroid + ellipticity from the
- * brightest pixel, fit) in one persistent launch. */
+ * brightest pixel, fit) in two persistent launches on `stream`: the start-up
+ * and the moment iteration, then the fit of every stamp whose moments
+ * converged.  Results are those of the three single stages run in turn. */
 int fse_fit_batch(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
                   const fse_stamp *idx, int64_t count, const float *inv_var,
                   const fse_opts *opts, fse_result *out, void *stream);
 
-/* The same chain launched once per stamp (one warp per launch).  A baseline
- * for measurement only; results are identical to fse_fit_batch. */
+/* The same chain launched per stamp (one warp per launch, two launches per
+ * stamp).  A baseline for measurement only; results are identical to
+ * fse_fit_batch. */
 int fse_fit_batch_plain(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
                         const fse_stamp *idx, int64_t count, const float *inv_var,
                         const fse_opts *opts, fse_result *out, void *stream);
@@ -248,8 +251,8 @@ int fse_fit_batch_host(fse_ctx *ctx, const void *pix, int64_t npix_total, int dt
 /* fse_fit_batch for a RAGGED batch (stamps of different sizes, 1 to
  * FSE_MAX_PIX pixels, in any order).  The stamps are bucketed on the device
  * into seven size classes (h*w up to 16^2, 24^2, 32^2, 48^2, 64^2, 96^2,
- * 128^2), and each class runs in its own persistent launch whose shared-memory
- * tile fits that class, largest class first.  Results are those of
+ * 128^2), and each class runs in its own pair of persistent launches whose
+ * shared-memory tile fits that class, largest class first.  Results are those of
  * fse_fit_batch, stamp by stamp.  opts->max_pix is not used (each class sets
  * its own); opts->warps_per_cta, if non-zero, applies to every class, else
  * the class uses the choice of fse_autotune or the library default.  With

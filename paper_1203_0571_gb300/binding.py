@@ -245,7 +245,7 @@ class Context:
 
     def fit_batch_plain(self, pix, index, *, scale=None, inv_var=None, opts=None, out=None,
                         stream=None):
-        """fse_fit_batch_plain: the same chain, one launch per stamp."""
+        """fse_fit_batch_plain: the same chain, one launch pair per stamp."""
         return self._dev_call("fse_fit_batch_plain", pix, index, out, scale, inv_var, opts, stream)
 
     def fit_batch_ragged(self, pix, index, *, scale=None, inv_var=None, opts=None, out=None,

@@ -285,7 +285,7 @@ void class_shape(const fse_ctx* ctx, const fse::LaunchArgs& a, const fse_opts& o
     launch_shape(o, fse::kClassPix[k], fse::kStageAll, wpc, nw);
 }
 
-// Classification, then one persistent launch per size class (largest first),
+// Classification, then the chain's launch pair per size class (largest first),
 // each with a shared-memory tile for its class.  Everything is stream-ordered
 // on `s` with no host synchronisation, so the sequence can be captured.
 int enqueue_ragged(fse_ctx* ctx, const fse::LaunchArgs& a, const fse_opts& o, cudaStream_t s) {

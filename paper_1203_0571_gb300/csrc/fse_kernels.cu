@@ -3,7 +3,8 @@
 // with an elliptical weight (Sec. 3, Appendices A and B) and the Sérsic
 // profile fit with I0 at its closed form (Sec. 4.1, Eqs. 10-13).
 //
-// Execution model: one persistent launch; every warp owns one stamp at a time
+// Execution model: two persistent launches per batch (the start-up and moment
+// iteration, then the fit); in each, every warp owns one stamp at a time
 // and takes the next from an atomic work counter.  The stamp is staged once
 // HBM -> shared memory (1-D TMA bulk copy for its 16-byte-aligned body, plain
 // loads for the ragged ends) and every later pass (start-up, moment
