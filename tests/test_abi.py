@@ -90,3 +90,27 @@ def test_static_entry_rejects_oversized_batch(lib):
                                   ctypes.byref(binding.default_opts()), None, None, err, len(err))
     assert rc == binding.FSE_EINVAL
     assert b"static work counter" in err.value
+
+
+def test_null_context_is_rejected_by_every_entry_point(lib):
+    """Every entry point that takes a context returns FSE_EINVAL for a NULL one,
+    before any CUDA call, so it is safe on a machine without a GPU."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    takes_ctx = re.findall(r"^\s*int\s+(fse_\w+)\s*\(\s*(?:const\s+)?fse_ctx\s*\*", text, flags=re.M)
+    takes_ctx = [f for f in takes_ctx if f not in ("fse_create",)]
+    assert {"fse_fit_batch", "fse_fit_batch_host", "fse_star_fit", "fse_moment_vjp", "fse_cutout",
+            "fse_sersic_chi2_grad", "fse_sync_check"} <= set(takes_ctx), takes_ctx
+    for name in takes_ctx:
+        fn = getattr(lib, name)
+        types = fn.argtypes
+        assert types, f"{name} has no ctypes signature in the binding"
+        args = []
+        for t in types:
+            if t in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_size_t):
+                args.append(0)
+            elif t in (ctypes.c_float, ctypes.c_double):
+                args.append(0.0)
+            else:
+                args.append(None)
+        assert fn(*args) == binding.FSE_EINVAL, name
+    assert lib.fse_last_error(None) == b"null context"
