@@ -19,10 +19,10 @@
 // of the batch.  The kernels start after the copy of the small first chunk;
 // the chunks then grow while the copy runs ahead of the kernels, level off,
 // and shrink again so that little compute is left once the last copy is done.
-// The host link's rate differs between machines (211 and about 120 GB/s
-// measured on two GB300 hosts, against about 100 GB/s of pixels consumed by
-// the kernels on 48x48 stamps), and this schedule stays within 10% of the
-// best over that range; few chunks, because every chunk adds two launch tails
+// The host link's rate differs between machines (211 GB/s measured on one
+// GB300 host; another behaved as about 120 GB/s, against about 100 GB/s of
+// pixels consumed by the kernels on 48x48 stamps), and by a model of the
+// pipeline this schedule stays within 10% of the best over that range; few chunks, because every chunk adds two launch tails
 // (on 100,000 stamps of 48x48, twelve chunks cost 11.0 ms against 9.5 ms for
 // one launch pair).
 constexpr int kHostChunks = 9;
