@@ -63,3 +63,4 @@ def test_reference_arm_other_ranks_do_no_work():
         steps = warmup = 1
         ref_stamps = 10
     assert bench.run_reference(A(), rank=1, world=2) is None
+
