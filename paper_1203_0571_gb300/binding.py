@@ -181,6 +181,31 @@ def _ptr(t):
     return None if t is None else _vp(t.data_ptr())
 
 
+def _index(index, where: str = "cuda"):
+    """Pointer and count of an fse_stamp array, after checking its layout: a
+    contiguous int64 tensor [N, 2] (see make_index) on the device type the call
+    reads it from; for host calls also a C-contiguous numpy array of STAMP_DTYPE
+    or int64 [N, 2].  Anything else raises TypeError before the library sees it."""
+    if isinstance(index, torch.Tensor):
+        if index.dtype != torch.int64 or index.dim() != 2 or index.shape[1] != 2:
+            raise TypeError(f"index must be an int64 tensor [N, 2] (make_index), "
+                            f"got {index.dtype} {tuple(index.shape)}")
+        if not index.is_contiguous():
+            raise TypeError("index must be contiguous")
+        if index.device.type != where:
+            raise TypeError(f"index must be on {where}, got {index.device}")
+        return _vp(index.data_ptr()), int(index.shape[0])
+    if isinstance(index, np.ndarray) and where == "cpu":
+        ok = (index.dtype == STAMP_DTYPE and index.ndim == 1) or \
+             (index.dtype == np.int64 and index.ndim == 2 and index.shape[1] == 2)
+        if not ok or not index.flags.c_contiguous:
+            raise TypeError(f"index must be a C-contiguous STAMP_DTYPE array or int64 [N, 2], "
+                            f"got {index.dtype} {index.shape}")
+        return _vp(index.ctypes.data), int(index.shape[0])
+    raise TypeError(f"index must be a tensor{' or numpy array' if where == 'cpu' else ''} "
+                    f"on {where}, got {type(index).__name__}")
+
+
 def _dtype_of(pix: torch.Tensor) -> int:
     if pix.dtype == torch.float32:
         return FSE_F32
@@ -217,10 +242,10 @@ class Context:
             raise FseError(rc, load().fse_last_error(self._h).decode())
 
     def _dev_call(self, fname, pix, index, out, scale, inv_var, opts, stream):
-        n = int(index.shape[0])
+        ip, n = _index(index)
         if out is None:
             out = torch.zeros((n, 64), dtype=torch.uint8, device=pix.device)
-        rc = getattr(load(), fname)(self._h, _ptr(pix), _dtype_of(pix), _ptr(scale), _ptr(index), n,
+        rc = getattr(load(), fname)(self._h, _ptr(pix), _dtype_of(pix), _ptr(scale), ip, n,
                                     _ptr(inv_var), ctypes.byref(opts or default_opts()), _ptr(out),
                                     _stream(stream))
         self._check(rc)
@@ -268,10 +293,10 @@ class Context:
                  out=None, stream=None):
         """fse_star_fit: Sec. 4.2 star profile at the moments' centre and ellipticity.
         moments is a result tensor (uint8 [N, 64]); returns uint8 [N, 32]."""
-        n = int(index.shape[0])
+        ip, n = _index(index)
         if out is None:
             out = torch.zeros((n, 32), dtype=torch.uint8, device=pix.device)
-        rc = load().fse_star_fit(self._h, _ptr(pix), _dtype_of(pix), _ptr(scale), _ptr(index), n,
+        rc = load().fse_star_fit(self._h, _ptr(pix), _dtype_of(pix), _ptr(scale), ip, n,
                                  _ptr(moments), {"gauss": FSE_STAR_GAUSS, "moffat": FSE_STAR_MOFFAT}[profile],
                                  ctypes.byref(opts or default_opts()), _ptr(out), _stream(stream))
         self._check(rc)
@@ -281,13 +306,13 @@ class Context:
                    scale=None, out=None, status=None, stream=None):
         """fse_moment_vjp: dL/dI (float32, laid out like pix) for v = dL/d(x0, y0,
         e1, e2, sigma_w) (float32 [N, 5]) at the moment fixed point in moments."""
-        n = int(index.shape[0])
+        ip, n = _index(index)
         v = v.to(torch.float32).contiguous()
         if v.shape != (n, 5):
             raise TypeError("v must be [N, 5]")
         if out is None:
             out = torch.zeros(pix.numel(), dtype=torch.float32, device=pix.device)
-        self._check(load().fse_moment_vjp(self._h, _ptr(pix), _dtype_of(pix), _ptr(scale), _ptr(index), n,
+        self._check(load().fse_moment_vjp(self._h, _ptr(pix), _dtype_of(pix), _ptr(scale), ip, n,
                                           _ptr(moments), mode, _ptr(v), _ptr(out), _ptr(status),
                                           _stream(stream)))
         return out
@@ -296,11 +321,11 @@ class Context:
                    scale=None, out=None, status=None, stream=None):
         """fse_moment_jvp: d(x0, y0, e1, e2, sigma_w) (float32 [N, 5]) along the
         pixel tangent (float32, laid out like pix)."""
-        n = int(index.shape[0])
+        ip, n = _index(index)
         tangent = tangent.to(torch.float32).contiguous()
         if out is None:
             out = torch.empty((n, 5), dtype=torch.float32, device=pix.device)
-        self._check(load().fse_moment_jvp(self._h, _ptr(pix), _dtype_of(pix), _ptr(scale), _ptr(index), n,
+        self._check(load().fse_moment_jvp(self._h, _ptr(pix), _dtype_of(pix), _ptr(scale), ip, n,
                                           _ptr(moments), mode, _ptr(tangent), _ptr(out), _ptr(status),
                                           _stream(stream)))
         return out
@@ -313,13 +338,13 @@ class Context:
         index (int64 [N, 2] view, see make_index) and the per-image
         fse_cutout_info records (uint8 [N, 24]).  Without `out` a first launch
         sizes the buffer (and the stream is synchronised once)."""
-        n = int(img_index.shape[0])
+        ip, n = _index(img_index)
         dev = images.device
         info = torch.zeros((n, 24), dtype=torch.uint8, device=dev)
         idx = torch.zeros((n, 2), dtype=torch.int64, device=dev)
         total = torch.zeros(1, dtype=torch.int64, device=dev)
         L = load()
-        args = lambda o, cap: (self._h, _ptr(images), _dtype_of(images), _ptr(scale), _ptr(img_index), n,
+        args = lambda o, cap: (self._h, _ptr(images), _dtype_of(images), _ptr(scale), ip, n,
                                float(side_factor), int(min_side), int(max_side), _ptr(info), _ptr(idx), _ptr(o),
                                int(cap), _ptr(total), _stream(stream))
         if out is None:
@@ -342,8 +367,7 @@ class Context:
         else:
             assert pix.dtype == np.float32 and pix.flags.c_contiguous
             dtype, pix_ptr, npix = FSE_F32, pix.ctypes.data, pix.size
-        idx_ptr, n = (index.data_ptr(), index.shape[0]) if isinstance(index, torch.Tensor) else \
-            (index.ctypes.data, index.shape[0])
+        idx_ptr, n = _index(index, "cpu")
         if out is None:
             out = np.zeros(n, dtype=RESULT_DTYPE)
         out_ptr = out.data_ptr() if isinstance(out, torch.Tensor) else out.ctypes.data
@@ -351,7 +375,7 @@ class Context:
                                              else scale.ctypes.data)
         ivp = None if inv_var is None else _vp(inv_var.data_ptr() if isinstance(inv_var, torch.Tensor)
                                                 else inv_var.ctypes.data)
-        rc = load().fse_fit_batch_host(self._h, _vp(pix_ptr), int(npix), dtype, sp, _vp(idx_ptr),
+        rc = load().fse_fit_batch_host(self._h, _vp(pix_ptr), int(npix), dtype, sp, idx_ptr,
                                        int(n), ivp, ctypes.byref(opts or default_opts()),
                                        _vp(out_ptr), _stream(stream))
         self._check(rc)
@@ -372,7 +396,7 @@ class Context:
 
         Returns (chi2 float64 [N] or None, dparams float32 [N, 7] or None,
         dpix float32 like pix or None)."""
-        n = int(index.shape[0])
+        ip, n = _index(index)
         dev = pix.device
         chi2 = torch.empty(n, dtype=torch.float64, device=dev) if want_chi2 else None
         dpar = torch.empty((n, 7), dtype=torch.float32, device=dev) if want_dparams else None
@@ -382,7 +406,7 @@ class Context:
             raise TypeError("params must be float32 [N, 7]")
         if gout is not None:
             gout = gout.to(torch.float64).contiguous()
-        rc = load().fse_sersic_chi2_grad(self._h, _ptr(pix), _dtype_of(pix), _ptr(scale), _ptr(index),
+        rc = load().fse_sersic_chi2_grad(self._h, _ptr(pix), _dtype_of(pix), _ptr(scale), ip,
                                          n, _ptr(inv_var), _ptr(params), _ptr(gout), _ptr(chi2),
                                          _ptr(dpar), _ptr(dpix), _stream(stream))
         self._check(rc)
@@ -461,11 +485,11 @@ def fse_sync_check(ctx: Context, *a, **k):
 def fit_batch_static(pix, index, *, scale=None, inv_var=None, opts=None, out=None, stream=None):
     """fse_fit_batch_static: the whole chain on the current device with no context
     and no device allocation inside the call (scratch in static device memory)."""
-    n = int(index.shape[0])
+    ip, n = _index(index)
     if out is None:
         out = torch.zeros((n, 64), dtype=torch.uint8, device=pix.device)
     err = ctypes.create_string_buffer(512)
-    rc = load().fse_fit_batch_static(_ptr(pix), _dtype_of(pix), _ptr(scale), _ptr(index), n,
+    rc = load().fse_fit_batch_static(_ptr(pix), _dtype_of(pix), _ptr(scale), ip, n,
                                      _ptr(inv_var), ctypes.byref(opts or default_opts()), _ptr(out),
                                      _stream(stream), err, len(err))
     if rc != FSE_OK:

@@ -114,3 +114,29 @@ def test_null_context_is_rejected_by_every_entry_point(lib):
                 args.append(None)
         assert fn(*args) == binding.FSE_EINVAL, name
     assert lib.fse_last_error(None) == b"null context"
+
+
+def test_index_layout_is_checked_before_the_library():
+    """Only the fse_stamp layout reaches the C ABI: int64 [N, 2] (make_index) on
+    the call's device type, contiguous; numpy STAMP_DTYPE or int64 [N, 2] on the
+    host.  Other layouts raise TypeError in the binding."""
+    import torch
+    idx = binding.make_index([0, 1024, 5], [32, 16, 3], [32, 64, 7], device="cpu")
+    ptr, n = binding._index(idx, "cpu")
+    assert n == 3 and ptr.value == idx.data_ptr()
+    assert binding._index(idx[1:], "cpu")[1] == 2 and binding._index(idx[:0], "cpu")[1] == 0
+    arr = idx.numpy().view(binding.STAMP_DTYPE).reshape(-1)
+    ptr, n = binding._index(arr, "cpu")
+    assert n == 3 and ptr.value == arr.ctypes.data
+    assert binding._index(idx.numpy(), "cpu")[1] == 3
+    bad = [idx.to(torch.int32), idx.float(), idx.reshape(-1), torch.zeros((3, 3), dtype=torch.int64),
+           idx.t().contiguous().t(), [[0, 1]]]
+    for b in bad:
+        with pytest.raises(TypeError):
+            binding._index(b, "cpu")
+    with pytest.raises(TypeError):
+        binding._index(idx, "cuda")          # a host tensor handed to a device call
+    with pytest.raises(TypeError):
+        binding._index(idx.numpy(), "cuda")  # numpy only for host calls
+    with pytest.raises(TypeError):
+        binding._index(idx.numpy()[:, :1].copy(), "cpu")
