@@ -27,6 +27,12 @@
 // one launch pair).
 constexpr int kHostChunks = 9;
 constexpr int kChunkUnits[kHostChunks] = {2, 4, 6, 8, 10, 10, 10, 8, 6};
+constexpr int chunk_units_total() {
+    int t = 0;
+    for (int u : kChunkUnits) t += u;
+    return t;
+}
+static_assert(chunk_units_total() == 64, "the chunks must cover the batch in 64ths");
 
 struct fse_ctx {
     int device = 0;
