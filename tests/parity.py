@@ -113,9 +113,10 @@ def compare(gpu, orc, keys=("x0", "y0", "e1", "e2", "re", "n", "flux", "chi2"), 
 
 
 def dump(name: str, rep: dict, extra: dict | None = None):
-    """Write a report next to the other run outputs if a gpurun_out/ folder exists."""
-    d = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-    if not os.path.isdir(d):
+    """Write the report as parity_<name>.json into the folder named by the
+    environment variable FSE_PARITY_DIR, when it is set and exists."""
+    d = os.environ.get("FSE_PARITY_DIR", "")
+    if not d or not os.path.isdir(d):
         return
     clean = {k: v for k, v in rep.items() if not k.startswith("_")}
     if extra:
