@@ -96,6 +96,8 @@ class Oracle:
         for f in ("orc_sersic_fit", "orc_measure"):
             getattr(L, f).argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Opts),
                                       ctypes.POINTER(Result)]
+        L.orc_sersic_fit_from.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Opts),
+                                          ctypes.c_double, ctypes.c_double, ctypes.POINTER(Result)]
         L.orc_moment_step.argtypes = [_dp, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 6 + \
                                      [ctypes.c_int, _dp]
         L.orc_fit_eval.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 + \
@@ -173,6 +175,16 @@ class Oracle:
         r.x0, r.y0, r.e1, r.e2, r.sigma_w = x0, y0, e1, e2, sigma_w
         self.L.orc_sersic_fit(_as_dp(I), None if iv is None else _as_dp(iv), I.shape[0],
                               I.shape[1], ctypes.byref(opts or self.default_opts()), ctypes.byref(r))
+        return _res_dict(r)
+
+    def sersic_fit_from(self, I, x0, y0, e1, e2, re0, n0, ivar=None, opts: Opts | None = None) -> dict:
+        """The Sec. 4.1 fit at a fixed centre and ellipticity, started from (re0, n0)."""
+        I = _img(I)
+        iv = None if ivar is None else _img(ivar)
+        r = Result()
+        r.x0, r.y0, r.e1, r.e2 = x0, y0, e1, e2
+        self.L.orc_sersic_fit_from(_as_dp(I), None if iv is None else _as_dp(iv), I.shape[0], I.shape[1],
+                                   ctypes.byref(opts or self.default_opts()), re0, n0, ctypes.byref(r))
         return _res_dict(r)
 
     def moment_step(self, I, xc, yc, g1, g2, sw, k_gain=0.75, ellip=True) -> dict:

@@ -563,9 +563,12 @@ static double gn_step(double H[2][2], const double g[2], const double th[2], con
     return fmax(fabs(q[0] - th[0]) / th[0], fabs(q[1] - th[1]) / th[1]);
 }
 
+/* start (may be NULL): (r_e, n) to start the iteration from instead of the
+ * Sec. 4.1 start below; used to test whether a lower chi^2 found elsewhere is
+ * another local minimum of the same profiled problem. */
 static void fit_stamp(const double *I, const double *ivar, int h, int w, const orc_opts *o,
                       double xc, double yc, double g1, double g2, double sw,
-                      orc_result *res)
+                      orc_result *res, const double *start)
 {
     int npix = h * w;
     double gabs = sqrt(g1 * g1 + g2 * g2);
@@ -583,6 +586,7 @@ static void fit_stamp(const double *I, const double *ivar, int h, int w, const o
         double I0c, chi2c = profiled_eval(&d, re0, n_start[c], &I0c, NULL, NULL);
         if (chi2c < best) { best = chi2c; th[1] = n_start[c]; }
     }
+    if (start) { th[0] = start[0]; th[1] = start[1]; clamp_theta(th, o, re_max); }
     /* Levenberg-Marquardt on theta = (r_e, n) (the paper used MINUIT), with
      * the gain-ratio damping update of Nielsen (1999): after an accepted step
      * lambda *= max(1/3, 1 - (2 rho - 1)^3), after a rejected one lambda *= nu,
@@ -684,7 +688,20 @@ void orc_sersic_fit(const double *I, const double *ivar, int h, int w, const orc
 {
     res->npix = h * w;
     if (!size_ok(h, w)) { res->status |= ORC_BAD_SIZE; return; }
-    fit_stamp(I, ivar, h, w, o, res->x0, res->y0, res->e1, res->e2, res->sigma_w, res);
+    fit_stamp(I, ivar, h, w, o, res->x0, res->y0, res->e1, res->e2, res->sigma_w, res, NULL);
+}
+
+/* The Sec. 4.1 fit with centre and ellipticity held fixed, started from a given
+ * (r_e, n) instead of the Sec. 4.1 start (the candidates of n are still
+ * evaluated, but not used).  For tests that check whether a lower chi^2 is a
+ * different local minimum of the r_e - n valley. */
+void orc_sersic_fit_from(const double *I, const double *ivar, int h, int w, const orc_opts *o,
+                         double re0, double n0, orc_result *res)
+{
+    res->npix = h * w;
+    if (!size_ok(h, w)) { res->status |= ORC_BAD_SIZE; return; }
+    double start[2] = { re0, n0 };
+    fit_stamp(I, ivar, h, w, o, res->x0, res->y0, res->e1, res->e2, res->sigma_w, res, start);
 }
 
 /* The whole chain of Sec. 4.1: start-up, centroid + ellipticity, fit. */
@@ -702,7 +719,7 @@ void orc_measure(const double *I, const double *ivar, int h, int w, const orc_op
     moment_iterate(I, h, w, o, 1, &xc, &yc, &g1, &g2, &sw, &res->it_mom, &res->status);
     res->x0 = xc; res->y0 = yc; res->e1 = g1; res->e2 = g2; res->sigma_w = sw; res->r50 = r50;
     if (!(res->status & ORC_MOM_CONVERGED)) return;
-    fit_stamp(I, ivar, h, w, o, xc, yc, g1, g2, sw, res);
+    fit_stamp(I, ivar, h, w, o, xc, yc, g1, g2, sw, res, NULL);
 }
 
 /* One weighted pass exposed for the pins: e^obs, the centroid step and the

@@ -134,6 +134,48 @@ def pin_centroid_gain(O):
             assert abs(left - f["centroid_contraction_k075"]["value"]) <= 1e-9, left
 
 
+def pin_centroid_newton_gain(O):
+    """Sec. 2 says k can also be "determined iteratively"; the oracle's k_gain <= 0
+    branch takes it from the moments, as a Newton step on sum I W theta = 0.  For
+    an elliptical Gaussian profile exp(-R^2(theta - D; g)/2 s^2) under a weight
+    exp(-R^2(theta; g)/2 s_w^2) of the same g (Eq. A1), the product is a Gaussian,
+    so sum I W theta = N(D) k D with k = s_w^2/(s^2 + s_w^2) and
+    N(D) proportional to exp(-R^2(D; g)/2 (s^2 + s_w^2)).  The Newton step is then
+    D / (1 - R^2(D; g)/(s^2 + s_w^2)) (Sherman-Morrison on the rank-one Jacobian),
+    for any g; the fixed gain would give k D instead."""
+    for (s, sw, g1, g2) in ((4.0, 3.0, 0.0, 0.0), (3.0, 3.0, 0.2, -0.25), (2.5, 5.0, -0.3, 0.1),
+                            (3.5, 2.0, 0.1, 0.35)):
+        img = _gauss(96, 96, 48.3, 47.6, g1, g2, s)
+        st = O.moment_step(img, 48.0, 48.0, g1, g2, sw, k_gain=0.0, ellip=False)
+        gg = g1 * g1 + g2 * g2
+        dx, dy = 0.3, -0.4
+        R2 = (1 + gg - 2 * g1) * dx * dx + (1 + gg + 2 * g1) * dy * dy - 4 * g2 * dx * dy
+        f = 1.0 / (1.0 - R2 / (s * s + sw * sw))
+        assert st["ok"], st
+        assert abs(st["dx"] - dx * f) <= 1e-10 and abs(st["dy"] - dy * f) <= 1e-10, (s, sw, g1, g2, st, f)
+
+
+def pin_gain_independent_fixed_point(O):
+    """The fixed point sum I W theta = 0 of Sec. 2 does not depend on the gain k:
+    on noisy stamps the iteration with k determined from the moments (k_gain = 0)
+    and with the paper's fixed k = 0.75 converge to the same centre and
+    ellipticity, with fewer passes for the determined gain; the fixed gain of 1
+    (Eqs. 5-6 with k = 1) reaches it as well."""
+    batch = synth.make_workload(0, count=12)
+    for i in range(batch.count):
+        I = batch.stamp(i)
+        ref = O.measure(I, opts=O.default_opts(k_gain=0.75))
+        if not (ref["status"] & 1):
+            continue
+        for k in (0.0, 1.0):
+            r = O.measure(I, opts=O.default_opts(k_gain=k))
+            assert r["status"] & 1, (i, k, r)
+            for key in ("x0", "y0", "e1", "e2"):
+                assert abs(r[key] - ref[key]) <= 1e-9, (i, k, key, r[key], ref[key])
+            if k == 0.0:
+                assert r["it_mom"] <= ref["it_mom"], (i, r["it_mom"], ref["it_mom"])
+
+
 def pin_ellipticity_exact(O):
     """For an elliptical profile f(R(g)) the weight W(R(g_w)) at g_w = g makes the
     product a sheared circular function, so e^obs = 2g/(1+g^2) = e_w and g is the
@@ -549,7 +591,8 @@ def pin_edge_cases(O):
 
 
 ALL_PINS = [pin_gamma_p_library, pin_sersic_b, pin_sersic_db, pin_flux_closed_form,
-            pin_flux_pixel_sum, pin_centroid_symmetric, pin_centroid_gain, pin_ellipticity_exact,
+            pin_flux_pixel_sum, pin_centroid_symmetric, pin_centroid_gain, pin_centroid_newton_gain,
+            pin_gain_independent_fixed_point, pin_ellipticity_exact,
             pin_ellipticity_step_newton, pin_matched_sigma_w, pin_stages_chain, pin_fit_noiseless,
             pin_fit_gradient_fd, pin_fit_minimum, pin_fit_chi2_distribution, pin_r50_gaussian,
             pin_chi2_grad_fd, pin_chi2_grad_noiseless, pin_star_gaussian, pin_star_moffat,

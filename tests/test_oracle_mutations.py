@@ -16,6 +16,14 @@ MUTATIONS = {
     "weight_width": ("double c = 1.0 / (2.0 * sw * sw);", "double c = 1.0 / (sw * sw);"),
     # Eqs. 5-6: gain k dropped from the centroid step
     "centroid_gain": ("s.dx = mx / (k_gain * N);", "s.dx = mx / N;"),
+    # Sec. 2, k determined from the moments: sign of the g2 cross term of d<x>/dy_c
+    "newton_J12_sign": ("double J12 = 2.0 * c * (B * Q12 - 2.0 * gw2 * Q11);",
+                        "double J12 = 2.0 * c * (B * Q12 + 2.0 * gw2 * Q11);"),
+    # Sec. 2, k determined from the moments: the -N of d<x>/dx_c dropped
+    "newton_J11_N": ("double J11 = 2.0 * c * (A * Q11 - 2.0 * gw2 * Q12) - N;",
+                     "double J11 = 2.0 * c * (A * Q11 - 2.0 * gw2 * Q12);"),
+    # Sec. 2, k determined from the moments: the Newton solve with J transposed
+    "newton_transpose": ("s.dx = -(J22 * mx - J12 * my) / dj;", "s.dx = -(J22 * mx - J21 * my) / dj;"),
     # Eq. A5: transposed operand in the X^SH_21 integrand
     "XSH21_operand": ("X21 += f * (4.0 * Wp * p12 * a1);", "X21 += f * (4.0 * Wp * p12 * a2);"),
     # Eq. B9: dropped W' term of P_1
