@@ -54,7 +54,7 @@ def config_dict(n, world):
         "stamps_per_gpu": n,
         "stamp_px": [48, 48],
         "pixel_dtype": "f32",
-        "launch": "one fse_fit_batch per step (two persistent kernel launches: moments, then fit)",
+        "launch": "one fse_fit_batch per step (three persistent kernel launches: start-up, moments, fit)",
         "l2": "inputs 0.92 GB per GPU, larger than the 129 MB L2; no flush",
         "parallelism": f"replicas{world}",
     }
@@ -309,7 +309,7 @@ def main():
     pb.record(stream)
     torch.cuda.synchronize()
     plain = {"value": pn / (pa.elapsed_time(pb) / 1e3), "unit": UNIT, "stamps": pn,
-             "launches": 2 * pn, "identical_results": bool(torch.equal(pout, out[:pn]))}
+             "launches": 3 * pn, "identical_results": bool(torch.equal(pout, out[:pn]))}
 
     if rank != 0:
         torch.distributed.destroy_process_group()
@@ -331,7 +331,7 @@ def main():
                      "peak_source": "152 SMs x 128 fp32 lanes x 2070 MHz (issue slots, FMA = 1 op)"},
         "cpu_baseline": cpu,
         "plain_per_stamp_launch": plain,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 3 * args.steps,
         "clocks": clk,
         "stats": {"converged_frac": float(conv.mean()), "it_mom_mean": float(res["it_mom"].mean()),
                   "it_fit_mean": float(res["it_fit"][conv].mean()) if conv.any() else 0.0,

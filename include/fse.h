@@ -217,14 +217,15 @@ int fse_sersic_fit(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
                    const fse_opts *opts, fse_result *inout, void *stream);
 
 /* The whole chain of Sec. 4.1 (start-up, centroid + ellipticity from the
- * brightest pixel, fit) in two persistent launches on `stream`: the start-up
- * and the moment iteration, then the fit of every stamp whose moments
- * converged.  Results are those of the three single stages run in turn. */
+ * brightest pixel, fit) in three persistent launches on `stream`: the start-up
+ * (brightest pixel, growth-curve r50, sigma_w), the moment iteration, then the
+ * fit of every stamp whose moments converged.  Results are those of the three
+ * single stages run in turn. */
 int fse_fit_batch(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
                   const fse_stamp *idx, int64_t count, const float *inv_var,
                   const fse_opts *opts, fse_result *out, void *stream);
 
-/* The same chain launched per stamp (one warp per launch, two launches per
+/* The same chain launched per stamp (one warp per launch, three launches per
  * stamp).  A baseline for measurement only; results are identical to
  * fse_fit_batch. */
 int fse_fit_batch_plain(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
@@ -312,12 +313,13 @@ int fse_star_fit(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
  * (zero centroid step, Eqs. 3-6; e^obs = e_w, the zero of the step of Eq. 9;
  * the matched weight).  Hence d theta / d I_p = -J^-1 W(p) m(p) with
  * J = dF/dtheta.  mode: FSE_MOM_ELLIP for the Secs. 2-3 fixed point (without
- * it g = 0 is held: the Sec. 2 centroid stage), and the sigma_w rule of the
- * moment stage: the matched weight (default; fse_opts.sigw_mode = 0),
- * FSE_MOM_SIGW_FIXED (held), or FSE_MOM_SIGW_R50 (sigw_mode = 1: sigma_w =
+ * it g = 0 is held: the Sec. 2 centroid stage), and the sigma_w rule the moment
+ * stage used, which the caller must name: FSE_MOM_SIGW_R50 for moments
+ * computed with fse_opts.sigw_mode = 1 (the fse_opts_default setting: sigma_w =
  * r50/sqrt(2 ln 2) from the start-up growth curve, Sec. 4.1, differentiated
- * with the brightest pixel and the crossing ring held).  A stamp whose status
- * has FSE_ST_SIGW_CLAMPED holds sigma_w.
+ * with the brightest pixel and the crossing ring held); neither sigma_w bit for
+ * sigw_mode = 0 (the matched weight); FSE_MOM_SIGW_FIXED to hold sigma_w.  A
+ * stamp whose status has FSE_ST_SIGW_CLAMPED holds sigma_w.
  * moments[s]: x0, y0, e1, e2, sigma_w, r50 and status of a moment stage
  * (fse_centroid, fse_ellipticity or fse_fit_batch).
  * fse_moment_vjp: v[s*5 + k] = dL/dtheta_k (entries of held parameters are
@@ -403,7 +405,9 @@ int fse_sync_check(fse_ctx *ctx, void *stream);
  *    indexes; a larger count returns FSE_EINVAL with a message.
  *  - First call on a device: builds the b(n) table (a kernel and a device
  *    synchronise) and looks up the scratch address; make it before any stream
- *    capture.  Later calls only clear the scratch and launch.
+ *    capture.  Later calls only clear the scratch and launch.  Both belong to
+ *    the device's CUDA context: the first call after a cudaDeviceReset (a new
+ *    primary context) sets them up again in the same way.
  *  - Calls that can overlap on the GPU (different streams or host threads)
  *    share the scratch and race: issue them in order on one stream.
  *  - A bounded device wait that expires marks the stamp FSE_ST_TIMEOUT.

@@ -265,7 +265,7 @@ class Context:
         return self._dev_call("fse_sersic_fit", pix, index, inout, scale, inv_var, opts, stream)
 
     def fit_batch(self, pix, index, *, scale=None, inv_var=None, opts=None, out=None, stream=None):
-        """fse_fit_batch: the whole chain in two persistent launches (moments, then fit)."""
+        """fse_fit_batch: the whole chain in three persistent launches (start-up, moments, fit)."""
         return self._dev_call("fse_fit_batch", pix, index, out, scale, inv_var, opts, stream)
 
     def fit_batch_plain(self, pix, index, *, scale=None, inv_var=None, opts=None, out=None,

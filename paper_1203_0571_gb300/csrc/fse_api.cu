@@ -74,7 +74,22 @@ namespace {
 
 constexpr int kQueues = 64;
 std::mutex g_table_mutex;
+// the context in which each device's b(n) table was built (0: not built); a
+// device reset makes a new primary context, whose table is built again
+unsigned long long g_table_ctx[256];
 bool g_table_built[256];
+
+// Build the b(n) table of the current device unless it exists in the current
+// context.  Synchronises the device when it builds.  Call under g_table_mutex.
+cudaError_t ensure_bn_table(int device) {
+    if (g_table_built[device] && g_table_ctx[device] == fse::current_context_id()) return cudaSuccess;
+    cudaError_t e = fse::build_bn_table(nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return e;
+    g_table_built[device] = true;
+    g_table_ctx[device] = fse::current_context_id();   // the launch made the context current
+    return cudaSuccess;
+}
 
 int set_error(fse_ctx* ctx, int code, const char* fmt, ...) {
     if (ctx) {
@@ -356,6 +371,7 @@ constexpr int kStaticWords = 2;                      // [0] work counter, [1] er
 constexpr int64_t kStaticMaxCount = 0x7fffffffLL;    // the 32-bit counter indexes at most this
 static __device__ __align__(256) unsigned int g_static_scratch[kStaticWords];
 unsigned int* g_static_addr[256];                    // its address on each device
+unsigned long long g_static_ctx[256];                 // in the context it was looked up in
 
 }  // namespace
 
@@ -421,15 +437,10 @@ int fse_create(fse_ctx** out, int device) {
     }
     {
         std::lock_guard<std::mutex> lk(g_table_mutex);
-        if (!g_table_built[device]) {
-            cudaError_t e = fse::build_bn_table(nullptr);
-            if (e == cudaSuccess) e = cudaDeviceSynchronize();
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                fse_destroy(ctx);
-                return FSE_ECUDA;
-            }
-            g_table_built[device] = true;
+        if (ensure_bn_table(device) != cudaSuccess) {
+            cudaGetLastError();
+            fse_destroy(ctx);
+            return FSE_ECUDA;
         }
     }
     *out = ctx;
@@ -1019,17 +1030,15 @@ int fse_fit_batch_static(const void* pix, int dtype, const float* scale, const f
         // first call on this device: the b(n) table (static device storage,
         // built by a kernel, then a device synchronise) and the scratch address
         std::lock_guard<std::mutex> lk(g_table_mutex);
-        if (!g_table_built[dev]) {
-            e = fse::build_bn_table(nullptr);
-            if (e == cudaSuccess) e = cudaDeviceSynchronize();
-            if (e != cudaSuccess) return fail(cuda_fail(&sink, e, "b(n) table"));
-            g_table_built[dev] = true;
-        }
-        if (!g_static_addr[dev]) {
+        e = ensure_bn_table(dev);
+        if (e != cudaSuccess) return fail(cuda_fail(&sink, e, "b(n) table"));
+        const unsigned long long cid = fse::current_context_id();
+        if (!g_static_addr[dev] || g_static_ctx[dev] != cid) {
             void* p = nullptr;
             e = cudaGetSymbolAddress(&p, g_static_scratch);
             if (e != cudaSuccess) return fail(cuda_fail(&sink, e, "static scratch address"));
             g_static_addr[dev] = static_cast<unsigned int*>(p);
+            g_static_ctx[dev] = cid;
         }
         scratch = g_static_addr[dev];
     }

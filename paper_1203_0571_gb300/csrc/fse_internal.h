@@ -14,8 +14,10 @@ enum Stage : int {
     kStageCentroid = 1,     // start-up + Sec. 2 centroid (circular weight)
     kStageEllipticity = 2,  // Secs. 2-3 from a given centre and sigma_w
     kStageFit = 3,          // Sec. 4.1 fit with centre and g fixed
-    kStageAll = 4,          // whole chain: runs as kStageMoments, then kStageFit with chain_fit
-    kStageMoments = 5,      // start-up + Secs. 2-3 (the first launch of the chain)
+    kStageAll = 4,          // whole chain: kStageStartup, kStageMoments, then kStageFit with chain_fit
+    kStageMoments = 5,      // Secs. 2-3 from the start-up's record (the second launch of the chain)
+    kStageStartup = 6,      // start-up alone: brightest pixel, growth-curve r50, sigma_w (Sec. 4.1);
+                            // the first launch of the chain and of fse_centroid
 };
 
 // Options as the kernels see them (fp32 where the per-pixel code uses them).
@@ -28,6 +30,8 @@ struct DevOpts {
     float n_min, n_max, re_min, re_max_frac;
     float lm_lambda0;
     int supersample;     // S > 1: the fit's model is the mean of S x S samples per pixel
+    int ring_slots;      // rings of the start-up histogram a stamp of max_pix pixels can need
+                         // (set at launch from max_pix)
 };
 
 struct LaunchArgs {
@@ -159,6 +163,12 @@ cudaError_t launch_chi2_grad(const GradArgs& a, cudaStream_t stream);
 // Shared memory of one stamp group (warps_per_stamp warps) for stamps of up
 // to max_pix pixels, with the per-pixel inverse-variance tile when ivar is set.
 size_t smem_per_group(int max_pix, bool ivar, int warps_per_stamp);
+// Identity of the calling thread's current CUDA context (the driver's context
+// id), or 0 when it cannot be had.  State kept per device for the life of the
+// process (the b(n) table, the shared-memory opt-in of a kernel, the static
+// scratch address) belongs to a context: after cudaDeviceReset the device's
+// primary context is a new one and that state must be set up again.
+unsigned long long current_context_id();
 // Library launch shape for a tile size: warps per stamp, and warps per CTA
 // (a multiple of it) as large as shared memory allows, up to four groups.
 void choose_launch(int max_pix, int* warps_per_cta, int* warps_per_stamp);

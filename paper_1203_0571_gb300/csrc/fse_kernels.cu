@@ -18,6 +18,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "fse_device.cuh"
 #include "fse_internal.h"
 
@@ -320,28 +322,51 @@ __host__ __device__ inline size_t group_bytes(int max_pix, bool ivar, int nw) {
     return warp_bytes(max_pix, ivar) + (nw > 1 ? static_cast<size_t>(nw) * 128 + 16 : 0);
 }
 
+// Rings the start-up's growth curve can need for stamps of at most max_pix
+// pixels and sides of at most FSE_MAX_SIDE: ring k holds the pixels at
+// distance k-1 < d <= k from the brightest pixel, so a stamp needs rings 0 to
+// ceil(corner distance) + 1 (the histogram's kmax), and the corner distance
+// is at most that of the most elongated h x w with h w <= max_pix.
+inline int ring_slots(int max_pix) {
+    int best = 0;
+    for (int h = 1; h <= FSE_MAX_SIDE; ++h) {
+        int w = max_pix / h;
+        if (w < 1) break;
+        if (w > FSE_MAX_SIDE) w = FSE_MAX_SIDE;
+        const int d = (h - 1) * (h - 1) + (w - 1) * (w - 1);
+        if (d > best) best = d;
+    }
+    int k = 0;
+    while (k * k < best) ++k;
+    return k + 2;
+}
+
 // The moment stages keep a smaller tile: the pixels, and an auxiliary area
-// only for the start-up's ring histogram (at most 182 rings for sides up to
-// 128) or the raw bf16 staging; no inverse variance (the moments do not use
-// it).  For 48x48 that is 10.7 KB per warp instead of 18.5 KB, so more warps
-// share an SM.
-constexpr size_t kHistBytes = 182 * 8;
-__host__ __device__ inline size_t aux_bytes_moments(int max_pix, bool bf16) {
+// only for the raw bf16 staging and, in the start-up launch, the ring
+// histogram (three 32-bit words per ring); no inverse variance (the moments do
+// not use it).  For 48x48 fp32 that is 9.2 KB per warp in the moment launch
+// and 10.8 KB in the start-up, instead of the fit's 18.5 KB.
+__host__ __device__ inline size_t aux_bytes_moments(int max_pix, bool bf16, int slots) {
     const size_t raw = bf16 ? static_cast<size_t>(max_pix + 8) * 2 : 0;
-    return align16(raw > kHistBytes ? raw : kHistBytes);
+    const size_t hist = static_cast<size_t>(slots) * 12;
+    return align16(raw > hist ? raw : hist);
 }
 __host__ __device__ inline constexpr bool moment_stage(int stage) {
-    return stage == kStageCentroid || stage == kStageEllipticity || stage == kStageMoments;
+    return stage == kStageCentroid || stage == kStageEllipticity || stage == kStageMoments ||
+           stage == kStageStartup;
 }
-__host__ __device__ inline size_t stage_aux_bytes(int stage, int max_pix, bool bf16) {
-    return moment_stage(stage) ? aux_bytes_moments(max_pix, bf16) : aux_bytes(max_pix);
+__host__ __device__ inline size_t stage_aux_bytes(int stage, int max_pix, bool bf16, int slots) {
+    return moment_stage(stage) ? aux_bytes_moments(max_pix, bf16, stage == kStageStartup ? slots : 0)
+                               : aux_bytes(max_pix);
 }
-__host__ __device__ inline size_t stage_warp_bytes(int stage, int max_pix, bool bf16, bool ivar) {
-    return pix_bytes(max_pix) + stage_aux_bytes(stage, max_pix, bf16) +
+__host__ __device__ inline size_t stage_warp_bytes(int stage, int max_pix, bool bf16, bool ivar, int slots) {
+    return pix_bytes(max_pix) + stage_aux_bytes(stage, max_pix, bf16, slots) +
            (ivar && !moment_stage(stage) ? pix_bytes(max_pix) : 0) + 16;
 }
-__host__ __device__ inline size_t stage_group_bytes(int stage, int max_pix, bool bf16, bool ivar, int nw) {
-    return stage_warp_bytes(stage, max_pix, bf16, ivar) + (nw > 1 ? static_cast<size_t>(nw) * 128 + 16 : 0);
+__host__ __device__ inline size_t stage_group_bytes(int stage, int max_pix, bool bf16, bool ivar, int nw,
+                                                    int slots) {
+    return stage_warp_bytes(stage, max_pix, bf16, ivar, slots) +
+           (nw > 1 ? static_cast<size_t>(nw) * 128 + 16 : 0);
 }
 
 // Stage a stamp (npix elements at gsrc) into shared memory.  The 16-byte
@@ -420,6 +445,11 @@ __device__ bool stage_stamp(float* buf, float** stamp, float* raw, const void* g
     g.sync();
     return ok;
 }
+
+// Model values above this many noise sigmas carry an fp32 rounding (6e-8 of the
+// value) that is no longer small against the residual; the final refinement
+// of the fit evaluates chi^2 for those pixels in fp64.
+constexpr float kBrightSigma = 512.f;
 
 // ------------------------------------------------------------------ moments
 struct MomState {
@@ -508,9 +538,9 @@ struct MomStep {
     bool ok;
 };
 
-__device__ __forceinline__ void shear_polarizability(const float (&m)[11], const MomState& st,
-                                                     float e1, float e2, float* P11, float* P12,
-                                                     float* P21, float* P22);
+__device__ __noinline__ void shear_polarizability(const float (&m)[11], const MomState& st,
+                                                  float e1, float e2, float* P11, float* P12,
+                                                  float* P21, float* P22);
 
 // The centroid step <x>/N = k dx (Eqs. 5-6) and the ellipticity step
 // dg = (1-|g_w|^2) (P^SH)^-1 (e^obs - e_w) (Eq. 9) with
@@ -563,6 +593,23 @@ __device__ __forceinline__ MomStep moment_step(const float (&m)[11], const MomSt
     }
     const float SR2 = A * Q11 + B * Q22 - 4.f * g2 * Q12;      // sum f W R^2
     r.sw_new = SR2 > 0.f ? sqrtf(SR2 / S0) : 0.f;
+    {
+        // The matched-weight rule s_w^2 = S(s_w) = sum f W R^2 / sum f W contracts
+        // slowly for cuspy profiles; near its fixed point take a Newton step on
+        // s_w^2 - S(s_w) = 0 instead, with dS/ds_w = (<R^4> - <R^2>^2) / s_w^3
+        // (<.> the f W - weighted means; sum f W R^4 from the fourth moments).
+        // The fixed point is the same.
+        const float G4 = 4.f * g2;
+        const float SR4 = A * A * m[6] + B * B * m[10] + (G4 * G4 + 2.f * A * B) * m[8] -
+                          2.f * A * G4 * m[7] - 2.f * B * G4 * m[9];
+        const float sw = st.sw, S = SR2 / S0;
+        const float dS = (SR4 / S0 - S * S) / (sw * sw * sw);
+        const float dF = 2.f * sw - dS;
+        const float sn = sw - (sw * sw - S) / dF;
+        if (fabsf(r.sw_new - sw) < 0.2f * sw && dF > 0.1f * sw && sn > 0.5f * sw && sn < 1.5f * sw &&
+            isfinite(sn))
+            r.sw_new = sn;
+    }
     if (!ellip) {
         r.ok = isfinite(r.dx) && isfinite(r.dy);
         return r;
@@ -584,10 +631,12 @@ __device__ __forceinline__ MomStep moment_step(const float (&m)[11], const MomSt
 }
 
 // P^SH = X^SH + dX^SH - e (e^SH + de^SH)^T (Eq. 8 with A5, A6, B7, B8) from the
-// eleven weighted moments; W' = dW/dR^2 = -c W with c = 1/(2 s_w^2).
-__device__ __forceinline__ void shear_polarizability(const float (&m)[11], const MomState& st,
-                                                     float e1, float e2, float* P11, float* P12,
-                                                     float* P21, float* P22) {
+// eleven weighted moments; W' = dW/dR^2 = -c W with c = 1/(2 s_w^2).  Kept out
+// of line: it is called once per pass from two places, and the moment
+// kernel's code size (instruction fetch) matters more than a call.
+__device__ __noinline__ void shear_polarizability(const float (&m)[11], const MomState& st,
+                                                  float e1, float e2, float* P11, float* P12,
+                                                  float* P21, float* P22) {
     const float Q11 = m[3], Q12 = m[4], Q22 = m[5];
     const float F40 = m[6], F31 = m[7], F22 = m[8], F13 = m[9], F04 = m[10];
     const float g1 = st.g1, g2 = st.g2;
@@ -632,64 +681,86 @@ __device__ __forceinline__ void shear_polarizability(const float (&m)[11], const
 }
 
 // Final refinement of the fixed point: one pass with the pixel offsets theta
-// kept exactly as float pairs, W to about one ulp (exp2_acc) and the
-// zeroth, first and second moments accumulated in double-float, followed by
-// one step from these sums: a Newton step for the centre (the derivative of
-// the weighted first moments, i.e. k taken from the moments) and the step of
-// Eq. 9 for g.  The fp32 iteration stops within the noise of its own sums
-// (~1e-6 px); this pass removes most of that noise.
+// (the fourth moments F, which only shape the step of Eq. 9 and the matched
+// weight's derivative, come from the iteration's last pass, a step away)
+// kept exactly as float pairs, the weight's exponent R^2 / (2 s_w^2) carried
+// as a float pair (the rounding of every step of Eq. A1 kept), W to about one
+// ulp (exp2_acc), and the zeroth, first and second moments accumulated in
+// double-float with the rounding of each product kept; then one step from
+// these sums: a Newton step for the centre (the derivative of the weighted
+// first moments, i.e. k taken from the moments), the step of Eq. 9 for g and,
+// for the matched weight, a Newton step for s_w.  The fp32 iteration stops
+// within the noise of its own sums (~1e-6 px); this pass removes most of
+// that noise.  The fixed point's accuracy is set by the weights' rounding:
+// with an fp32 exponent (relative errors of ~2e-7 at two weight sizes) the
+// centre moved by ~1e-7 px, which first-order chi^2 sensitivities of up to
+// ~6e5 per px on bright stamps turn into 1e-5 of chi^2.
 template <int NW>
 __device__ float moment_refine(const float* __restrict__ s, int w, int npix, const Grp<NW>& g,
-                               bool ellip, MomState& st) {
+                               bool ellip, bool matched, float sw_max, const float (&F)[5], MomState& st) {
     const float gg = st.g1 * st.g1 + st.g2 * st.g2;
     const float A = 1.f + gg - 2.f * st.g1;
     const float B = 1.f + gg + 2.f * st.g1;
     const float G4 = 4.f * st.g2;
     const float cw = -kLog2e / (2.f * st.sw * st.sw);
-    float dh[6], dl[6], cx[5], F[5];
+    float dh[6], dl[6], cx[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) dh[i] = dl[i] = 0.f;
-#pragma unroll
-    for (int i = 0; i < 5; ++i) cx[i] = F[i] = 0.f;
+    for (int i = 0; i < 6; ++i) dh[i] = dl[i] = cx[i] = 0.f;
     OffsetWalk ow(g.t, w, Grp<NW>::NT, st.xi, st.yi);
+#pragma unroll 1
     for (int p = g.t; p < npix; p += Grp<NW>::NT) {
         const float k1 = ow.u, k2 = ow.v;
         // theta = k - x_f exactly as hi + lo (|k| >= |x_f| unless k = 0, where lo = 0)
         const float t1 = k1 - st.xf, t1l = -st.xf - (t1 - k1);
         const float t2 = k2 - st.yf, t2l = -st.yf - (t2 - k2);
-        const float t11 = t1 * t1, t22 = t2 * t2, t12 = t1 * t2;
-        const float R2 = fmaf(A, t11, fmaf(B, t22, -G4 * t12));
-        const float f = s[p] * exp2_acc(R2 * cw);
+        // theta_a theta_b as hi + lo: the rounding of the product and the first-order low parts
+        const float p11 = t1 * t1, e11 = fmaf(t1, t1, -p11) + 2.f * t1 * t1l;
+        const float p22 = t2 * t2, e22 = fmaf(t2, t2, -p22) + 2.f * t2 * t2l;
+        const float p12 = t1 * t2, e12 = fmaf(t1, t2, -p12) + fmaf(t1, t2l, t1l * t2);
+        // R^2 = A theta1^2 + B theta2^2 - 4 g2 theta1 theta2 (Eq. A1) as hi + lo
+        const float ra = A * p11, rb = B * p22, rc = G4 * p12;
+        const float s1 = ra + rb;
+        const float s1e = (ra - (s1 - (s1 - ra))) + (rb - (s1 - ra));
+        const float R2 = s1 - rc;
+        const float R2e = (s1 - (R2 - (R2 - s1))) + (-rc - (R2 - s1));
+        const float R2l = (fmaf(A, p11, -ra) + fmaf(B, p22, -rb) - fmaf(G4, p12, -rc)) + (s1e + R2e) +
+                          fmaf(A, e11, fmaf(B, e22, -G4 * e12));
+        const float x = R2 * cw;
+        const float xl = fmaf(R2, cw, -x) + R2l * cw;
+        const float Wh = exp2_acc(x);
+        const float W = fmaf(Wh, xl * static_cast<float>(kLn2), Wh);
+        const float I = s[p];
+        const float f = I * W, fl = fmaf(I, W, -f);
+        float q;
         df_add(dh[0], dl[0], f);
-        df_add(dh[1], dl[1], f * t1);
-        df_add(dh[2], dl[2], f * t2);
-        df_add(dh[3], dl[3], f * t11);
-        df_add(dh[4], dl[4], f * t12);
-        df_add(dh[5], dl[5], f * t22);
-        cx[0] = fmaf(f, t1l, cx[0]);
-        cx[1] = fmaf(f, t2l, cx[1]);
-        cx[2] = fmaf(2.f * f * t1, t1l, cx[2]);
-        cx[3] = fmaf(f, fmaf(t1, t2l, t1l * t2), cx[3]);
-        cx[4] = fmaf(2.f * f * t2, t2l, cx[4]);
-        const float f11 = f * t11, f22 = f * t22;
-        F[0] = fmaf(f11, t11, F[0]);
-        F[1] = fmaf(f11, t12, F[1]);
-        F[2] = fmaf(f11, t22, F[2]);
-        F[3] = fmaf(f22, t12, F[3]);
-        F[4] = fmaf(f22, t22, F[4]);
+        cx[0] += fl;
+        q = f * t1;
+        df_add(dh[1], dl[1], q);
+        cx[1] += fmaf(f, t1, -q) + fmaf(f, t1l, fl * t1);
+        q = f * t2;
+        df_add(dh[2], dl[2], q);
+        cx[2] += fmaf(f, t2, -q) + fmaf(f, t2l, fl * t2);
+        q = f * p11;
+        df_add(dh[3], dl[3], q);
+        cx[3] += fmaf(f, p11, -q) + fmaf(f, e11, fl * p11);
+        q = f * p12;
+        df_add(dh[4], dl[4], q);
+        cx[4] += fmaf(f, p12, -q) + fmaf(f, e12, fl * p12);
+        q = f * p22;
+        df_add(dh[5], dl[5], q);
+        cx[5] += fmaf(f, p22, -q) + fmaf(f, e22, fl * p22);
         ow.next();
     }
     g.allsum_df(dh, dl);
     g.allsum(cx);
-    g.allsum(F);
     // The first moments vanish at the fixed point; once accumulated exactly
     // they are small numbers that fp32 carries to full relative precision.
-    const float M0 = dh[0] + dl[0];
-    const float M1x = dh[1] + (dl[1] + cx[0]);
-    const float M1y = dh[2] + (dl[2] + cx[1]);
-    const float Q11 = dh[3] + (dl[3] + cx[2]);
-    const float Q12 = dh[4] + (dl[4] + cx[3]);
-    const float Q22 = dh[5] + (dl[5] + cx[4]);
+    const float M0 = dh[0] + (dl[0] + cx[0]);
+    const float M1x = dh[1] + (dl[1] + cx[1]);
+    const float M1y = dh[2] + (dl[2] + cx[2]);
+    const float Q11 = dh[3] + (dl[3] + cx[3]);
+    const float Q12 = dh[4] + (dl[4] + cx[4]);
+    const float Q22 = dh[5] + (dl[5] + cx[5]);
     if (!(M0 > 0.f) || !(Q11 + Q22 > 0.f)) return 1.f;
     const float c = 1.f / (2.f * st.sw * st.sw);
     const float g1 = st.g1, g2 = st.g2;
@@ -701,14 +772,17 @@ __device__ float moment_refine(const float* __restrict__ s, int w, int npix, con
     if (!(dj > 0.f)) return 1.f;
     const float dx = -(J22 * M1x - J12 * M1y) / dj;
     const float dy = -(-J21 * M1x + J11 * M1y) / dj;
+    // the second moments as doubles (a few operations per stamp): the
+    // residuals below cancel at the fixed point
+    const double M0d = static_cast<double>(dh[0]) + (static_cast<double>(dl[0]) + cx[0]);
+    const double Q11d = static_cast<double>(dh[3]) + (static_cast<double>(dl[3]) + cx[3]);
+    const double Q12d = static_cast<double>(dh[4]) + (static_cast<double>(dl[4]) + cx[4]);
+    const double Q22d = static_cast<double>(dh[5]) + (static_cast<double>(dl[5]) + cx[5]);
     float dg1 = 0.f, dg2 = 0.f;
     if (ellip) {
         // e - e_w = [ (Q11 - Q22, 2 Q12) (1 + |g|^2) - 2 g T ] / (T (1 + |g|^2)): the
-        // bracket cancels at the fixed point, so it is formed from the exact
-        // sums in fp64 (a few multiply-adds) before the fp32 division.
-        const double Q11d = static_cast<double>(dh[3]) + (static_cast<double>(dl[3]) + cx[2]);
-        const double Q22d = static_cast<double>(dh[5]) + (static_cast<double>(dl[5]) + cx[4]);
-        const double Q12d = static_cast<double>(dh[4]) + (static_cast<double>(dl[4]) + cx[3]);
+        // bracket cancels at the fixed point, so it is formed in fp64 before the
+        // fp32 division.
         const double Td = Q11d + Q22d;
         const double opg = 1.0 + static_cast<double>(g1) * g1 + static_cast<double>(g2) * g2;
         const float n1 = static_cast<float>((Q11d - Q22d) * opg - 2.0 * g1 * Td);
@@ -725,14 +799,33 @@ __device__ float moment_refine(const float* __restrict__ s, int w, int npix, con
         dg1 = sc * (P22 * r1 - P12 * r2);
         dg2 = sc * (-P21 * r1 + P11 * r2);
     }
+    float ds = 0.f;
+    if (matched && st.sw > 0.5f && st.sw < sw_max) {
+        // Newton on s_w^2 - sum f W R^2 / sum f W = 0 (the matched weight), the
+        // residual formed in fp64; a step that would leave the clamp interval
+        // is not taken (the iteration's clamped s_w stays)
+        const double sw = st.sw;
+        const double SR2 = static_cast<double>(A) * Q11d + static_cast<double>(B) * Q22d -
+                           static_cast<double>(G4) * Q12d;
+        const float res = static_cast<float>(sw * sw - SR2 / M0d);
+        const float S = static_cast<float>(SR2 / M0d);
+        const float SR4 = A * A * F[0] + B * B * F[4] + (G4 * G4 + 2.f * A * B) * F[2] -
+                          2.f * A * G4 * F[1] - 2.f * B * G4 * F[3];
+        const float dS = (SR4 / M0 - S * S) / (st.sw * st.sw * st.sw);
+        const float dF = 2.f * st.sw - dS;
+        ds = dF > 0.f ? -res / dF : 0.f;
+        if (!(st.sw + ds > 0.5f && st.sw + ds < sw_max) || !isfinite(ds)) ds = 0.f;
+    }
     // a refinement moves the point by at most the iteration's own noise
-    if (!(fabsf(dx) <= 1e-3f && fabsf(dy) <= 1e-3f && fabsf(dg1) <= 1e-3f && fabsf(dg2) <= 1e-3f))
+    if (!(fabsf(dx) <= 1e-3f && fabsf(dy) <= 1e-3f && fabsf(dg1) <= 1e-3f && fabsf(dg2) <= 1e-3f &&
+          fabsf(ds) <= 1e-3f * st.sw))
         return 1.f;
     st.xf += dx;
     st.yf += dy;
     st.g1 += dg1;
     st.g2 += dg2;
-    return fmaxf(fmaxf(fabsf(dx), fabsf(dy)), fmaxf(fabsf(dg1), fabsf(dg2)));
+    st.sw += ds;
+    return fmaxf(fmaxf(fmaxf(fabsf(dx), fabsf(dy)), fmaxf(fabsf(dg1), fabsf(dg2))), fabsf(ds) / st.sw);
 }
 
 constexpr float kMomRefineSkip = 1e-7f;
@@ -745,6 +838,7 @@ __device__ int moment_iterate(const float* s, int h, int w, int npix, const Grp<
     st.yr = st.yi;
     const float sw_max = 0.5f * static_cast<float>(h < w ? h : w);
     float prev = 0.f;   // size of the previous step, for the contraction estimate
+    float F4[5] = {0.f, 0.f, 0.f, 0.f, 0.f};   // the last pass's fourth moments
     // with the determined gain (k_gain = 0): a centre step that does not shrink
     // switches the rest of the iteration to the fixed gain
     float k_use = o.k_gain, prev_c = 0.f;
@@ -752,6 +846,8 @@ __device__ int moment_iterate(const float* s, int h, int w, int npix, const Grp<
     for (it = 1; it <= o.max_iter_mom; ++it) {
         float m[11];
         moment_pass(s, w, npix, g, st, m);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) F4[i] = m[6 + i];
         const MomStep d = moment_step(m, st, k_use, ellip);
         if (k_use <= 0.f) {
             const float dc = fmaxf(fabsf(d.dx), fabsf(d.dy));
@@ -823,9 +919,12 @@ __device__ int moment_iterate(const float* s, int h, int w, int npix, const Grp<
     // centre and g steps are taken separately); a second runs unless the first
     // moved the point by less than 1e-7
     if (status & FSE_ST_MOM_CONVERGED) {
-        if (moment_refine(s, w, npix, g, ellip, st) > kMomRefineSkip) {
-            moment_refine(s, w, npix, g, ellip, st);
-            status |= FSE_ST_MOM_REFINE2;
+        // one call site (the pass is large code): a second round runs only when
+        // the first moved the point by more than kMomRefineSkip
+#pragma unroll 1
+        for (int r = 0; r < 2; ++r) {
+            if (r == 1) status |= FSE_ST_MOM_REFINE2;
+            if (moment_refine(s, w, npix, g, ellip, o.sigw_mode == 0, sw_max, F4, st) <= kMomRefineSkip) break;
         }
     }
     return it;
@@ -837,31 +936,36 @@ struct InitOut {
     float r50;
     bool finite;
     bool fallback;   // stamp total <= 0
+    bool overflow;   // the stamp needs more rings than the tile holds (not expected)
 };
+
+// ceil(sqrt(d2)) for an integer 0 <= d2 <= 2 * 127^2 (sides of at most
+// FSE_MAX_SIDE = 128 pixels), with one MUFU operation and integer arithmetic:
+// d2 becomes a float through the bits of 2^23 + d2 (exact below 2^23), and the
+// root is rounded to the nearest integer k0 by adding 2^23 (whose ulp is 1).
+// sqrt.approx.f32 is within about 2^-22 relative of the square root, under
+// 1e-4 here, so k0 is the floor or the ceiling of the true root, and the
+// comparison k0^2 < d2 turns either into the ceiling.
+__device__ __forceinline__ int ring_of(int d2) {
+    const float f = __int_as_float(0x4B000000 | d2) - 8388608.f;
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(f));
+    const int k0 = __float_as_int(r + 8388608.f) - 0x4B000000;
+    return k0 + (k0 * k0 < d2 ? 1 : 0);
+}
 
 // Brightest pixel, and the half-light radius r50 from the growth curve around
 // it (Sec. 4.1): pixels are binned in rings of integer radius k (k-1 < d <= k)
 // and the enclosed sum is tracked until it reaches half the stamp total; r50
 // interpolates linearly in the ring that crosses.  Sums are exact 64-bit
 // fixed point (pixel * 2^S), so the crossing ring does not depend on the
-// summation order.
-// ceil(sqrt(d2)) for an integer 0 <= d2 <= 2 * 127^2 (sides of at most
-// FSE_MAX_SIDE = 128 pixels).  sqrt.approx.f32 is within about 2^-22 relative
-// of the square root, under 1e-4 absolute here, while the square root of a
-// non-square integer below 2 * 128^2 lies at least 1 / 364 from every
-// integer.  Its floor is therefore the integer square root, or one less at a
-// perfect square, and the comparison turns either into the ceiling.
-__device__ __forceinline__ int ring_of(int d2) {
-    float r;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(static_cast<float>(d2)));
-    int k = static_cast<int>(r);
-    k += (k * k < d2) ? 1 : 0;
-    return k;
-}
-
+// summation order.  Each 64-bit value q is accumulated as three 32-bit
+// pieces, q = q2 2^(2b) + q1 2^b + q0 with 0 <= q0, q1 < 2^b and
+// b = 31 - ceil(log2 npix): no piece's sum over the stamp can leave 32 bits,
+// so native 32-bit shared-memory atomics add them exactly.
 template <int NW>
 __device__ InitOut stamp_init(const float* s, int h, int w, int npix, const Grp<NW>& g,
-                              unsigned long long* hist) {
+                              unsigned* hist, int slots) {
     constexpr int NT = Grp<NW>::NT;
     const int lane = g.lane;
     InitOut o;
@@ -903,6 +1007,7 @@ __device__ InitOut stamp_init(const float* s, int h, int w, int npix, const Grp<
     }
     o.peak = imax;
     o.fallback = false;
+    o.overflow = false;
     o.r50 = static_cast<float>(kSqrt2Ln2);
     if (!o.finite) return o;
     const int pr = imax / w, pc = imax - (imax / w) * w;
@@ -912,68 +1017,77 @@ __device__ InitOut stamp_init(const float* s, int h, int w, int npix, const Grp<
     int S = 62 - e;
     S = S > 100 ? 100 : (S < -100 ? -100 : S);
     const float fs = ldexpf(1.f, S);
-    const int dh = (h - 1 > pr ? h - 1 - pr : pr), dw = (w - 1 > pc ? w - 1 - pc : pc);
+    // the largest row and column distance from the brightest pixel to an edge
+    const int dh = (h - 1 - pr > pr ? h - 1 - pr : pr), dw = (w - 1 - pc > pc ? w - 1 - pc : pc);
     const int kmax = static_cast<int>(ceilf(sqrtf(static_cast<float>(dh * dh + dw * dw)))) + 1;
-    for (int k = g.t; k <= kmax; k += NT) hist[k] = 0ull;
-    g.sync();
-    // Each thread takes a block of C consecutive pixels, starting at offset
-    // t mod C within it and wrapping to the block's start: the threads of a
-    // warp sit about C pixels apart, mostly on different rings, so their
-    // shared-memory atomics seldom meet on one address, and with C + 1 odd
-    // their pixel loads fall in distinct banks.  The sums are integers, so the
-    // order of the additions does not change them.
-    long long tot = 0;
-    const int C = (npix + NT - 1) / NT;
-    const int b0 = g.t * C;
-    const int row0 = b0 / w, col0 = b0 - row0 * w;
-    int j = g.t % C;
-    int p = b0 + j;
-    int row = p / w, col = p - row * w;
-    // not unrolled: unrolled, this loop added 4 KB to the moment kernel's code
-    // and the call took 2% longer (instruction fetch)
-#pragma unroll 1
-    for (int i = 0; i < C; ++i) {
-        if (p < npix) {
-            const long long q = __float2ll_rn(s[p] * fs);
-            tot += q;
-            const int di = row - pr, dj = col - pc;
-            atomicAdd(&hist[ring_of(di * di + dj * dj)], static_cast<unsigned long long>(q));
-        }
-        ++p;
-        if (++col == w) {
-            col = 0;
-            ++row;
-        }
-        if (++j == C) {
-            j = 0;
-            p = b0;
-            row = row0;
-            col = col0;
-        }
-    }
-    tot = g.allsum_ll(tot);
-    g.sync();   // every ring of the histogram is complete (the scan reads them)
-    if (tot <= 0) {
-        o.fallback = true;
+    const int nb = kmax + 1;
+    if (nb > slots) {   // the tile is sized for every stamp it may hold; kept as a guard
+        o.overflow = true;
         return o;
     }
+    unsigned* h0 = hist;
+    unsigned* h1 = hist + nb;
+    int* h2 = reinterpret_cast<int*>(hist + 2 * nb);
+    for (int k = g.t; k < 3 * nb; k += NT) hist[k] = 0u;
+    g.sync();
+    const int b = 31 - (npix > 1 ? 32 - __clz(npix - 1) : 0);
+    const unsigned mask = (1u << b) - 1u;
+    // Each thread takes a block of Cb consecutive pixels, Cb odd: the threads
+    // of a warp sit about Cb pixels apart (a row or more), mostly on
+    // different rings, so the atomics of one instruction seldom meet on one
+    // address, and their pixel loads fall in distinct banks.  The sums are
+    // integers, so the order of the additions does not change them.
+    {
+        const int Cb = ((npix + NT - 1) / NT) | 1;
+        const int b0 = g.t * Cb;
+        const int pend = b0 + Cb < npix ? b0 + Cb : npix;
+        int row = b0 / w, col = b0 - row * w;
+        int di = row - pr, dj = col - pc;
+        int d2 = di * di + dj * dj;
+#pragma unroll 1
+        for (int p = b0; p < pend; ++p) {
+            const long long q = __float2ll_rn(s[p] * fs);
+            const int k = ring_of(d2);
+            atomicAdd(&h0[k], static_cast<unsigned>(q) & mask);
+            atomicAdd(&h1[k], static_cast<unsigned>(static_cast<unsigned long long>(q) >> b) & mask);
+            atomicAdd(&h2[k], static_cast<int>(q >> (2 * b)));
+            // the next pixel: one column on, or the first of the next row
+            d2 += 2 * dj + 1;
+            ++dj;
+            if (++col == w) {
+                col = 0;
+                ++di;
+                dj = -pc;
+                d2 = di * di + dj * dj;
+            }
+        }
+    }
+    g.sync();   // every ring of the histogram is complete (the scan reads them)
     // warp scan over the rings: lane owns rings [lane*ch, lane*ch + ch)
-    const int nb = kmax + 1;
     const int ch = (nb + 31) / 32;
     const int k0 = lane * ch;
     long long own = 0;
-    for (int k = k0; k < k0 + ch && k < nb; ++k) own += static_cast<long long>(hist[k]);
+    for (int k = k0; k < k0 + ch && k < nb; ++k)
+        own += static_cast<long long>(h0[k]) + (static_cast<long long>(h1[k]) << b) +
+               static_cast<long long>(h2[k]) * (1ll << (2 * b));
     long long incl = own;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         const long long o2 = __shfl_up_sync(kFull, incl, off);
         if (lane >= off) incl += o2;
     }
+    const long long tot = __shfl_sync(kFull, incl, 31);
+    if (tot <= 0) {
+        o.fallback = true;
+        g.sync();   // the histogram's space is reused after this
+        return o;
+    }
     long long run = incl - own;     // enclosed sum before ring k0
     int kc = -1;
     long long prev = 0, cur = 0;
     for (int k = k0; k < k0 + ch && k < nb; ++k) {
-        const long long nxt = run + static_cast<long long>(hist[k]);
+        const long long nxt = run + static_cast<long long>(h0[k]) + (static_cast<long long>(h1[k]) << b) +
+                              static_cast<long long>(h2[k]) * (1ll << (2 * b));
         if (2 * nxt >= tot) {
             kc = k;
             prev = run;
@@ -1233,10 +1347,6 @@ struct Precise {
     bool ok;
 };
 
-// Model values above this many noise sigmas carry an fp32 rounding (6e-8 of the
-// value) that is no longer small against the residual; the final refinement
-// evaluates chi^2 for those pixels in fp64.
-constexpr float kBrightSigma = 512.f;
 
 // fp64 squared residual of one bright pixel (kept out of line: rarely taken).
 struct BrightModel {
@@ -1462,8 +1572,8 @@ __device__ Precise fit_refine(const float* __restrict__ s, const float* __restri
                 rr_lo = static_cast<float>(rrd - rr_hi);
                 bright = true;
             }
+            pw.next();
         }
-        pw.next();
         if (IVAR) {
             const float q = sq[p];
             E *= q;
@@ -1713,9 +1823,12 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
 template <int STAGE, int DT, bool IVAR, int NW, bool SUP = false>
 // Fit stages: 168 registers per thread let three CTAs of four warps share an
 // SM (the launch shape of 48x48 and smaller tiles); more would leave two.
-// Moment stages: 96 registers (they need 102 uncapped, and spill nothing at
-// 96) let five CTAs of four warps share an SM with their compact tile.
-__global__ void __maxnreg__(moment_stage(STAGE) ? 96 : 168) estimator_kernel(LaunchArgs a) {
+// Moment stages and the start-up: 96 registers (they spill nothing at 96) let
+// five CTAs of four warps share an SM with their compact tile.  With eight
+// warps per stamp (the 128x128 tiles) the tile already limits an SM to two
+// CTAs of 256 threads, so 128 registers cost no occupancy and keep the group
+// reductions of the refinement pass out of local memory.
+__global__ void __maxnreg__(moment_stage(STAGE) ? (NW >= 8 ? 128 : 96) : 168) estimator_kernel(LaunchArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -1728,12 +1841,14 @@ __global__ void __maxnreg__(moment_stage(STAGE) ? 96 : 168) estimator_kernel(Lau
     const int max_pix = a.opts.max_pix;
     constexpr bool kBf16 = DT == FSE_BF16;
     constexpr bool kIv = IVAR && !moment_stage(STAGE);   // the moments do not use inverse variance
-    const size_t wb = stage_warp_bytes(STAGE, max_pix, kBf16, IVAR);
-    unsigned char* wbase = smem + static_cast<size_t>(grp) * stage_group_bytes(STAGE, max_pix, kBf16, IVAR, NW);
+    const int slots = a.opts.ring_slots;
+    const size_t wb = stage_warp_bytes(STAGE, max_pix, kBf16, IVAR, slots);
+    unsigned char* wbase =
+        smem + static_cast<size_t>(grp) * stage_group_bytes(STAGE, max_pix, kBf16, IVAR, NW, slots);
     float* pixbuf = reinterpret_cast<float*>(wbase);
     float* aux = reinterpret_cast<float*>(wbase + pix_bytes(max_pix));
     float* ivbuf = kIv ? reinterpret_cast<float*>(wbase + pix_bytes(max_pix) +
-                                                  stage_aux_bytes(STAGE, max_pix, kBf16))
+                                                  stage_aux_bytes(STAGE, max_pix, kBf16, slots))
                        : nullptr;
     uint64_t* bar = reinterpret_cast<uint64_t*>(wbase + wb - 16);
     g.red = reinterpret_cast<float*>(wbase + wb);   // used when NW > 1
@@ -1769,18 +1884,27 @@ __global__ void __maxnreg__(moment_stage(STAGE) ? 96 : 168) estimator_kernel(Lau
         const int h = ix.h, w = ix.w;
         const long long npl = static_cast<long long>(h) * w;
         fse_result res;
-        if (STAGE == kStageEllipticity || STAGE == kStageFit) {
-            res = a.out[si];
-        } else {
+        if (STAGE == kStageStartup) {
             res = fse_result{};
+        } else {
+            res = a.out[si];
         }
-        uint32_t status = (STAGE == kStageEllipticity || STAGE == kStageFit)
-                              ? (res.status & (FSE_ST_SIGW_CLAMPED | FSE_ST_INIT_FALLBACK |
+        uint32_t status = STAGE == kStageStartup
+                              ? 0u
+                              : (res.status & (FSE_ST_SIGW_CLAMPED | FSE_ST_INIT_FALLBACK |
                                                (STAGE == kStageFit ? (FSE_ST_MOM_CONVERGED |
                                                                       FSE_ST_MOM_MAXITER)
-                                                                   : 0u)))
-                              : 0u;
+                                                                   : 0u)));
         bool skip = false;
+        if (STAGE == kStageCentroid || STAGE == kStageMoments) {
+            // the record of the start-up launch: a stamp it refused keeps that
+            // record as it is
+            status = res.status;
+            if (status & (FSE_ST_BAD_SIZE | FSE_ST_NONFINITE | FSE_ST_TIMEOUT)) {
+                g.sync();   // every thread has read the record
+                continue;
+            }
+        }
         // the centre as the moment stage holds it (integer + fraction, finer
         // than the float x0 of the record), handed from the first launch of the
         // chain to the second in the record's fit fields
@@ -1831,26 +1955,39 @@ __global__ void __maxnreg__(moment_stage(STAGE) ? 96 : 168) estimator_kernel(Lau
         }
         const int npix = static_cast<int>(npl);
         MomState st;
-        if (!skip && (STAGE == kStageCentroid || STAGE == kStageAll || STAGE == kStageMoments)) {
-            const InitOut in =
-                stamp_init(s, h, w, npix, g, reinterpret_cast<unsigned long long*>(aux));
-            if (!in.finite) {
-                status |= FSE_ST_NONFINITE;
-                skip = true;
-            } else {
-                if (in.fallback) status |= FSE_ST_INIT_FALLBACK;
-                float sw = in.r50 / static_cast<float>(kSqrt2Ln2);
-                const float smax = 0.5f * static_cast<float>(h < w ? h : w);
-                if (sw < 0.5f) { sw = 0.5f; status |= FSE_ST_SIGW_CLAMPED; }
-                if (sw > smax) { sw = smax; status |= FSE_ST_SIGW_CLAMPED; }
-                st.xi = in.peak % w;
-                st.yi = in.peak / w;
-                st.xf = st.yf = 0.f;
-                st.g1 = st.g2 = 0.f;
-                st.sw = sw;
-                res.r50 = in.r50;
-                res.sigma_w = sw;
+        if (STAGE == kStageStartup) {
+            // the start-up of Sec. 4.1, recorded for the moment launch: the
+            // brightest pixel (as x0, y0), r50 and the weight size it gives
+            if (!skip) {
+                const InitOut in = stamp_init(s, h, w, npix, g, reinterpret_cast<unsigned*>(aux), slots);
+                if (!in.finite) {
+                    status |= FSE_ST_NONFINITE;
+                } else if (in.overflow) {
+                    status |= FSE_ST_BAD_SIZE;
+                } else {
+                    if (in.fallback) status |= FSE_ST_INIT_FALLBACK;
+                    float sw = in.r50 / static_cast<float>(kSqrt2Ln2);
+                    const float smax = 0.5f * static_cast<float>(h < w ? h : w);
+                    if (sw < 0.5f) { sw = 0.5f; status |= FSE_ST_SIGW_CLAMPED; }
+                    if (sw > smax) { sw = smax; status |= FSE_ST_SIGW_CLAMPED; }
+                    res.x0 = static_cast<float>(in.peak % w);
+                    res.y0 = static_cast<float>(in.peak / w);
+                    res.r50 = in.r50;
+                    res.sigma_w = sw;
+                }
             }
+            res.status = status;
+            if (g.t == 0) a.out[si] = res;
+            g.sync();
+            continue;
+        }
+        if (!skip && (STAGE == kStageCentroid || STAGE == kStageMoments)) {
+            // start at the brightest pixel with the start-up's weight size
+            st.xi = static_cast<int>(res.x0);
+            st.yi = static_cast<int>(res.y0);
+            st.xf = st.yf = 0.f;
+            st.g1 = st.g2 = 0.f;
+            st.sw = res.sigma_w;
         } else if (!skip) {
             // centre (and for the fit, ellipticity) from the previous stage
             bool fin = true;
@@ -1880,8 +2017,7 @@ __global__ void __maxnreg__(moment_stage(STAGE) ? 96 : 168) estimator_kernel(Lau
         }
         if (!skip && STAGE != kStageFit) {
             const bool ellip = STAGE != kStageCentroid;
-            res.it_mom = moment_iterate(s, h, w, npix, g, o,
-                                        ellip, st, status);
+            res.it_mom = moment_iterate(s, h, w, npix, g, o, ellip, st, status);
             res.x0 = static_cast<float>(st.xi) + st.xf;
             res.y0 = static_cast<float>(st.yi) + st.yf;
             res.sigma_w = st.sw;
@@ -1914,16 +2050,26 @@ __global__ void __maxnreg__(moment_stage(STAGE) ? 96 : 168) estimator_kernel(Lau
 }
 
 template <int STAGE, int DT, bool IVAR, int NW, bool SUP = false>
-cudaError_t launch_t(const LaunchArgs& a, cudaStream_t stream) {
+cudaError_t launch_t(const LaunchArgs& a_in, cudaStream_t stream) {
+    LaunchArgs a = a_in;
+    a.opts.ring_slots = ring_slots(a.opts.max_pix);
     const int groups = a.warps_per_cta / NW;
     if (groups < 1 || groups * NW != a.warps_per_cta || groups > 15) return cudaErrorInvalidValue;
-    const size_t smem = stage_group_bytes(STAGE, a.opts.max_pix, DT == FSE_BF16, IVAR, NW) * groups;
+    const size_t smem =
+        stage_group_bytes(STAGE, a.opts.max_pix, DT == FSE_BF16, IVAR, NW, a.opts.ring_slots) * groups;
     auto kern = estimator_kernel<STAGE, DT, IVAR, NW, SUP>;
-    // the shared-memory opt-in is raised once per instantiation and size (per device)
+    // the shared-memory opt-in is raised once per instantiation and size (per
+    // device and context: a device reset clears it)
     static size_t opted[64] = {0};
+    static unsigned long long opted_ctx[64] = {0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev >= 64) return e != cudaSuccess ? e : cudaErrorInvalidDevice;
+    const unsigned long long cid = current_context_id();
+    if (cid != opted_ctx[dev]) {
+        opted[dev] = 0;
+        opted_ctx[dev] = cid;
+    }
     if (smem > opted[dev]) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem));
@@ -1958,8 +2104,8 @@ cudaError_t launch_nw(const LaunchArgs& a, cudaStream_t stream) {
             return launch_t<STAGE, DT, IVAR, 1, true>(a, stream);
         }
     }
-    // several warps per stamp: the two launches of the whole chain
-    if constexpr (STAGE == kStageMoments || STAGE == kStageFit) {
+    // several warps per stamp: the three launches of the whole chain
+    if constexpr (STAGE == kStageMoments || STAGE == kStageFit || STAGE == kStageStartup) {
         switch (nw) {
             case 1: return launch_t<STAGE, DT, IVAR, 1>(a, stream);
             case 2: return launch_t<STAGE, DT, IVAR, 2>(a, stream);
@@ -1975,15 +2121,48 @@ cudaError_t launch_nw(const LaunchArgs& a, cudaStream_t stream) {
 
 template <int STAGE>
 cudaError_t launch_stage(const LaunchArgs& a, cudaStream_t stream) {
-    const bool iv = a.inv_var != nullptr;
-    if (a.dtype == FSE_BF16)
-        return iv ? launch_nw<STAGE, FSE_BF16, true>(a, stream) : launch_nw<STAGE, FSE_BF16, false>(a, stream);
-    return iv ? launch_nw<STAGE, FSE_F32, true>(a, stream) : launch_nw<STAGE, FSE_F32, false>(a, stream);
+    if constexpr (moment_stage(STAGE)) {
+        // the moment stages and the start-up do not read the inverse variance
+        if (a.dtype == FSE_BF16) return launch_nw<STAGE, FSE_BF16, false>(a, stream);
+        return launch_nw<STAGE, FSE_F32, false>(a, stream);
+    } else {
+        const bool iv = a.inv_var != nullptr;
+        if (a.dtype == FSE_BF16)
+            return iv ? launch_nw<STAGE, FSE_BF16, true>(a, stream) : launch_nw<STAGE, FSE_BF16, false>(a, stream);
+        return iv ? launch_nw<STAGE, FSE_F32, true>(a, stream) : launch_nw<STAGE, FSE_F32, false>(a, stream);
+    }
 }
 
 }  // namespace
 
 // ------------------------------------------------------------------ host wrappers
+unsigned long long current_context_id() {
+    // the driver's cuCtxGetCurrent and cuCtxGetId, looked up through the
+    // runtime (no link dependency on the driver library)
+    using GetCurrent = int (*)(void**);
+    using GetId = int (*)(void*, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(p);
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) return 0;
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
+
 size_t smem_per_group(int max_pix, bool ivar, int warps_per_stamp) {
     return group_bytes(max_pix, ivar, warps_per_stamp);
 }
@@ -2020,20 +2199,37 @@ cudaError_t eval_bn(const double* n, double* b, double* db, int64_t count, cudaS
     return cudaGetLastError();
 }
 
+// The start-up launch before a moment launch on the same stream; the work
+// counter is cleared between the two.
+static cudaError_t launch_startup(const LaunchArgs& a, cudaStream_t stream) {
+    LaunchArgs u = a;
+    u.stage = kStageStartup;
+    cudaError_t e = launch_stage<kStageStartup>(u, stream);
+    if (e != cudaSuccess || a.static_assign) return e;
+    return cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), stream);
+}
+
 cudaError_t launch_estimator(const LaunchArgs& a, cudaStream_t stream) {
     switch (a.stage) {
-        case kStageCentroid: return launch_stage<kStageCentroid>(a, stream);
+        case kStageCentroid: {
+            cudaError_t e = launch_startup(a, stream);
+            if (e != cudaSuccess) return e;
+            return launch_stage<kStageCentroid>(a, stream);
+        }
         case kStageEllipticity: return launch_stage<kStageEllipticity>(a, stream);
         case kStageFit: return launch_stage<kStageFit>(a, stream);
         default: {
-            // The whole chain as two persistent launches on the same stream: the
-            // moment stage, then the fit of the stamps whose moments converged.
-            // Each kernel holds only its own phase's code and registers, which
-            // measured 10.6 ms against 12.9 ms for one fused kernel (100,000
-            // stamps of 48x48); the pixels are read from HBM once more.
+            // The whole chain as three persistent launches on the same stream:
+            // the start-up, the moment iteration, then the fit of the stamps
+            // whose moments converged.  Each kernel holds only its own phase's
+            // code (instruction fetch stalls grow with a kernel's code), its
+            // registers and its tile; the pixels are read from HBM once per
+            // launch.
+            cudaError_t e = launch_startup(a, stream);
+            if (e != cudaSuccess) return e;
             LaunchArgs m = a;
             m.stage = kStageMoments;
-            cudaError_t e = launch_stage<kStageMoments>(m, stream);
+            e = launch_stage<kStageMoments>(m, stream);
             if (e != cudaSuccess) return e;
             if (!a.static_assign) {
                 e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), stream);
