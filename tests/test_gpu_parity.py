@@ -43,10 +43,14 @@ def gpu_run(ctx, batch, fn="fit_batch", inout=None, **kw):
     return B.results(out)
 
 
-def assert_gate(rep, min_gated=0.85):
-    assert rep["gated"] >= min_gated * rep["n"], {k: v for k, v in rep.items() if not k.startswith("_")}
-    assert rep["within_tolerance"] == rep["gated"], (
-        rep["failing"], rep["max_err"], {k: v for k, v in rep.items() if k in ("n", "gated")})
+def assert_gate(rep, max_gpu_short_frac=0.01, max_subpixel_frac=0.01):
+    """The parity gate of tests/parity.py: every gated stamp within tolerance,
+    every exclusion and status disagreement confirmed by the oracle, at most
+    max_gpu_short_frac of the stamps (rounded up) that the oracle converged
+    and the GPU did not, and at most max_subpixel_frac of them disagreeing at
+    the sub-pixel weight clamp, each listed with its reason."""
+    PR.assert_gate(rep, max_gpu_short=int(np.ceil(max_gpu_short_frac * rep["n"])),
+                   max_subpixel=int(np.ceil(max_subpixel_frac * rep["n"])))
 
 
 def test_bn_table(ctx, O):
@@ -76,9 +80,10 @@ def test_stage_centroid(ctx, O):
     batch = synth.make_workload(0)
     g = gpu_run(ctx, batch, "centroid")
     o = PR.oracle_results(O, batch, np.arange(batch.count), stage="centroid")
-    rep = PR.compare(g, o, keys=("x0", "y0"), fit=False)
+    rep = PR.compare(g, o, keys=("x0", "y0"), fit=False, O=O, batch=batch, ids=np.arange(batch.count),
+                     ellip=False)
     PR.dump("stage_centroid", rep)
-    assert_gate(rep, 0.95)
+    assert_gate(rep)
     both = ((g["status"] & 1) & (o["status"] & 1)).astype(bool)
     assert np.max(np.abs(g["r50"][both] / o["r50"][both] - 1)) <= 1e-6
     assert np.max(np.abs(g["sigma_w"][both] / o["sigma_w"][both] - 1)) <= 1e-6
@@ -91,9 +96,9 @@ def test_stage_ellipticity(ctx, O):
     ge = gpu_run(ctx, batch, "ellipticity", inout=gc.copy())
     oc = PR.oracle_results(O, batch, ids, stage="centroid")
     oe = PR.oracle_results(O, batch, ids, stage="ellipticity", init=oc)
-    rep = PR.compare(ge, oe, keys=("x0", "y0", "e1", "e2"), fit=False)
+    rep = PR.compare(ge, oe, keys=("x0", "y0", "e1", "e2"), fit=False, O=O, batch=batch, ids=ids)
     PR.dump("stage_ellipticity", rep)
-    assert_gate(rep, 0.9)
+    assert_gate(rep)
 
 
 def test_stage_fit_isolated(ctx, O):
@@ -145,7 +150,7 @@ def test_ragged_unaligned(ctx, O):
     o = PR.oracle_results(O, batch, ids)
     rep = PR.compare(g[ids], o, O=O, batch=batch, ids=ids)
     PR.dump("ragged", rep)
-    assert_gate(rep, 0.8)
+    assert_gate(rep)
 
 
 def test_bf16_pixels(ctx, O):
@@ -155,7 +160,7 @@ def test_bf16_pixels(ctx, O):
     o = PR.oracle_results(O, batch, ids)
     rep = PR.compare(g, o, O=O, batch=batch, ids=ids)
     PR.dump("bf16", rep)
-    assert_gate(rep, 0.8)
+    assert_gate(rep)
 
 
 def test_inverse_variance(ctx, O):
@@ -261,8 +266,9 @@ def test_fixed_gain_reaches_the_same_fixed_point(ctx, O):
     o = PR.oracle_results(O, batch, ids)
     g75 = gpu_run(ctx, batch, opts=opts_for(batch, k_gain=0.75))
     g0 = gpu_run(ctx, batch)
-    for g in (g75, g0):
+    for name, g in (("k075", g75), ("k_newton", g0)):
         rep = PR.compare(g, o, O=O, batch=batch, ids=ids)
+        PR.dump(f"gain_{name}", rep)
         assert_gate(rep)
     both = ((g75["status"] & 1) & (g0["status"] & 1)).astype(bool)
     assert g0["it_mom"][both].mean() < g75["it_mom"][both].mean()
@@ -296,3 +302,59 @@ def test_side_limit(ctx, O):
         assert abs(g["r50"][j] / o["r50"][j] - 1) <= 1e-6, (h, w, g["r50"][j], o["r50"][j])
         assert (g["status"][j] & 1) and (o["status"][j] & 1), (h, w)
         assert abs(g["x0"][j] - o["x0"][j]) <= 1e-4 and abs(g["y0"][j] - o["y0"][j]) <= 1e-4, (h, w)
+
+
+@pytest.mark.parametrize("case", ["small-32px", "uniform-48px"])
+def test_matched_weight_chain(ctx, O, case):
+    """The whole chain with the matched-weight rule sigma_w^2 = sum I W R^2 /
+    sum I W (the weight-size iteration of Sec. 4.2.1 applied to the weight of
+    Secs. 2-3; fse_opts.sigw_mode = 0) on both sides: 256 stamps of 32x32 and
+    400 stamps sampled from the 48x48 workload."""
+    if case == "small-32px":
+        batch = synth.make_workload(0)
+    else:
+        ids = np.sort(np.random.default_rng(21).choice(100_000, 400, replace=False))
+        batch = synth.make_workload(1, ids=ids)
+    g = gpu_run(ctx, batch, opts=opts_for(batch, sigw_mode=0))
+    ids = np.arange(batch.count)
+    oo = O.default_opts(sigw_mode=0)
+    o = PR.oracle_results(O, batch, ids, opts=oo)
+    rep = PR.compare(g, o, O=O, batch=batch, ids=ids, sigw_mode=0, orc_opts=oo)
+    PR.dump(f"matched_{case}", rep)
+    # cuspy galaxies drive the matched weight to its 0.5 px clamp, below the
+    # pixel scale, where the iteration has several fixed points: measured 12 of
+    # 256 and 15 of 400 stamps whose convergence differs there
+    assert_gate(rep, max_subpixel_frac=0.08)
+    # the weight size is the matched one on both sides, where it is not clamped
+    # (57 % of the small workload's stamps; the cuspier rest reach the 0.5 px clamp)
+    both = (((g["status"] & 1) & (o["status"] & 1)) != 0) & ((g["status"] & B.ST["SIGW_CLAMPED"]) == 0)
+    assert both.mean() > 0.5
+    assert np.max(np.abs(g["sigma_w"][both] / o["sigma_w"][both] - 1)) <= 1e-5
+
+
+def test_growth_curve_far_from_the_brightest_pixel(ctx, O):
+    """The start-up's growth curve (Sec. 4.1) when the brightest pixel is far
+    from the stamp's centre, in every quadrant: a bright spike on a broad
+    galaxy, so that half the light is enclosed only at rings reaching towards
+    the far corners.  r50 and the start (the brightest pixel) agree with the
+    oracle whichever corner the spike is nearest."""
+    rng = np.random.default_rng(31)
+    spikes = [(40, 40), (5, 44), (44, 3), (46, 46), (1, 1), (24, 46), (46, 24), (3, 3), (30, 2)]
+    stamps = []
+    for (sy, sx) in spikes:
+        img = synth.single_stamp(48, 48, n=1.0, re=9.0, g1=0.1, g2=-0.05, xc=23.6, yc=24.3, I0=40.0,
+                                 noise_sigma=1.0, seed=int(rng.integers(1 << 30)))
+        img[sy, sx] += 500.0
+        stamps.append(img)
+    pix = np.concatenate([s_.astype(np.float32).ravel() for s_ in stamps])
+    n = len(stamps)
+    offs = np.arange(n) * 48 * 48
+    idx = B.make_index(offs, [48] * n, [48] * n)
+    g = B.results(ctx.centroid(torch.as_tensor(pix).cuda(), idx, opts=B.default_opts(max_pix=48 * 48)))
+    o, _ = O.batch(pix, offs, np.full(n, 48), np.full(n, 48), stage="centroid")
+    for j, (sy, sx) in enumerate(spikes):
+        assert np.isfinite(o["r50"][j]) and o["r50"][j] > 5.0, (sy, sx, o["r50"][j])
+        assert abs(g["r50"][j] / o["r50"][j] - 1) <= 1e-6, (sy, sx, g["r50"][j], o["r50"][j])
+        start_bits = B.ST["NONFINITE"] | B.ST["BAD_SIZE"] | B.ST["INIT_FALLBACK"] | B.ST["SIGW_CLAMPED"]
+        assert (int(g["status"][j]) ^ int(o["status"][j])) & start_bits == 0, (sy, sx, g["status"][j], o["status"][j])
+        assert (g["x0"][j], g["y0"][j]) == (sx, sy) or g["status"][j] & 1

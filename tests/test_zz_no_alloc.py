@@ -6,21 +6,10 @@ import numpy as np
 import pytest
 import torch
 
-import parity as PR
 from paper_1203_0571_gb300 import binding as B
 from paper_1203_0571_gb300 import synth
 
 pytestmark = pytest.mark.gpu
-
-
-def within_tolerance(g, r):
-    assert np.array_equal(g["status"], r["status"])
-    for k, tol in PR.TOL.items():
-        a, b = g[k].astype(np.float64), r[k].astype(np.float64)
-        same = (a == b) | (np.isnan(a) & np.isnan(b))     # includes equal infinities
-        with np.errstate(invalid="ignore"):
-            err = np.abs(a - b) if k in PR.ABS else np.abs(a - b) / np.maximum(np.abs(b), 1e-300)
-        assert np.all(same | (err <= tol)), (k, float(np.nanmax(np.where(same, 0.0, err))))
 
 
 def test_static_entry_matches_fit_batch():
@@ -39,6 +28,9 @@ def test_static_entry_matches_fit_batch():
     second = B.results(out)
     ref = B.results(B.Context(0).fit_batch(batch.pix, idx, opts=opts))
     assert ((ref["status"] & 3) == 3).mean() > 0.9
-    within_tolerance(first, ref)
-    within_tolerance(second, ref)
+    # the same two kernels with the same arguments: the results are identical,
+    # byte for byte, on both calls (a scratch word left non-zero by the first
+    # call would make the second skip or repeat stamps)
+    assert first.tobytes() == ref.tobytes()
+    assert second.tobytes() == ref.tobytes()
 
