@@ -488,10 +488,13 @@ struct OffsetWalk {
 };
 
 // One weighted pass: S0 = sum f W, S1 = sum f W theta, the three second and
-// five fourth moments of f W (f = pixel value).  Everything the centroid step
-// (Eqs. 5-6) and the ellipticity step (Eqs. 8-9 with A5-A6, B7-B14) needs is a
-// linear combination of these eleven sums.
-template <int NW>
+// (FOURTH) five fourth moments of f W (f = pixel value).  Everything the
+// centroid step (Eqs. 5-6) and the ellipticity step (Eqs. 8-9 with A5-A6,
+// B7-B14) needs is a linear combination of these eleven sums.  The fourth
+// moments only shape the step of Eq. 9 (through P^SH) and the matched weight's
+// derivative, not the fixed point; a pass without them leaves acc[6..10] as
+// they were (the last pass that summed them).
+template <int NW, bool FOURTH>
 __device__ __forceinline__ void moment_pass(const float* __restrict__ s, int w, int npix,
                                             const Grp<NW>& g, const MomState& st,
                                             float (&acc)[11]) {
@@ -500,8 +503,9 @@ __device__ __forceinline__ void moment_pass(const float* __restrict__ s, int w, 
     const float B = 1.f + gg + 2.f * st.g1;
     const float G4 = 4.f * st.g2;
     const float cw = -kLog2e / (2.f * st.sw * st.sw);
+    constexpr int N = FOURTH ? 11 : 6;
 #pragma unroll
-    for (int i = 0; i < 11; ++i) acc[i] = 0.f;
+    for (int i = 0; i < N; ++i) acc[i] = 0.f;
     // centre relative to the reference pixel; rounding it to fp32 here costs
     // at most 2.4e-7 px, below the noise of these sums (the refinement passes
     // use exact offsets)
@@ -523,14 +527,25 @@ __device__ __forceinline__ void moment_pass(const float* __restrict__ s, int w, 
         acc[3] = fmaf(f, t11, acc[3]);
         acc[4] = fmaf(f, t12, acc[4]);
         acc[5] = fmaf(f, t22, acc[5]);
-        const float f11 = f * t11, f22 = f * t22;
-        acc[6] = fmaf(f11, t11, acc[6]);    // theta1^4
-        acc[7] = fmaf(f11, t12, acc[7]);    // theta1^3 theta2
-        acc[8] = fmaf(f11, t22, acc[8]);    // theta1^2 theta2^2
-        acc[9] = fmaf(f22, t12, acc[9]);    // theta1 theta2^3
-        acc[10] = fmaf(f22, t22, acc[10]);  // theta2^4
+        if constexpr (FOURTH) {
+            const float f11 = f * t11, f22 = f * t22;
+            acc[6] = fmaf(f11, t11, acc[6]);    // theta1^4
+            acc[7] = fmaf(f11, t12, acc[7]);    // theta1^3 theta2
+            acc[8] = fmaf(f11, t22, acc[8]);    // theta1^2 theta2^2
+            acc[9] = fmaf(f22, t12, acc[9]);    // theta1 theta2^3
+            acc[10] = fmaf(f22, t22, acc[10]);  // theta2^4
+        }
     }
-    g.allsum(acc);
+    if constexpr (FOURTH) {
+        g.allsum(acc);
+    } else {
+        float a6[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) a6[i] = acc[i];
+        g.allsum(a6);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) acc[i] = a6[i];
+    }
 }
 
 struct MomStep {
@@ -843,9 +858,15 @@ __device__ int moment_iterate(const float* s, int h, int w, int npix, const Grp<
     // switches the rest of the iteration to the fixed gain
     float k_use = o.k_gain, prev_c = 0.f;
     int it;
+    float m[11];
+    // the fourth moments are summed while the ellipticity (or the matched
+    // weight size) still moves by more than 1e-3; later passes reuse them
+    bool fourth = true;
     for (it = 1; it <= o.max_iter_mom; ++it) {
-        float m[11];
-        moment_pass(s, w, npix, g, st, m);
+        if (fourth)
+            moment_pass<NW, true>(s, w, npix, g, st, m);
+        else
+            moment_pass<NW, false>(s, w, npix, g, st, m);
 #pragma unroll
         for (int i = 0; i < 5; ++i) F4[i] = m[6 + i];
         const MomStep d = moment_step(m, st, k_use, ellip);
@@ -882,6 +903,8 @@ __device__ int moment_iterate(const float* s, int h, int w, int npix, const Grp<
             st.g1 = n1;
             st.g2 = n2;
         }
+        fourth = it < 3 || fmaxf(fabsf(d.dg1), fabsf(d.dg2)) > 1e-3f ||
+                 (o.sigw_mode == 0 && fabsf(d.sw_new - st.sw) > 1e-3f * st.sw);
         float dsig = 0.f;
         if (o.sigw_mode == 0) {
             float ns = d.sw_new;
@@ -1332,8 +1355,8 @@ __device__ void fit_start(const float* __restrict__ s, const float* __restrict__
 
 // Refinement at the LM optimum: a pass with both exponentials to
 // about one ulp (exp2_acc), the residual sums sum E r, sum v r, sum v a r and
-// sum r^2 accumulated in double-float, then one Gauss-Newton step of the
-// reduced problem and chi^2 from its quadratic model.  The fp32 LM stops
+// sum r^2 accumulated in double-float (the J^T J sums in fp32), then one Newton
+// step of the reduced problem and chi^2 from its quadratic model.  The fp32 LM stops
 // within the noise of its own sums; this pass removes most of that noise.
 // A precise evaluation of the profiled problem at (r_e, n): chi^2 at I0*, the
 // Newton step for (r_e, n) (Gauss-Newton where the full Hessian is not
@@ -1535,12 +1558,12 @@ __device__ Precise fit_refine(const float* __restrict__ s, const float* __restri
                 m2 *= q;
                 m3 *= q;
             }
-            df_add(rh[0], rl[0], E * E);
-            df_add(rh[1], rl[1], E * v);
-            df_add(rh[2], rl[2], E * va);
-            df_add(rh[3], rl[3], v * v);
-            df_add(rh[4], rl[4], v * va);
-            df_add(rh[5], rl[5], va * va);
+            rh[0] = fmaf(E, E, rh[0]);
+            rh[1] = fmaf(E, v, rh[1]);
+            rh[2] = fmaf(E, va, rh[2]);
+            rh[3] = fmaf(v, v, rh[3]);
+            rh[4] = fmaf(v, va, rh[4]);
+            rh[5] = fmaf(va, va, rh[5]);
             df_add(rh[6], rl[6], E * r);
             df_add(rh[7], rl[7], v * r);
             df_add(rh[8], rl[8], va * r);
@@ -1581,12 +1604,15 @@ __device__ Precise fit_refine(const float* __restrict__ s, const float* __restri
         }
         const float v = E * u, va = v * a;
         const float vr = v * r, var = va * r;
-        df_add(rh[0], rl[0], E * E);
-        df_add(rh[1], rl[1], E * v);
-        df_add(rh[2], rl[2], E * va);
-        df_add(rh[3], rl[3], v * v);
-        df_add(rh[4], rl[4], v * va);
-        df_add(rh[5], rl[5], va * va);
+        // J^T J (the first six sums) only shapes the Newton step: fp32.  The
+        // gradient sums and chi^2, which cancel or must hold 1e-7 at the
+        // optimum, are double-float.
+        rh[0] = fmaf(E, E, rh[0]);
+        rh[1] = fmaf(E, v, rh[1]);
+        rh[2] = fmaf(E, va, rh[2]);
+        rh[3] = fmaf(v, v, rh[3]);
+        rh[4] = fmaf(v, va, rh[4]);
+        rh[5] = fmaf(va, va, rh[5]);
         df_add(rh[6], rl[6], E * r);
         df_add(rh[7], rl[7], vr);
         df_add(rh[8], rl[8], var);
