@@ -37,11 +37,20 @@ WORKLOAD = 1
 # Algorithmic fp32 lane-operations per pixel (FMA = 1, MUFU ex2/lg2 = 1) of each
 # pass of the method as formulated here; see the design notes for the derivation.
 OPS_INIT = 12          # brightest pixel, total, growth-curve ring histogram
-OPS_MOMENT = 24        # one weighted pass (11 moments, 1 ex2)
-OPS_MOM_REFINE = 88    # one moment refinement pass (exact offsets, ~1-ulp exp2, double-float sums)
+OPS_MOMENT = 24        # one weighted pass with the fourth moments (11 sums, 1 ex2)
+OPS_MOMENT_2 = 17      # one weighted pass without them (6 sums), counted from the third pass on
+OPS_MOM_REFINE = 110   # one moment refinement pass (exact offsets, float-pair weight exponent,
+                       # ~1-ulp exp2, double-float sums with the products' rounding kept)
 OPS_FIT_SETUP = 8 + 26  # 0.5 log2 R^2 per pixel + the four-candidate start pass (8 ex2)
 OPS_FIT = 18           # one profile pass (10 sums, 2 ex2)
-OPS_REFINE = 76        # one fit refinement pass (two ~1-ulp exp2, double-float and curvature sums)
+OPS_REFINE = 61        # one fit refinement pass (two ~1-ulp exp2, double-float gradient and chi^2
+                       # sums, fp32 J^T J and curvature sums)
+# The per-pass figures of the survey's roofline: a moment pass 1 ex2 + ~30 fp32
+# operations, a fit pass 3 MUFU + ~30; every pixel pass the kernels run counts
+# once at these rates (the start-up and the refinement passes included, the
+# four-candidate fit start as one fit pass).
+SURVEY_MOMENT = 31
+SURVEY_FIT = 33
 SMS = 152
 LANES_PER_SM = 128
 
@@ -60,17 +69,36 @@ def config_dict(n, world):
     }
 
 
-def algorithmic_ops(res) -> float:
+def pass_counts(res):
+    """Pixel passes each stamp ran, by kind: start-up, moment iterations (the
+    first two with fourth moments), moment refinements, fit start, fit
+    iterations, fit refinements.  A refinement runs once, and a second time
+    where the status bit says so (more than two are not counted: errs low)."""
     st = res["status"]
-    npix = res["npix"].astype(np.float64)
     ok = (st & (32 | 16)) == 0
     fit = ((st & 1) != 0) & ok
-    ops = npix * (OPS_INIT + OPS_MOMENT * res["it_mom"]) * ok
-    # one refinement pass of each kind, and a second where the status says it ran
-    ops += npix * OPS_MOM_REFINE * (1 + ((st & (1 << 13)) != 0)) * fit
-    ops += npix * (OPS_FIT_SETUP + OPS_FIT * res["it_fit"]) * fit
-    ops += npix * OPS_REFINE * (1 + ((st & (1 << 14)) != 0)) * (((st & 2) != 0) & ((st & 128) == 0) & fit)
-    return float(ops.sum())
+    it = res["it_mom"].astype(np.float64) * ok
+    return {"init": ok.astype(np.float64), "mom4": np.minimum(it, 2.0), "mom": np.maximum(it - 2.0, 0.0),
+            "mom_refine": (1.0 + ((st & (1 << 13)) != 0)) * fit, "fit_start": fit.astype(np.float64),
+            "fit": res["it_fit"].astype(np.float64) * fit,
+            "fit_refine": (1.0 + ((st & (1 << 14)) != 0)) * (((st & 2) != 0) & ((st & 128) == 0) & fit)}
+
+
+def algorithmic_ops(res) -> float:
+    """The builder's count: each pass at the operations it performs per pixel."""
+    c = pass_counts(res)
+    per_px = (OPS_INIT * c["init"] + OPS_MOMENT * c["mom4"] + OPS_MOMENT_2 * c["mom"] +
+              OPS_MOM_REFINE * c["mom_refine"] + OPS_FIT_SETUP * c["fit_start"] + OPS_FIT * c["fit"] +
+              OPS_REFINE * c["fit_refine"])
+    return float((res["npix"].astype(np.float64) * per_px).sum())
+
+
+def survey_ops(res) -> float:
+    """The survey's count: every pass at 31 (moment kind) or 33 (fit kind) per pixel."""
+    c = pass_counts(res)
+    per_px = (SURVEY_MOMENT * (c["init"] + c["mom4"] + c["mom"] + c["mom_refine"]) +
+              SURVEY_FIT * (c["fit_start"] + c["fit"] + c["fit_refine"]))
+    return float((res["npix"].astype(np.float64) * per_px).sum())
 
 
 class ClockSampler:
@@ -163,25 +191,112 @@ def whole_job_rate(world: int, units_per_rank: int, slowest_s: float) -> float:
     return world * units_per_rank / slowest_s
 
 
-def cpu_oracle_rate(batch, target_s: float, max_stamps: int):
-    """The FP64 oracle on the host cores over a bounded sample of the workload."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_rate(which: int, target_s: float, max_stamps: int, threads: int = 0, first: int = 0):
+    """The FP64 oracle over a bounded sample of workload `which` (stamps
+    first, first+1, ...), sized from a pilot run to about target_s seconds."""
     import oracle as O
     from paper_1203_0571_gb300 import synth
     O.build()
-    pilot = 256
-    sub = synth.make_workload(WORKLOAD, count=pilot)
+    # the thread count is set on every call: OpenMP keeps the last one set
+    threads = threads if threads > 0 else (os.cpu_count() or 1)
+    pilot = 64 if threads == 1 else 256
+    sub = synth.make_workload(which, count=pilot, first=first)
     t = time.perf_counter()
-    O.batch(sub.pix.numpy(), sub.offset.numpy(), sub.h.numpy(), sub.w.numpy())
+    O.batch(sub.pix.numpy(), sub.offset.numpy(), sub.h.numpy(), sub.w.numpy(), threads=threads)
     dt = max(time.perf_counter() - t, 1e-3)
     count = int(min(max_stamps, max(pilot, pilot * target_s / dt)))
-    sub = synth.make_workload(WORKLOAD, count=count)
+    sub = synth.make_workload(which, count=count, first=first)
     t = time.perf_counter()
-    res, used = O.batch(sub.pix.numpy(), sub.offset.numpy(), sub.h.numpy(), sub.w.numpy())
+    res, used = O.batch(sub.pix.numpy(), sub.offset.numpy(), sub.h.numpy(), sub.w.numpy(), threads=threads)
     dt = time.perf_counter() - t
-    return {"value": count / dt, "unit": UNIT, "cores": used, "kind": "oracle",
+    return count, dt, used, res
+
+
+def cpu_oracle_rate(target_s: float, max_stamps: int):
+    """The FP64 oracle on the host cores over a bounded sample of the workload,
+    on all cores and on one (the paper timed one core of a 2.2 GHz CPU)."""
+    count, dt, used, res = oracle_rate(WORKLOAD, target_s, max_stamps)
+    c1, dt1, _, _ = oracle_rate(WORKLOAD, target_s / 3, max_stamps, threads=1)
+    return {"value": count / dt, "unit": UNIT, "cores": used, "kind": "oracle", "cpu": cpu_model(),
             "sample": f"first {count} stamps of the 100,000-stamp uniform-48px workload, "
                       f"whole chain, FP64, {used} threads, {dt:.2f} s wall",
+            "single_core": {"value": c1 / dt1, "unit": UNIT, "cores": 1,
+                            "sample": f"first {c1} stamps, 1 thread, {dt1:.2f} s wall"},
             "it_mom_mean": float(np.mean(res["it_mom"])), "it_fit_mean": float(np.mean(res["it_fit"]))}
+
+
+def run_oracle_rates(args):
+    """Per-stamp oracle rates on seeded 10,000-stamp samples of the ragged,
+    gradient and precision workloads (and the benchmark's), on all host cores
+    and on one, bounded in time per sample; one JSON line."""
+    from paper_1203_0571_gb300 import synth
+    out = {"cpu": cpu_model(), "cores": os.cpu_count(), "kind": "oracle", "rates": {}}
+    for which in (1, 2, 3, 4, 5):
+        name = synth.WORKLOADS[which].name
+        n, dt, used, res = oracle_rate(which, 3 * args.cpu_seconds, 10_000)
+        n1, dt1, _, _ = oracle_rate(which, args.cpu_seconds / 4, 10_000, threads=1)
+        conv = ((res["status"] & 3) == 3).mean()
+        out["rates"][name] = {"stamps": n, "threads": used, "stamps_per_s": n / dt, "s_per_stamp_1core": dt1 / n1,
+                              "stamps_1core": n1, "converged_frac": float(conv),
+                              "mean_px": float(res["npix"].mean())}
+        print(json.dumps({name: out["rates"][name]}), file=sys.stderr, flush=True)
+    print(json.dumps(out), flush=True)
+
+
+def ragged_rate(ctx, B, synth, local, calls: int = 3):
+    """The ragged workload (1,000,000 stamps, sides clip(round(8 r_e), 16, 128))
+    through fse_fit_batch_ragged: size-class launches with autotuned shapes,
+    captured once into a CUDA graph and replayed; CUDA events on the stream."""
+    dev = f"cuda:{local}"
+    rb = synth.make_workload(2, device=dev)
+    ridx = B.make_index(rb.offset, rb.h, rb.w, device=dev)
+    rout = torch.empty((rb.count, 64), dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    ctx.autotune(rb.pix, ridx, out=rout)
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t
+    gopts = B.default_opts(flags=B.FSE_FLAG_GRAPH)
+    stream = torch.cuda.current_stream()
+    ctx.fit_batch_ragged(rb.pix, ridx, out=rout, opts=gopts, stream=stream)   # captures the graph
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(calls):
+        ctx.fit_batch_ragged(rb.pix, ridx, out=rout, opts=gopts, stream=stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / calls
+    r = B.results(rout)
+    px = int(rb.pix.numel())
+    out = {"workload": "ragged-16-128px: 1,000,000 stamps, square side clip(round(8 r_e), 16, 128), "
+                       "r_e logU[1,15] px, other parameters as the 32x32 workload, fp32, seed 2",
+           "stamps": rb.count, "pixels": px, "value": rb.count / (ms / 1e3), "unit": "stamps/s",
+           "px_per_s": px / (ms / 1e3), "ms_per_call": ms, "calls": calls,
+           "launch": "seven size classes, three launches each, replayed as one CUDA graph, autotuned shapes",
+           "autotune_s": tune_s, "converged_frac": float(((r["status"] & 3) == 3).mean())}
+    del rb, ridx, rout
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args, rank, world):
@@ -225,7 +340,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
     ap.add_argument("--ref-stamps", type=int, default=2000)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ragged", action="store_true")
+    ap.add_argument("--oracle-rates", action="store_true",
+                    help="time the oracle on samples of the other workloads (host cores only) and exit")
     args = ap.parse_args()
+    if args.oracle_rates:
+        return run_oracle_rates(args)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
 
@@ -278,6 +398,7 @@ def main():
     ms = max_over_ranks(total_ms / args.steps, f"cuda:{local}")
     res = B.results(out)
     ops = algorithmic_ops(res)
+    sops = survey_ops(res)
     kernel_ms = statistics.mean(step_ms)
     peak_gops = SMS * LANES_PER_SM * 2070.0 * 1e6 / 1e9     # at the maximum SM clock
     achieved = ops / (kernel_ms / 1e3) / 1e9
@@ -311,12 +432,14 @@ def main():
     plain = {"value": pn / (pa.elapsed_time(pb) / 1e3), "unit": UNIT, "stamps": pn,
              "launches": 3 * pn, "identical_results": bool(torch.equal(pout, out[:pn]))}
 
+    ragged = None if args.no_ragged else ragged_rate(ctx, B, synth, local)
+
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
     cpu = None
     if world == 1 and not args.no_cpu:
-        cpu = cpu_oracle_rate(batch, args.cpu_seconds, 40000)
+        cpu = cpu_oracle_rate(args.cpu_seconds, 40000)
     conv = (res["status"] & 3) == 3
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -325,10 +448,14 @@ def main():
         "e2e": e2e,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
                      "frac": achieved / peak_gops, "traffic": kernel_traffic(),
-                     "kernel": "estimator_kernel<moments> + estimator_kernel<fit> (the two launches of "
+                     "frac_survey": sops / (kernel_ms / 1e3) / 1e9 / peak_gops,
+                     "ops_per_call_survey": sops,
+                     "kernel": "estimator_kernel<startup> + <moments> + <fit> (the three launches of "
                                "one fse_fit_batch, f32)", "kernel_ms": kernel_ms,
                      "ops_per_launch": ops,
+                     "passes_per_stamp": {k: float(v.mean()) for k, v in pass_counts(res).items()},
                      "peak_source": "152 SMs x 128 fp32 lanes x 2070 MHz (issue slots, FMA = 1 op)"},
+        "ragged": ragged,
         "cpu_baseline": cpu,
         "plain_per_stamp_launch": plain,
         "gpu_launches": 3 * args.steps,

@@ -278,6 +278,22 @@ int fse_autotune(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
                  const fse_stamp *idx, int64_t count, const float *inv_var,
                  const fse_opts *opts, fse_result *out, void *stream);
 
+/* Keep the launch shapes fse_autotune chose for this context's device, so that
+ * a later process can reuse them instead of timing again (no counterpart in the
+ * paper).  fse_tuning_save writes every dtype and inverse-variance setting
+ * tuned so far to the JSON file `path` (written to path.tmp, then renamed), one
+ * entry per device name, dtype and setting, each with the size classes' pixel
+ * bounds, warps per CTA and warps per stamp; entries of other devices already
+ * in the file are kept.  fse_tuning_load applies the entries for this
+ * context's device name whose size classes match this library's and whose
+ * shapes are valid ones (1, 2, 4 or 8 warps, a multiple of the warps per
+ * stamp, within shared memory), as if fse_autotune had chosen them; a CUDA
+ * graph cached by fse_fit_batch_ragged is captured again.  Returns FSE_OK, or
+ * FSE_EINVAL (NULL argument, unreadable or unwritable file, no applicable
+ * entry: the context keeps its shapes).  Host calls; no device work. */
+int fse_tuning_save(const fse_ctx *ctx, const char *path);
+int fse_tuning_load(fse_ctx *ctx, const char *path);
+
 /* The launch shape the ragged path uses for each of the seven size classes
  * (tuned or default), for a dtype and with (1) or without (0) inverse
  * variance: warps per CTA and warps per stamp (host arrays of 7; the second

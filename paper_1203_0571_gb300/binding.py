@@ -22,6 +22,7 @@ from . import _build
 
 FSE_OK, FSE_EINVAL, FSE_ENOMEM, FSE_ECUDA, FSE_ETIMEOUT, FSE_EUNSUPPORTED = range(6)
 FSE_F32, FSE_BF16 = 0, 1
+FSE_FLAG_GRAPH = 1 << 0
 FSE_MAX_PIX = 128 * 128
 
 ST = dict(MOM_CONVERGED=1 << 0, FIT_CONVERGED=1 << 1, MOM_MAXITER=1 << 2, FIT_MAXITER=1 << 3,
@@ -32,9 +33,9 @@ ST = dict(MOM_CONVERGED=1 << 0, FIT_CONVERGED=1 << 1, MOM_MAXITER=1 << 2, FIT_MA
 # exported symbols, in the order include/fse.h declares them
 EXPORTS = ["fse_create", "fse_destroy", "fse_last_error", "fse_opts_default", "fse_centroid",
            "fse_ellipticity", "fse_sersic_fit", "fse_fit_batch", "fse_fit_batch_plain",
-           "fse_fit_batch_host", "fse_fit_batch_ragged", "fse_autotune", "fse_tuned_warps",
-           "fse_star_fit", "fse_moment_vjp", "fse_moment_jvp", "fse_cutout", "fse_sersic_b",
-           "fse_sersic_chi2_grad", "fse_sync_check", "fse_fit_batch_static"]
+           "fse_fit_batch_host", "fse_fit_batch_ragged", "fse_autotune", "fse_tuning_save",
+           "fse_tuning_load", "fse_tuned_warps", "fse_star_fit", "fse_moment_vjp", "fse_moment_jvp",
+           "fse_cutout", "fse_sersic_b", "fse_sersic_chi2_grad", "fse_sync_check", "fse_fit_batch_static"]
 CUTOUT_DTYPE = np.dtype([("row0", "<i4"), ("col0", "<i4"), ("h", "<i4"), ("w", "<i4"), ("r50", "<f4"),
                          ("status", "<u4")])
 FSE_MOM_ELLIP, FSE_MOM_SIGW_FIXED, FSE_MOM_SIGW_R50 = 1, 2, 4
@@ -121,6 +122,9 @@ def load(build: bool = True, path: str | None = None) -> ctypes.CDLL:
                                        ctypes.POINTER(Opts), _vp, _vp, ctypes.c_char_p,
                                        ctypes.c_size_t]
     L.fse_fit_batch_static.restype = ctypes.c_int
+    for f in ("fse_tuning_save", "fse_tuning_load"):
+        getattr(L, f).argtypes = [_vp, ctypes.c_char_p]
+        getattr(L, f).restype = ctypes.c_int
     _lib = L
     return L
 
@@ -288,6 +292,15 @@ class Context:
         n = (ctypes.c_int32 * 7)()
         self._check(load().fse_tuned_warps(self._h, dtype, int(inv_var), w, n))
         return list(zip(w, n))
+
+    def tuning_save(self, path: str) -> None:
+        """fse_tuning_save: write this context's autotuned launch shapes to a JSON file."""
+        self._check(load().fse_tuning_save(self._h, os.fsencode(path)))
+
+    def tuning_load(self, path: str) -> bool:
+        """fse_tuning_load: apply the saved launch shapes for this device; False
+        when the file holds none that apply (or cannot be read)."""
+        return load().fse_tuning_load(self._h, os.fsencode(path)) == FSE_OK
 
     def star_fit(self, pix, index, moments, *, profile: str = "gauss", scale=None, opts=None,
                  out=None, stream=None):

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "fse.h"
 #include "fse_internal.h"
@@ -788,6 +789,159 @@ int fse_tuned_warps(const fse_ctx* ctx, int dtype, int has_inv_var, int32_t* war
         warps_per_cta[k] = w;
         if (warps_per_stamp) warps_per_stamp[k] = n;
     }
+    return FSE_OK;
+}
+
+// ---- the launch-shape cache of fse_autotune (fse_tuning_save / _load)
+// One JSON object per line inside "entries", so that a saving process can keep
+// the lines of other devices without a full JSON parser:
+//   {"format": "libfse-launch-shapes/1", "entries": [
+//   {"device": "<name>", "dtype": "f32", "inv_var": 0, "class_pix": [...7],
+//    "warps_per_cta": [...7], "warps_per_stamp": [...7]},
+//   ...
+//   ]}
+static const char kTuneFormat[] = "libfse-launch-shapes/1";
+
+static bool device_name(int device, char* name, size_t len) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    snprintf(name, len, "%s", prop.name);
+    for (char* c = name; *c; ++c)
+        if (*c == '"' || *c == '\\' || static_cast<unsigned char>(*c) < 32) *c = '_';
+    return true;
+}
+
+// The integers of the JSON array after `"key": [` in line, at most n of them.
+static int json_ints(const char* line, const char* key, long* v, int n) {
+    char pat[64];
+    snprintf(pat, sizeof pat, "\"%s\": [", key);
+    const char* p = strstr(line, pat);
+    if (!p) return 0;
+    p += strlen(pat);
+    int k = 0;
+    while (k < n) {
+        char* end = nullptr;
+        const long x = strtol(p, &end, 10);
+        if (end == p) break;
+        v[k++] = x;
+        p = end;
+        while (*p == ' ' || *p == ',') ++p;
+        if (*p == ']') break;
+    }
+    return k;
+}
+
+static bool json_str(const char* line, const char* key, char* out, size_t len) {
+    char pat[64];
+    snprintf(pat, sizeof pat, "\"%s\": \"", key);
+    const char* p = strstr(line, pat);
+    if (!p) return false;
+    p += strlen(pat);
+    const char* q = strchr(p, '"');
+    if (!q || static_cast<size_t>(q - p) >= len) return false;
+    memcpy(out, p, q - p);
+    out[q - p] = 0;
+    return true;
+}
+
+int fse_tuning_save(const fse_ctx* ctx, const char* path) {
+    if (!ctx || !path) return FSE_EINVAL;
+    fse_ctx* c = const_cast<fse_ctx*>(ctx);
+    char name[256];
+    if (!device_name(ctx->device, name, sizeof name)) return set_error(c, FSE_ECUDA, "device properties");
+    // the entries of other devices already in the file are kept
+    std::vector<std::string> keep;
+    if (FILE* f = fopen(path, "r")) {
+        char line[4096];
+        while (fgets(line, sizeof line, f)) {
+            char dev[256];
+            if (strncmp(line, "{\"device\": ", 11) != 0 || !json_str(line, "device", dev, sizeof dev)) continue;
+            if (strcmp(dev, name) == 0) continue;
+            std::string l(line);
+            while (!l.empty() && (l.back() == '\n' || l.back() == '\r' || l.back() == ',')) l.pop_back();
+            keep.push_back(l);
+        }
+        fclose(f);
+    }
+    for (int dt = 0; dt < 2; ++dt)
+        for (int iv = 0; iv < 2; ++iv) {
+            bool any = false;
+            for (int k = 0; k < kK; ++k) any = any || ctx->tuned[dt][iv][k] > 0;
+            if (!any) continue;
+            char buf[1024];
+            int n = snprintf(buf, sizeof buf, "{\"device\": \"%s\", \"dtype\": \"%s\", \"inv_var\": %d, \"class_pix\": [",
+                             name, dt ? "bf16" : "f32", iv);
+            for (int k = 0; k < kK; ++k) n += snprintf(buf + n, sizeof buf - n, "%s%d", k ? ", " : "", fse::kClassPix[k]);
+            n += snprintf(buf + n, sizeof buf - n, "], \"warps_per_cta\": [");
+            for (int k = 0; k < kK; ++k) n += snprintf(buf + n, sizeof buf - n, "%s%d", k ? ", " : "", ctx->tuned[dt][iv][k]);
+            n += snprintf(buf + n, sizeof buf - n, "], \"warps_per_stamp\": [");
+            for (int k = 0; k < kK; ++k) n += snprintf(buf + n, sizeof buf - n, "%s%d", k ? ", " : "", ctx->tuned_nw[dt][iv][k]);
+            snprintf(buf + n, sizeof buf - n, "]}");
+            keep.push_back(buf);
+        }
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "w");
+    if (!f) return set_error(c, FSE_EINVAL, "cannot write %s", tmp.c_str());
+    fprintf(f, "{\"format\": \"%s\", \"entries\": [\n", kTuneFormat);
+    for (size_t i = 0; i < keep.size(); ++i) fprintf(f, "%s%s\n", keep[i].c_str(), i + 1 < keep.size() ? "," : "");
+    fprintf(f, "]}\n");
+    const bool ok = fclose(f) == 0 && rename(tmp.c_str(), path) == 0;
+    if (!ok) return set_error(c, FSE_EINVAL, "cannot write %s", path);
+    return FSE_OK;
+}
+
+int fse_tuning_load(fse_ctx* ctx, const char* path) {
+    if (!ctx || !path) return FSE_EINVAL;
+    char name[256];
+    if (!device_name(ctx->device, name, sizeof name)) return set_error(ctx, FSE_ECUDA, "device properties");
+    FILE* f = fopen(path, "r");
+    if (!f) return set_error(ctx, FSE_EINVAL, "cannot read %s", path);
+    char line[4096];
+    bool format_ok = false;
+    int applied = 0;
+    while (fgets(line, sizeof line, f)) {
+        char fmt[64];
+        if (json_str(line, "format", fmt, sizeof fmt)) format_ok = strcmp(fmt, kTuneFormat) == 0;
+        char dev[256], dts[16];
+        if (!format_ok || strncmp(line, "{\"device\": ", 11) != 0 || !json_str(line, "device", dev, sizeof dev) ||
+            strcmp(dev, name) != 0 || !json_str(line, "dtype", dts, sizeof dts))
+            continue;
+        long ivv[1], pix[kK], w[kK], nw[kK];
+        if (json_ints(line, "inv_var", ivv, 1) != 1) {
+            const char* p = strstr(line, "\"inv_var\": ");
+            if (!p) continue;
+            ivv[0] = strtol(p + 11, nullptr, 10);
+        }
+        const int dt = strcmp(dts, "bf16") == 0 ? 1 : (strcmp(dts, "f32") == 0 ? 0 : -1);
+        const int iv = ivv[0] != 0;
+        if (dt < 0 || json_ints(line, "class_pix", pix, kK) != kK || json_ints(line, "warps_per_cta", w, kK) != kK ||
+            json_ints(line, "warps_per_stamp", nw, kK) != kK)
+            continue;
+        // the entry must be for this library's size classes, and every shape
+        // one that fse_autotune could have chosen (0 keeps the library default)
+        bool ok = true;
+        for (int k = 0; k < kK && ok; ++k) {
+            ok = pix[k] == fse::kClassPix[k];
+            if (!ok || w[k] == 0) continue;
+            const bool pow2 = (w[k] == 1 || w[k] == 2 || w[k] == 4 || w[k] == 8) &&
+                              (nw[k] == 1 || nw[k] == 2 || nw[k] == 4 || nw[k] == 8);
+            ok = pow2 && w[k] % nw[k] == 0 &&
+                 fse::smem_per_group(fse::kClassPix[k], iv != 0, static_cast<int>(nw[k])) * (w[k] / nw[k]) <=
+                     227 * 1024;
+        }
+        if (!ok) continue;
+        for (int k = 0; k < kK; ++k) {
+            ctx->tuned[dt][iv][k] = static_cast<int>(w[k]);
+            ctx->tuned_nw[dt][iv][k] = w[k] ? static_cast<int>(nw[k]) : 0;
+        }
+        ++applied;
+    }
+    fclose(f);
+    if (!applied) return set_error(ctx, FSE_EINVAL, "%s holds no launch shapes for %s", path, name);
+    ++ctx->tune_version;
     return FSE_OK;
 }
 

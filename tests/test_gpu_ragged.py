@@ -115,3 +115,46 @@ def test_ragged_with_invalid_sizes_and_bf16(ctx):
     out = ctx.fit_batch_ragged(bb.pix, ib, scale=bb.scale, opts=B.default_opts(flags=1, **ONE))
     torch.cuda.synchronize()
     assert torch.equal(out, ref)
+
+
+OTHER_DEVICE = ('{"device": "Some Other GPU", "dtype": "f32", "inv_var": 0, '
+                '"class_pix": [256, 576, 1024, 2304, 4096, 9216, 16384], '
+                '"warps_per_cta": [1, 1, 1, 1, 1, 1, 1], "warps_per_stamp": [1, 1, 1, 1, 1, 1, 1]}')
+
+
+def test_tuned_shapes_saved_and_reused_by_a_new_context(ragged, tmp_path):
+    """fse_tuning_save / fse_tuning_load: the shapes one context's autotuner
+    chose are reused by a new context (another process would do the same)
+    without timing again: the same shapes and byte-identical ragged results.
+    Entries of other devices in the file are kept; a file with none for this
+    device leaves the library's shapes."""
+    import json
+    cpu, b, idx = ragged
+    tuner = B.Context(0)
+    tuner.autotune(b.pix, idx)
+    shapes = tuner.tuned_warps()
+    path = tmp_path / "shapes.json"
+    path.write_text('{"format": "libfse-launch-shapes/1", "entries": [\n' + OTHER_DEVICE + '\n]}\n')
+    tuner.tuning_save(str(path))
+    saved = json.loads(path.read_text())
+    assert saved["format"] == "libfse-launch-shapes/1"
+    devices = [e["device"] for e in saved["entries"]]
+    assert "Some Other GPU" in devices and torch.cuda.get_device_name(0) in devices, devices
+    mine = [e for e in saved["entries"] if e["device"] == torch.cuda.get_device_name(0)]
+    assert [(c, n) for c, n in zip(mine[0]["warps_per_cta"], mine[0]["warps_per_stamp"])] == shapes
+
+    fresh = B.Context(0)
+    assert fresh.tuning_load(str(path))
+    assert fresh.tuned_warps() == shapes
+    r_tuner = tuner.fit_batch_ragged(b.pix, idx)
+    r_fresh = fresh.fit_batch_ragged(b.pix, idx)
+    torch.cuda.synchronize()
+    assert torch.equal(r_tuner, r_fresh)
+
+    other = tmp_path / "other.json"
+    other.write_text('{"format": "libfse-launch-shapes/1", "entries": [\n' + OTHER_DEVICE + '\n]}\n')
+    plain = B.Context(0)
+    defaults = plain.tuned_warps()
+    assert not plain.tuning_load(str(other))
+    assert not plain.tuning_load(str(tmp_path / "missing.json"))
+    assert plain.tuned_warps() == defaults
