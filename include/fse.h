@@ -404,6 +404,19 @@ int fse_sersic_chi2_grad(fse_ctx *ctx, const void *pix, int dtype, const float *
                          const float *params, const double *gout, double *chi2,
                          float *dparams, float *dpix, void *stream);
 
+/* Replicas over stamp ranges: the stamps are independent, so a batch spread
+ * over several devices (or processes) is cut into `parts` contiguous index
+ * ranges of about equal total pixels, each device runs fse_fit_batch on its
+ * range, and the results are concatenated in range order (no collective on
+ * the data path).  starts (host, parts + 1 entries) receives the boundaries:
+ * range r is idx[starts[r] .. starts[r+1]), starts[0] = 0, starts[parts] =
+ * count; range r starts at the first stamp at or past r/parts of the pixels,
+ * so a range holds at most one stamp's pixels more than an equal share.  A
+ * stamp of invalid size counts as one pixel.  idx is a HOST array.  Returns
+ * FSE_OK, or FSE_EINVAL (NULL pointer, parts < 1, count < 0).  No counterpart
+ * in the paper, which measured one galaxy at a time. */
+int fse_partition(const fse_stamp *idx, int64_t count, int32_t parts, int64_t *starts);
+
 /* Wait for `stream` and report a bounded device wait that expired during any
  * earlier call of this context (FSE_ETIMEOUT), or FSE_OK.  Clears the flag. */
 int fse_sync_check(fse_ctx *ctx, void *stream);

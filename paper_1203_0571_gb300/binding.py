@@ -35,7 +35,8 @@ EXPORTS = ["fse_create", "fse_destroy", "fse_last_error", "fse_opts_default", "f
            "fse_ellipticity", "fse_sersic_fit", "fse_fit_batch", "fse_fit_batch_plain",
            "fse_fit_batch_host", "fse_fit_batch_ragged", "fse_autotune", "fse_tuning_save",
            "fse_tuning_load", "fse_tuned_warps", "fse_star_fit", "fse_moment_vjp", "fse_moment_jvp",
-           "fse_cutout", "fse_sersic_b", "fse_sersic_chi2_grad", "fse_sync_check", "fse_fit_batch_static"]
+           "fse_cutout", "fse_sersic_b", "fse_sersic_chi2_grad", "fse_partition", "fse_sync_check",
+           "fse_fit_batch_static"]
 CUTOUT_DTYPE = np.dtype([("row0", "<i4"), ("col0", "<i4"), ("h", "<i4"), ("w", "<i4"), ("r50", "<f4"),
                          ("status", "<u4")])
 FSE_MOM_ELLIP, FSE_MOM_SIGW_FIXED, FSE_MOM_SIGW_R50 = 1, 2, 4
@@ -122,6 +123,8 @@ def load(build: bool = True, path: str | None = None) -> ctypes.CDLL:
                                        ctypes.POINTER(Opts), _vp, _vp, ctypes.c_char_p,
                                        ctypes.c_size_t]
     L.fse_fit_batch_static.restype = ctypes.c_int
+    L.fse_partition.argtypes = [_vp, ctypes.c_int64, ctypes.c_int32, _vp]
+    L.fse_partition.restype = ctypes.c_int
     for f in ("fse_tuning_save", "fse_tuning_load"):
         getattr(L, f).argtypes = [_vp, ctypes.c_char_p]
         getattr(L, f).restype = ctypes.c_int
@@ -134,6 +137,20 @@ def use_library(path: str) -> ctypes.CDLL:
     global _lib
     _lib = None
     return load(path=path)
+
+
+def partition(index, parts: int) -> np.ndarray:
+    """fse_partition: boundaries (parts + 1 int64) of contiguous index ranges of
+    about equal total pixels, for replicas over stamp ranges.  index is a host
+    array (make_index on the CPU, or a STAMP_DTYPE / int64 [N, 2] numpy array)."""
+    if isinstance(index, torch.Tensor):
+        index = index.detach().cpu().contiguous()
+    ip, n = _index(index, where="cpu")
+    starts = np.zeros(parts + 1, dtype=np.int64)
+    rc = load().fse_partition(ip, n, int(parts), _vp(starts.ctypes.data))
+    if rc != FSE_OK:
+        raise FseError(rc, f"fse_partition(count={n}, parts={parts})")
+    return starts
 
 
 def default_opts(**kw) -> Opts:

@@ -945,6 +945,32 @@ int fse_tuning_load(fse_ctx* ctx, const char* path) {
     return FSE_OK;
 }
 
+int fse_partition(const fse_stamp* idx, int64_t count, int32_t parts, int64_t* starts) {
+    if (!starts || parts < 1 || count < 0 || (count > 0 && !idx)) return FSE_EINVAL;
+    // prefix sums of the pixels; a stamp of invalid size weighs one pixel (the
+    // estimator only flags it)
+    double total = 0.0;
+    for (int64_t i = 0; i < count; ++i) {
+        const int64_t h = idx[i].h, w = idx[i].w;
+        total += (h >= 1 && w >= 1 && h <= FSE_MAX_SIDE && w <= FSE_MAX_SIDE) ? static_cast<double>(h * w) : 1.0;
+    }
+    starts[0] = 0;
+    double run = 0.0;
+    int64_t i = 0;
+    for (int32_t r = 1; r < parts; ++r) {
+        // the first stamp whose start lies at or past r/parts of the pixels
+        const double target = total * r / parts;
+        while (i < count && run < target) {
+            const int64_t h = idx[i].h, w = idx[i].w;
+            run += (h >= 1 && w >= 1 && h <= FSE_MAX_SIDE && w <= FSE_MAX_SIDE) ? static_cast<double>(h * w) : 1.0;
+            ++i;
+        }
+        starts[r] = i;
+    }
+    starts[parts] = count;
+    return FSE_OK;
+}
+
 int fse_star_fit(fse_ctx* ctx, const void* pix, int dtype, const float* scale, const fse_stamp* idx,
                  int64_t count, const fse_result* moments, int profile, const fse_opts* opts,
                  fse_star_result* out, void* stream) {
