@@ -8,7 +8,10 @@ restated with numpy and checked exhaustively on the CPU:
 - the three 32-bit pieces of each 64-bit fixed-point pixel value, whose sums
   over a stamp stay inside 32 bits and rebuild the 64-bit sum exactly;
 - the number of rings the tile reserves, against a brute-force maximum over
-  all stamp shapes.
+  all stamp shapes;
+- the cut-out's ring index for images of sides up to 32768 (d2 < 2^31): the
+  truncated approximate root and two conditional increments, next to every
+  perfect square and on random d2.
 """
 import math
 
@@ -87,3 +90,32 @@ def test_ring_slots_cover_every_shape():
         worst = max(v for (h, w), v in need.items() if h * w <= max_pix)
         assert ring_slots(max_pix) == worst, max_pix
     assert ring_slots(48 * 48) == 131 and ring_slots(128 * 128) == 182
+
+
+def ring_ceil32(d2, rel_err):
+    """The cut-out's ring index for d2 < 2^31: the float nearest d2, its root
+    off by rel_err, truncated, and two conditional increments (uint32)."""
+    f = d2.astype(np.float32)                                   # round to nearest
+    r = (np.sqrt(f.astype(np.float64)) * (1.0 + rel_err)).astype(np.float32)
+    k = r.astype(np.uint64)                                     # truncation
+    d = d2.astype(np.uint64)
+    for _ in range(2):
+        k = k + ((k * k) < d).astype(np.uint64)
+    assert np.all(k * k < 2 ** 32)
+    return k.astype(np.int64)
+
+
+def test_cutout_ring_index_near_squares():
+    """Images with both sides <= 32768: d2 <= 2 * 32767^2 < 2^31.  The hard
+    cases sit next to perfect squares, where the root is closest to an
+    integer; every square up to the largest d2 is taken with its neighbours,
+    plus random d2, and the root is perturbed by up to 2^-21 relative."""
+    dmax = 2 * 32767 ** 2
+    k = np.arange(0, math.isqrt(dmax) + 2, dtype=np.int64)
+    d2 = np.concatenate([k * k - 1, k * k, k * k + 1,
+                         np.random.default_rng(1).integers(0, dmax + 1, 200000)])
+    d2 = d2[(d2 >= 0) & (d2 <= dmax)]
+    root = np.array([math.isqrt(int(x)) for x in d2], dtype=np.int64)
+    want = root + (root * root != d2)
+    for rel in (-2.0 ** -21, -2.0 ** -23, 0.0, 2.0 ** -23, 2.0 ** -21):
+        assert np.array_equal(ring_ceil32(d2, rel), want), rel
