@@ -460,29 +460,82 @@ struct MomState {
     int xr, yr;      // reference pixel of the stored per-pixel offsets
 };
 
-// The offsets (column - xr, row - yr) of a thread's pixels p = t, t + nt, ...
-// of a row-major stamp of width w, as floats.  They are integers below 2^24,
-// exact in fp32, so stepping them with float adds gives the same values as
-// converting the integer offsets, without a conversion per pixel.
-struct OffsetWalk {
-    float u, v;      // column and row offset of the current pixel
-    float du, dv;    // one step of nt pixels: dv rows and du columns
-    float wrap, fw;  // u >= wrap: the column passed the right edge (w - xr); fw = w
-    __device__ __forceinline__ OffsetWalk(int t, int w, int nt, int xr, int yr) {
-        const int row = t / w, dr = nt / w;
-        u = static_cast<float>(t - row * w - xr);
-        v = static_cast<float>(row - yr);
-        du = static_cast<float>(nt - dr * w);
+// The moment sums run over the pixels whose weight W = 2^(-R^2 log2(e) /
+// (2 s_w^2)) is at least 2^-40, i.e. R^2 <= 80 ln 2 s_w^2: a pixel outside
+// adds less than 2^-40 |I| |theta|^k to a sum, so all of them together move
+// the centre by less than 2^-40 sum|I| max|theta| / sum I W (below 1e-9 px on
+// the benchmark's faintest stamps) and g and s_w by as little.  The ellipse
+// A t1^2 + B t2^2 - 4 g2 t1 t2 <= Rc^2 (Eq. A1; the determinant of the form
+// is (1 - |g|^2)^2) lies inside |t1| <= Rc sqrt(B) / (1 - |g|^2), |t2| <=
+// Rc sqrt(A) / (1 - |g|^2); the box adds a pixel of margin and is cut to the
+// stamp.  Compact objects (stars, small galaxies) cover a fraction of their
+// stamp, which is the work saved.
+constexpr float kWeightCut = 7.4446500f;   // sqrt(80 ln 2)
+
+struct Box {
+    int r0, c0;   // first row and column
+    int bh, bw;   // rows and columns (at least one each)
+    // stamp index of the box's last pixel
+    __device__ __forceinline__ int last(int w) const { return (r0 + bh - 1) * w + c0 + bw - 1; }
+};
+
+__device__ __forceinline__ Box weight_box(const MomState& st, int h, int w) {
+    const float gg = st.g1 * st.g1 + st.g2 * st.g2;
+    const float rc = kWeightCut * st.sw / (1.f - gg);
+    const float hx = fminf(rc * sqrtf(1.f + gg + 2.f * st.g1) + 1.f, 4096.f);
+    const float hy = fminf(rc * sqrtf(1.f + gg - 2.f * st.g1) + 1.f, 4096.f);
+    const float xc = static_cast<float>(st.xi) + st.xf, yc = static_cast<float>(st.yi) + st.yf;
+    Box b;
+    b.c0 = max(0, static_cast<int>(floorf(xc - hx)));
+    b.r0 = max(0, static_cast<int>(floorf(yc - hy)));
+    const int c1 = min(w - 1, static_cast<int>(ceilf(xc + hx)));
+    const int r1 = min(h - 1, static_cast<int>(ceilf(yc + hy)));
+    // a centre outside the stamp (the iteration then stops) or a non-finite
+    // state falls back to the whole stamp
+    if (!(c1 >= b.c0 && r1 >= b.r0) || !(hx > 0.f && hy > 0.f)) {
+        b.c0 = b.r0 = 0;
+        b.bw = w;
+        b.bh = h;
+    } else {
+        b.bw = c1 - b.c0 + 1;
+        b.bh = r1 - b.r0 + 1;
+    }
+    return b;
+}
+
+// The pixels q = t, t + nt, ... of a box, row-major within it (the stamp
+// index p grows with q, so a walk ends once p passes the box's last pixel;
+// a thread with t beyond the box starts past it): their offsets
+// (column - xr, row - yr) from the reference pixel and their index in the
+// stamp of width w.  The offsets are integers below 2^24, exact in fp32, so
+// stepping them with float adds gives the same values as converting the
+// integer offsets, without a conversion per pixel.
+struct BoxWalk {
+    float u, v;
+    int p;
+    float du, dv, wrap, fbw;
+    int dp, dwrap;
+    __device__ __forceinline__ BoxWalk(int t, const Box& b, int w, int nt, int xr, int yr) {
+        const int row = t / b.bw, col = t - row * b.bw;
+        const int dr = nt / b.bw, dc = nt - dr * b.bw;
+        u = static_cast<float>(b.c0 + col - xr);
+        v = static_cast<float>(b.r0 + row - yr);
+        p = (b.r0 + row) * w + b.c0 + col;
+        du = static_cast<float>(dc);
         dv = static_cast<float>(dr);
-        wrap = static_cast<float>(w - xr);
-        fw = static_cast<float>(w);
+        wrap = static_cast<float>(b.c0 + b.bw - xr);
+        fbw = static_cast<float>(b.bw);
+        dp = dr * w + dc;
+        dwrap = w - b.bw;
     }
     __device__ __forceinline__ void next() {
         u += du;
         v += dv;
+        p += dp;
         if (u >= wrap) {
-            u -= fw;
+            u -= fbw;
             v += 1.f;
+            p += dwrap;
         }
     }
 };
@@ -495,7 +548,7 @@ struct OffsetWalk {
 // derivative, not the fixed point; a pass without them leaves acc[6..10] as
 // they were (the last pass that summed them).
 template <int NW, bool FOURTH>
-__device__ __forceinline__ void moment_pass(const float* __restrict__ s, int w, int npix,
+__device__ __forceinline__ void moment_pass(const float* __restrict__ s, int w, const Box& bx,
                                             const Grp<NW>& g, const MomState& st,
                                             float (&acc)[11]) {
     const float gg = st.g1 * st.g1 + st.g2 * st.g2;
@@ -512,15 +565,17 @@ __device__ __forceinline__ void moment_pass(const float* __restrict__ s, int w, 
     const float cx = static_cast<float>(st.xi - st.xr) + st.xf;
     const float cy = static_cast<float>(st.yi - st.yr) + st.yf;
     // pixel offsets from the reference pixel, exact integers in fp32
-    OffsetWalk ow(g.t, w, Grp<NW>::NT, st.xr, st.yr);
+    BoxWalk ow(g.t, bx, w, Grp<NW>::NT, st.xr, st.yr);
+    const int plast = bx.last(w);   // the walk's index grows with each step
 #pragma unroll 2
-    for (int p = g.t; p < npix; p += Grp<NW>::NT) {
+    while (ow.p <= plast) {
         const float t1 = ow.u - cx;
         const float t2 = ow.v - cy;
+        const float I = s[ow.p];
         ow.next();
         const float t11 = t1 * t1, t22 = t2 * t2, t12 = t1 * t2;
         const float R2 = fmaf(A, t11, fmaf(B, t22, -G4 * t12));
-        const float f = s[p] * ex2(R2 * cw);
+        const float f = I * ex2(R2 * cw);
         acc[0] += f;
         acc[1] = fmaf(f, t1, acc[1]);
         acc[2] = fmaf(f, t2, acc[2]);
@@ -709,9 +764,12 @@ __device__ __noinline__ void shear_polarizability(const float (&m)[11], const Mo
 // that noise.  The fixed point's accuracy is set by the weights' rounding:
 // with an fp32 exponent (relative errors of ~2e-7 at two weight sizes) the
 // centre moved by ~1e-7 px, which first-order chi^2 sensitivities of up to
-// ~6e5 per px on bright stamps turn into 1e-5 of chi^2.
+// ~6e5 per px on bright stamps turn into 1e-5 of chi^2.  The sums run over
+// the weight's box (weight_box).  Returns the largest move (pixels, g, and
+// s_w relative), or -1 when no step was taken (singular sums, or a step
+// larger than the iteration's own noise).
 template <int NW>
-__device__ float moment_refine(const float* __restrict__ s, int w, int npix, const Grp<NW>& g,
+__device__ float moment_refine(const float* __restrict__ s, int h, int w, const Grp<NW>& g,
                                bool ellip, bool matched, float sw_max, const float (&F)[5], MomState& st) {
     const float gg = st.g1 * st.g1 + st.g2 * st.g2;
     const float A = 1.f + gg - 2.f * st.g1;
@@ -721,9 +779,12 @@ __device__ float moment_refine(const float* __restrict__ s, int w, int npix, con
     float dh[6], dl[6], cx[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) dh[i] = dl[i] = cx[i] = 0.f;
-    OffsetWalk ow(g.t, w, Grp<NW>::NT, st.xi, st.yi);
+    const Box bx = weight_box(st, h, w);
+    BoxWalk ow(g.t, bx, w, Grp<NW>::NT, st.xi, st.yi);
+    const int plast = bx.last(w);
 #pragma unroll 1
-    for (int p = g.t; p < npix; p += Grp<NW>::NT) {
+    while (ow.p <= plast) {
+        const int p = ow.p;
         const float k1 = ow.u, k2 = ow.v;
         // theta = k - x_f exactly as hi + lo (|k| >= |x_f| unless k = 0, where lo = 0)
         const float t1 = k1 - st.xf, t1l = -st.xf - (t1 - k1);
@@ -776,7 +837,7 @@ __device__ float moment_refine(const float* __restrict__ s, int w, int npix, con
     const float Q11 = dh[3] + (dl[3] + cx[3]);
     const float Q12 = dh[4] + (dl[4] + cx[4]);
     const float Q22 = dh[5] + (dl[5] + cx[5]);
-    if (!(M0 > 0.f) || !(Q11 + Q22 > 0.f)) return 1.f;
+    if (!(M0 > 0.f) || !(Q11 + Q22 > 0.f)) return -1.f;
     const float c = 1.f / (2.f * st.sw * st.sw);
     const float g1 = st.g1, g2 = st.g2;
     const float J11 = 2.f * c * (A * Q11 - 2.f * g2 * Q12) - M0;
@@ -784,7 +845,7 @@ __device__ float moment_refine(const float* __restrict__ s, int w, int npix, con
     const float J21 = 2.f * c * (A * Q12 - 2.f * g2 * Q22);
     const float J22 = 2.f * c * (B * Q22 - 2.f * g2 * Q12) - M0;
     const float dj = J11 * J22 - J12 * J21;
-    if (!(dj > 0.f)) return 1.f;
+    if (!(dj > 0.f)) return -1.f;
     const float dx = -(J22 * M1x - J12 * M1y) / dj;
     const float dy = -(-J21 * M1x + J11 * M1y) / dj;
     // the second moments as doubles (a few operations per stamp): the
@@ -809,7 +870,7 @@ __device__ float moment_refine(const float* __restrict__ s, int w, int npix, con
         float P11, P12, P21, P22;
         shear_polarizability(m, st, (Q11 - Q22) / T, 2.f * Q12 / T, &P11, &P12, &P21, &P22);
         const float det = P11 * P22 - P12 * P21;
-        if (!(fabsf(det) > 0.f) || !isfinite(det)) return 1.f;
+        if (!(fabsf(det) > 0.f) || !isfinite(det)) return -1.f;
         const float sc = (1.f - gg) / det;
         dg1 = sc * (P22 * r1 - P12 * r2);
         dg2 = sc * (-P21 * r1 + P11 * r2);
@@ -834,7 +895,7 @@ __device__ float moment_refine(const float* __restrict__ s, int w, int npix, con
     // a refinement moves the point by at most the iteration's own noise
     if (!(fabsf(dx) <= 1e-3f && fabsf(dy) <= 1e-3f && fabsf(dg1) <= 1e-3f && fabsf(dg2) <= 1e-3f &&
           fabsf(ds) <= 1e-3f * st.sw))
-        return 1.f;
+        return -1.f;
     st.xf += dx;
     st.yf += dy;
     st.g1 += dg1;
@@ -844,6 +905,7 @@ __device__ float moment_refine(const float* __restrict__ s, int w, int npix, con
 }
 
 constexpr float kMomRefineSkip = 1e-7f;
+constexpr int kMomRefineMax = 4;   // refinement passes at most (matched weight; else one fewer)
 
 // Iterate to the stop rule.  Returns the number of passes; sets status bits.
 template <int NW>
@@ -863,10 +925,11 @@ __device__ int moment_iterate(const float* s, int h, int w, int npix, const Grp<
     // weight size) still moves by more than 1e-3; later passes reuse them
     bool fourth = true;
     for (it = 1; it <= o.max_iter_mom; ++it) {
+        const Box bx = weight_box(st, h, w);
         if (fourth)
-            moment_pass<NW, true>(s, w, npix, g, st, m);
+            moment_pass<NW, true>(s, w, bx, g, st, m);
         else
-            moment_pass<NW, false>(s, w, npix, g, st, m);
+            moment_pass<NW, false>(s, w, bx, g, st, m);
 #pragma unroll
         for (int i = 0; i < 5; ++i) F4[i] = m[6 + i];
         const MomStep d = moment_step(m, st, k_use, ellip);
@@ -939,15 +1002,19 @@ __device__ int moment_iterate(const float* s, int h, int w, int npix, const Grp<
         it = o.max_iter_mom;
     }
     // refinement steps: the first leaves about a tenth of its own step (the
-    // centre and g steps are taken separately); a second runs unless the first
-    // moved the point by less than 1e-7
+    // centre, g and s_w steps are taken separately); another runs while the
+    // last moved the point by more than kMomRefineSkip, up to kMomRefineMax
+    // passes for the matched weight (whose s_w step couples to the others
+    // most strongly, for weights of a pixel or less) and one fewer otherwise.
+    // A step the refinement does not take (negative return) ends them.
     if (status & FSE_ST_MOM_CONVERGED) {
-        // one call site (the pass is large code): a second round runs only when
-        // the first moved the point by more than kMomRefineSkip
+        // one call site: the pass is large code
 #pragma unroll 1
-        for (int r = 0; r < 2; ++r) {
+        const int rmax = o.sigw_mode == 0 ? kMomRefineMax : kMomRefineMax - 1;
+        for (int r = 0; r < rmax; ++r) {
             if (r == 1) status |= FSE_ST_MOM_REFINE2;
-            if (moment_refine(s, w, npix, g, ellip, o.sigw_mode == 0, sw_max, F4, st) <= kMomRefineSkip) break;
+            const float moved = moment_refine(s, h, w, g, ellip, o.sigw_mode == 0, sw_max, F4, st);
+            if (moved <= kMomRefineSkip) break;
         }
     }
     return it;
