@@ -608,16 +608,20 @@ struct MomStep {
     bool ok;
 };
 
-__device__ __noinline__ void shear_polarizability(const float (&m)[11], const MomState& st,
-                                                  float e1, float e2, float* P11, float* P12,
-                                                  float* P21, float* P22);
+struct Pol {
+    float P11, P12, P21, P22;
+};
+
+__device__ __noinline__ Pol shear_polarizability(float Q11, float Q12, float Q22, float F40, float F31,
+                                                 float F22, float F13, float F04, float g1, float g2,
+                                                 float sw, float e1, float e2);
 
 // The centroid step <x>/N = k dx (Eqs. 5-6) and the ellipticity step
 // dg = (1-|g_w|^2) (P^SH)^-1 (e^obs - e_w) (Eq. 9) with
 // P^SH = X^SH + dX^SH - e (e^SH + de^SH)^T (Eq. 8, A5, A6, B7, B8), evaluated
 // from the eleven weighted moments.  W' = dW/dR^2 = -c W with c = 1/(2 s_w^2).
 __device__ __forceinline__ MomStep moment_step(const float (&m)[11], const MomState& st,
-                                               float k_gain, bool ellip) {
+                                               float k_gain, bool ellip, bool matched) {
     MomStep r;
     r.ok = false;
     r.dx = r.dy = r.dg1 = r.dg2 = 0.f;
@@ -632,8 +636,9 @@ __device__ __forceinline__ MomStep moment_step(const float (&m)[11], const MomSt
     // Eqs. 5-6 with the fixed gain k (k_gain, or 0.75 where the determined
     // gain below is not usable)
     const float kf = k_gain > 0.f ? k_gain : 0.75f;
-    r.dx = m[1] / (kf * S0);
-    r.dy = m[2] / (kf * S0);
+    const float ik = 1.f / (kf * S0);
+    r.dx = m[1] * ik;
+    r.dy = m[2] * ik;
     if (k_gain <= 0.f) {
         // k determined from the current moments: the derivative of
         // (sum I W theta_1, sum I W theta_2) with respect to the centre, which
@@ -650,20 +655,22 @@ __device__ __forceinline__ MomStep moment_step(const float (&m)[11], const MomSt
         const float J21 = 2.f * c * (A * Q12 - 2.f * g2 * Q22);
         const float J22 = 2.f * c * (B * Q22 - 2.f * g2 * Q12) - S0;
         const float dj = J11 * J22 - J12 * J21;
-        const float nx = -(J22 * m[1] - J12 * m[2]) / dj;
-        const float ny = -(-J21 * m[1] + J11 * m[2]) / dj;
-        const float num = sqrtf(m[1] * m[1] + m[2] * m[2]);
-        const float den = S0 * sqrtf(nx * nx + ny * ny);
+        const float idj = 1.f / dj;
+        const float nx = -(J22 * m[1] - J12 * m[2]) * idj;
+        const float ny = -(-J21 * m[1] + J11 * m[2]) * idj;
+        // |M1| against S0 |n| compared squared: [0.15, 1.5] -> [0.0225, 2.25]
+        const float num2 = m[1] * m[1] + m[2] * m[2];
+        const float den2 = S0 * S0 * (nx * nx + ny * ny);
         const bool near = fmaxf(fabsf(r.dx), fabsf(r.dy)) < 0.25f && st.sw > 0.6f;
         if (near && dj > 0.f && isfinite(nx) && isfinite(ny) &&
-            (den == 0.f || (num >= 0.15f * den && num <= 1.5f * den))) {
+            (den2 == 0.f || (num2 >= 0.0225f * den2 && num2 <= 2.25f * den2))) {
             r.dx = nx;
             r.dy = ny;
         }
     }
-    const float SR2 = A * Q11 + B * Q22 - 4.f * g2 * Q12;      // sum f W R^2
-    r.sw_new = SR2 > 0.f ? sqrtf(SR2 / S0) : 0.f;
-    {
+    if (matched) {
+        const float SR2 = A * Q11 + B * Q22 - 4.f * g2 * Q12;      // sum f W R^2
+        r.sw_new = SR2 > 0.f ? sqrtf(SR2 / S0) : 0.f;
         // The matched-weight rule s_w^2 = S(s_w) = sum f W R^2 / sum f W contracts
         // slowly for cuspy profiles; near its fixed point take a Newton step on
         // s_w^2 - S(s_w) = 0 instead, with dS/ds_w = (<R^4> - <R^2>^2) / s_w^3
@@ -686,35 +693,33 @@ __device__ __forceinline__ MomStep moment_step(const float (&m)[11], const MomSt
     }
     const float T = Q11 + Q22;
     if (!(T > 0.f)) return r;
-    const float e1 = (Q11 - Q22) / T, e2 = 2.f * Q12 / T;
-    float P11, P12, P21, P22;
-    shear_polarizability(m, st, e1, e2, &P11, &P12, &P21, &P22);
-    const float det = P11 * P22 - P12 * P21;
+    const float iT = 1.f / T;
+    const float e1 = (Q11 - Q22) * iT, e2 = 2.f * Q12 * iT;
+    const Pol P = shear_polarizability(Q11, Q12, Q22, m[6], m[7], m[8], m[9], m[10], g1, g2, st.sw, e1, e2);
+    const float det = P.P11 * P.P22 - P.P12 * P.P21;
     if (!(fabsf(det) > 0.f) || !isfinite(det)) return r;
     const float ew = 2.f / (1.f + gg);
     const float r1 = e1 - ew * g1, r2 = e2 - ew * g2;
     const float sc = (1.f - gg) / det;
-    r.dg1 = sc * (P22 * r1 - P12 * r2);
-    r.dg2 = sc * (-P21 * r1 + P11 * r2);
+    r.dg1 = sc * (P.P22 * r1 - P.P12 * r2);
+    r.dg2 = sc * (-P.P21 * r1 + P.P11 * r2);
     r.ok = isfinite(r.dg1) && isfinite(r.dg2) && isfinite(r.dx) && isfinite(r.dy);
     return r;
 }
 
 // P^SH = X^SH + dX^SH - e (e^SH + de^SH)^T (Eq. 8 with A5, A6, B7, B8) from the
-// eleven weighted moments; W' = dW/dR^2 = -c W with c = 1/(2 s_w^2).  Kept out
-// of line: it is called once per pass from two places, and the moment
-// kernel's code size (instruction fetch) matters more than a call.
-__device__ __noinline__ void shear_polarizability(const float (&m)[11], const MomState& st,
-                                                  float e1, float e2, float* P11, float* P12,
-                                                  float* P21, float* P22) {
-    const float Q11 = m[3], Q12 = m[4], Q22 = m[5];
-    const float F40 = m[6], F31 = m[7], F22 = m[8], F13 = m[9], F04 = m[10];
-    const float g1 = st.g1, g2 = st.g2;
+// second and fourth weighted moments; W' = dW/dR^2 = -c W with
+// c = 1/(2 s_w^2).  Kept out of line: it is called once per pass from two
+// places, and the moment kernel's code size (instruction fetch) matters more
+// than a call; arguments and result travel in registers.
+__device__ __noinline__ Pol shear_polarizability(float Q11, float Q12, float Q22, float F40, float F31,
+                                                 float F22, float F13, float F04, float g1, float g2,
+                                                 float sw, float e1, float e2) {
     const float gg = g1 * g1 + g2 * g2;
     const float A = 1.f + gg - 2.f * g1, B = 1.f + gg + 2.f * g1;
     const float T = Q11 + Q22;
     const float iT = 1.f / T;
-    const float c = 1.f / (2.f * st.sw * st.sw);
+    const float c = 1.f / (2.f * sw * sw);
     const float ApB = A + B, AmB = A - B;
     const float F31m13 = F31 - F13, F31p13 = F31 + F13;
     // Appendix A: sum f W chi_a psi_b and sum f W theta^2 psi_b
@@ -744,10 +749,12 @@ __device__ __noinline__ void shear_polarizability(const float (&m)[11], const Mo
     X22 += (g1 * P4 - g2 * P3) * iT;
     eS1 += (-g1 * P5 - g2 * P6) * iT;
     eS2 += (g1 * P6 - g2 * P5) * iT;
-    *P11 = X11 - e1 * eS1;
-    *P12 = X12 - e1 * eS2;
-    *P21 = X21 - e2 * eS1;
-    *P22 = X22 - e2 * eS2;
+    Pol P;
+    P.P11 = X11 - e1 * eS1;
+    P.P12 = X12 - e1 * eS2;
+    P.P21 = X21 - e2 * eS1;
+    P.P22 = X22 - e2 * eS2;
+    return P;
 }
 
 // Final refinement of the fixed point: one pass with the pixel offsets theta
@@ -866,9 +873,9 @@ __device__ float moment_refine(const float* __restrict__ s, int h, int w, const 
         const float T = Q11 + Q22;
         const float den = T * (1.f + gg);
         const float r1 = n1 / den, r2 = n2 / den;
-        const float m[11] = {M0, M1x, M1y, Q11, Q12, Q22, F[0], F[1], F[2], F[3], F[4]};
-        float P11, P12, P21, P22;
-        shear_polarizability(m, st, (Q11 - Q22) / T, 2.f * Q12 / T, &P11, &P12, &P21, &P22);
+        const Pol P = shear_polarizability(Q11, Q12, Q22, F[0], F[1], F[2], F[3], F[4], g1, g2, st.sw,
+                                           (Q11 - Q22) / T, 2.f * Q12 / T);
+        const float P11 = P.P11, P12 = P.P12, P21 = P.P21, P22 = P.P22;
         const float det = P11 * P22 - P12 * P21;
         if (!(fabsf(det) > 0.f) || !isfinite(det)) return -1.f;
         const float sc = (1.f - gg) / det;
@@ -932,7 +939,7 @@ __device__ int moment_iterate(const float* s, int h, int w, int npix, const Grp<
             moment_pass<NW, false>(s, w, bx, g, st, m);
 #pragma unroll
         for (int i = 0; i < 5; ++i) F4[i] = m[6 + i];
-        const MomStep d = moment_step(m, st, k_use, ellip);
+        const MomStep d = moment_step(m, st, k_use, ellip, o.sigw_mode == 0);
         if (k_use <= 0.f) {
             const float dc = fmaxf(fabsf(d.dx), fabsf(d.dy));
             if (it > 2 && dc >= prev_c) k_use = 0.75f;
@@ -1009,8 +1016,8 @@ __device__ int moment_iterate(const float* s, int h, int w, int npix, const Grp<
     // A step the refinement does not take (negative return) ends them.
     if (status & FSE_ST_MOM_CONVERGED) {
         // one call site: the pass is large code
-#pragma unroll 1
         const int rmax = o.sigw_mode == 0 ? kMomRefineMax : kMomRefineMax - 1;
+#pragma unroll 1
         for (int r = 0; r < rmax; ++r) {
             if (r == 1) status |= FSE_ST_MOM_REFINE2;
             const float moved = moment_refine(s, h, w, g, ellip, o.sigw_mode == 0, sw_max, F4, st);

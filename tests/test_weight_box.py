@@ -57,3 +57,23 @@ def test_box_saves_work_on_compact_objects():
     assert bh <= 19 and bw <= 19
     # a weight wider than the stamp: the whole stamp
     assert weight_box(24, 24, 0.1, -0.2, 0.3, 0.1, 12.0, 48, 48) == (0, 0, 48, 48)
+
+
+def test_bench_counts_the_same_box():
+    """bench.py's operation count takes the moment passes over the same box."""
+    import bench
+    rng = np.random.default_rng(3)
+    n = 500
+    rec = np.zeros(n, dtype=[("x0", "f4"), ("y0", "f4"), ("e1", "f4"), ("e2", "f4"), ("sigma_w", "f4")])
+    rec["x0"] = rng.uniform(0, 47, n)
+    rec["y0"] = rng.uniform(0, 47, n)
+    gabs, phi = rng.uniform(0, 0.9, n), rng.uniform(0, 2 * np.pi, n)
+    rec["e1"], rec["e2"] = gabs * np.cos(phi), gabs * np.sin(phi)
+    rec["sigma_w"] = rng.uniform(0.5, 6, n)
+    got = bench.box_pixels(rec, 48, 48)
+    for j in range(n):
+        xi, yi = int(np.rint(rec["x0"][j])), int(np.rint(rec["y0"][j]))
+        r0, c0, bh, bw = weight_box(xi, yi, rec["x0"][j] - xi, rec["y0"][j] - yi, rec["e1"][j], rec["e2"][j],
+                                    rec["sigma_w"][j], 48, 48)
+        # fp32 versus fp64 rounding of the edges moves a side by a pixel at most
+        assert abs(got[j] - bh * bw) <= bh + bw + 1, (j, got[j], bh * bw)
