@@ -926,6 +926,7 @@ __device__ int moment_iterate(const float* s, int h, int w, int npix, const Grp<
     // with the determined gain (k_gain = 0): a centre step that does not shrink
     // switches the rest of the iteration to the fixed gain
     float k_use = o.k_gain, prev_c = 0.f;
+    const float inv_tol_pos = 1.f / o.tol_pos, inv_tol_g = 1.f / o.tol_g, inv_tol_sig = 1.f / o.tol_sig;
     int it;
     float m[11];
     // the fourth moments are summed while the ellipticity (or the matched
@@ -965,10 +966,11 @@ __device__ int moment_iterate(const float* s, int h, int w, int npix, const Grp<
             // |g| < 1: a step past (1 + |g_w|)/2 is shortened radially to it
             const float cap = 0.5f * (1.f + sqrtf(st.g1 * st.g1 + st.g2 * st.g2));
             float n1 = st.g1 + d.dg1, n2 = st.g2 + d.dg2;
-            const float nn = sqrtf(n1 * n1 + n2 * n2);
-            if (nn > cap) {
-                n1 *= cap / nn;
-                n2 *= cap / nn;
+            const float nn2 = n1 * n1 + n2 * n2;
+            if (nn2 > cap * cap) {
+                const float f = cap * rsqrtf(nn2);
+                n1 *= f;
+                n2 *= f;
             }
             st.g1 = n1;
             st.g2 = n2;
@@ -980,7 +982,7 @@ __device__ int moment_iterate(const float* s, int h, int w, int npix, const Grp<
             float ns = d.sw_new;
             if (ns < 0.5f) { ns = 0.5f; status |= FSE_ST_SIGW_CLAMPED; }
             if (ns > sw_max) { ns = sw_max; status |= FSE_ST_SIGW_CLAMPED; }
-            dsig = fabsf(ns - st.sw) / st.sw;
+            dsig = __fdividef(fabsf(ns - st.sw), st.sw);
             st.sw = ns;
         }
         const float xc = static_cast<float>(st.xi) + st.xf, yc = static_cast<float>(st.yi) + st.yf;
@@ -994,10 +996,12 @@ __device__ int moment_iterate(const float* s, int h, int w, int npix, const Grp<
         // estimated as |step| rho / (1 - rho) with rho = |step_k| / |step_k-1|;
         // steps below a quarter of the tolerances (where the fp32 sums' noise
         // makes rho meaningless) always stop.
-        const float sz = fmaxf(fmaxf(fabsf(d.dx), fabsf(d.dy)) / o.tol_pos,
-                               fmaxf(fmaxf(fabsf(d.dg1), fabsf(d.dg2)) / o.tol_g, dsig / o.tol_sig));
-        const float rho = prev > 0.f ? fminf(sz / prev, 0.95f) : 0.f;
-        const float left = (sz > 0.25f && rho > 0.5f) ? sz * rho / (1.f - rho) : sz;
+        // (step sizes in units of the tolerances; the stop rule needs no
+        // correctly rounded quotients)
+        const float sz = fmaxf(fmaxf(fabsf(d.dx), fabsf(d.dy)) * inv_tol_pos,
+                               fmaxf(fmaxf(fabsf(d.dg1), fabsf(d.dg2)) * inv_tol_g, dsig * inv_tol_sig));
+        const float rho = prev > 0.f ? fminf(__fdividef(sz, prev), 0.95f) : 0.f;
+        const float left = (sz > 0.25f && rho > 0.5f) ? __fdividef(sz * rho, 1.f - rho) : sz;
         prev = sz;
         if (left <= 1.f) {
             status |= FSE_ST_MOM_CONVERGED;
