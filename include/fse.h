@@ -111,7 +111,7 @@ typedef struct {
     double  tol_pos;        /* stop when |centroid step| <= tol_pos px        (1e-6)    */
     double  tol_g;          /* ... and |ellipticity step| <= tol_g            (1e-6)    */
     double  tol_sig;        /* ... and |sigma_w step|/sigma_w <= tol_sig, mode 0 (1e-6) */
-    double  tol_fit;        /* fit stops when max relative (r_e, n) step <= tol_fit (1e-6) */
+    double  tol_fit;        /* fit stops when max relative (r_e, n) step <= tol_fit (1e-4) */
     int32_t max_iter_mom;   /* moment iterations                              (60)      */
     int32_t max_iter_fit;   /* fit iterations                                 (60)      */
     double  k_gain;         /* centroid gain k of Sec. 2.  0 (default): k determined

@@ -385,7 +385,7 @@ void fse_opts_default(fse_opts* o) {
     o->tol_pos = 1e-6;
     o->tol_g = 1e-6;
     o->tol_sig = 1e-6;
-    o->tol_fit = 1e-6;
+    o->tol_fit = 1e-4;
     o->max_iter_mom = 60;
     o->max_iter_fit = 60;
     o->k_gain = 0.0;

@@ -1715,7 +1715,7 @@ __device__ Precise fit_refine(const float* __restrict__ s, const float* __restri
     return refine_tail<float>(rh, rl, T, chi2_rr, I0g, re, n, bf, dbf, bn_d2_f(n));
 }
 
-constexpr float kFitRefineSkip = 1e-5f;   // a Newton step below this ends the refinement
+constexpr float kFitRefineSkip = 1e-4f;   // a Newton step below this ends the refinement
 constexpr float kFitRefineCap = 0.2f;     // largest relative step of one refinement pass
 constexpr float kFitRefineTrusted = 1e-2f; // steps up to this are taken without a chi^2 test
 constexpr int kFitRefineMax = 16;         // refinement passes at most
@@ -1846,13 +1846,16 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
     bool refined = false;
     if (isfinite(cur.chi2) && re > re_min && re < re_max && n > n_min && n < n_max) {
         // Newton refinement on exact chi^2 (double-float sums): the error left
-        // after a step is about the square of the step, so a step below 1e-5
-        // ends it, applied with chi^2 from the quadratic model (exact to third
-        // order in the step).  Steps up to 1e-2 are taken as they are; larger
-        // ones are capped at 20 % of each parameter and taken only if the
-        // exact chi^2 does not rise, else retried at a quarter of the length.  This also finishes fits that the
-        // fp32 iteration left early in a flat valley, where chi^2 changes below
-        // its fp32 resolution.
+        // after a step is about the square of the step, so a step below 1e-4
+        // (relative; about 1e-8 left) ends it, applied with chi^2 from the
+        // quadratic model (exact to third order in the step).  The fp32
+        // iteration above therefore stops at a 1e-4 step (tol_fit) and leaves
+        // the last stretch to this quadratically converging pass.  Steps up to
+        // 1e-2 are taken as they are; larger ones are capped at 20 % of each
+        // parameter and taken only if the exact chi^2 does not rise, else
+        // retried at a quarter of the length.  This also finishes fits that
+        // the fp32 iteration left early in a flat valley, where chi^2 changes
+        // below its fp32 resolution.
         // one call site (the pixel pass is large): each round evaluates the
         // next point, then accepts or rejects it against the best so far
         Precise P;
