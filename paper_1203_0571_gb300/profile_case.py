@@ -1,11 +1,14 @@
 """A small, self-contained launch of libfse for profiler captures.
 
-    python -m paper_1203_0571_gb300.profile_case [--what fit_batch|adjoint|star|moment_vjp|moment_jvp|cutout]
-        [--profile gauss|moffat] [--workload 1] [--stamps 20000] [--warmup 3] [--launches 1]
+    python -m paper_1203_0571_gb300.profile_case [--what fit_batch|ragged|adjoint|star|moment_vjp|moment_jvp|cutout]
+        [--profile gauss|moffat] [--workload 1] [--stamps 20000] [--warmup 3] [--launches 1] [--bf16]
 
 Generates the first `stamps` stamps of a synthetic workload on the GPU, runs
 `warmup` launches, then `launches` more, and prints the per-launch time.
-fit_batch runs the whole chain; adjoint runs fse_sersic_chi2_grad at the
+fit_batch runs the whole chain; ragged runs fse_fit_batch_ragged on a whole
+ragged workload (default the 1,000,000 ragged stamps; --workload 4 the
+4,000,000 stamps of 32-64 px, --bf16 with bf16 pixels) after fse_autotune,
+as a replayed CUDA graph; adjoint runs fse_sersic_chi2_grad at the
 generating parameters with the pixel gradient (the backward launch of the
 autograd bridge); star runs fse_star_fit (Sec. 4.2) at the centre and
 ellipticity of a preceding fse_centroid + fse_ellipticity; moment_vjp and
@@ -32,8 +35,10 @@ from . import synth
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--what", choices=["fit_batch", "adjoint", "star", "moment_vjp", "moment_jvp", "cutout"],
+    ap.add_argument("--what", choices=["fit_batch", "ragged", "adjoint", "star", "moment_vjp", "moment_jvp",
+                                       "cutout"],
                     default="fit_batch")
+    ap.add_argument("--bf16", action="store_true", help="ragged: pixels stored as bf16 with a per-stamp scale")
     ap.add_argument("--profile", choices=["gauss", "moffat"], default="gauss")
     ap.add_argument("--supersample", type=int, default=1,
                     help="fit_batch: the fit's model as the mean of S x S samples per pixel")
@@ -52,6 +57,9 @@ def main():
         return moment_grad(ctx, args.what == "moment_jvp", args.workload if args.workload is not None else 1,
                            args.stamps if args.stamps is not None else 100000, args.warmup, args.launches,
                            args.sigw)
+    if args.what == "ragged":
+        return ragged(ctx, args.workload if args.workload is not None else 2, args.stamps, args.warmup,
+                      args.launches, args.bf16)
     if args.what == "cutout":
         return cutout(ctx, args.stamps if args.stamps is not None else 500, args.warmup, args.launches)
     if args.what == "star":
@@ -154,6 +162,40 @@ def moment_grad(ctx, jvp, workload, stamps, warmup, launches, sigw):
                       "sigw": sigw,
                       "ms_per_launch": a.elapsed_time(b) / launches,
                       "status_zero": float((st == 0).float().mean())}))
+
+
+def ragged(ctx, workload, stamps, warmup, launches, bf16):
+    """fse_fit_batch_ragged on a whole ragged workload: autotuned launch shapes,
+    captured once into a CUDA graph and replayed."""
+    import time
+    batch = synth.make_workload(workload, count=stamps, device="cuda")
+    if bf16:
+        batch = synth.encode_bf16(batch)
+    idx = B.make_index(batch.offset, batch.h, batch.w)
+    out = torch.empty((batch.count, 64), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    ctx.autotune(batch.pix, idx, scale=batch.scale, out=out)
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t
+    gopts = B.default_opts(flags=B.FSE_FLAG_GRAPH)
+    for _ in range(max(warmup, 1)):      # the first call captures the graph
+        ctx.fit_batch_ragged(batch.pix, idx, scale=batch.scale, out=out, opts=gopts)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(launches):
+        ctx.fit_batch_ragged(batch.pix, idx, scale=batch.scale, out=out, opts=gopts)
+    b.record()
+    ctx.sync_check()
+    ms = a.elapsed_time(b) / launches
+    res = B.results(out)
+    npx = float((batch.h.long() * batch.w.long()).sum())
+    print(json.dumps({"workload": synth.WORKLOADS[workload].name, "stamps": batch.count, "pixels": npx,
+                      "pixel_dtype": "bf16" if bf16 else "f32", "ms_per_call": ms,
+                      "stamps_per_s": batch.count / (ms / 1e3), "pixels_per_s": npx / (ms / 1e3),
+                      "tune_s": tune_s, "tuned_warps": ctx.tuned_warps(B.FSE_BF16 if bf16 else B.FSE_F32),
+                      "converged": float(((res["status"] & 3) == 3).mean())}))
 
 
 def cutout(ctx, images, warmup, launches):
