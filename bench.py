@@ -275,14 +275,16 @@ def cpu_oracle_rate(target_s: float, max_stamps: int):
 
 def run_oracle_rates(args):
     """Per-stamp oracle rates on seeded 10,000-stamp samples of the ragged,
-    gradient and precision workloads (and the benchmark's), on all host cores
-    and on one, bounded in time per sample; one JSON line."""
+    gradient and precision workloads (and the benchmark's), and on the whole
+    256-stamp small workload, on all host cores and on one, bounded in time
+    per sample; one JSON line."""
     from paper_1203_0571_gb300 import synth
     out = {"cpu": cpu_model(), "cores": os.cpu_count(), "kind": "oracle", "rates": {}}
-    for which in (1, 2, 3, 4, 5):
+    for which in (0, 1, 2, 3, 4, 5):
         name = synth.WORKLOADS[which].name
-        n, dt, used, res = oracle_rate(which, 3 * args.cpu_seconds, 10_000)
-        n1, dt1, _, _ = oracle_rate(which, args.cpu_seconds / 4, 10_000, threads=1)
+        cap = 10_000 if which else 256          # the small 32x32 workload whole
+        n, dt, used, res = oracle_rate(which, 3 * args.cpu_seconds, cap)
+        n1, dt1, _, _ = oracle_rate(which, args.cpu_seconds / 4, cap, threads=1)
         conv = ((res["status"] & 3) == 3).mean()
         out["rates"][name] = {"stamps": n, "threads": used, "stamps_per_s": n / dt, "s_per_stamp_1core": dt1 / n1,
                               "stamps_1core": n1, "converged_frac": float(conv),

@@ -294,6 +294,17 @@ int fse_autotune(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
 int fse_tuning_save(const fse_ctx *ctx, const char *path);
 int fse_tuning_load(fse_ctx *ctx, const char *path);
 
+/* The launch shapes a file written by fse_tuning_save holds for the device
+ * named `device` (cudaDeviceProp.name), read without a context or a GPU, with
+ * the checks fse_tuning_load applies (format "libfse-launch-shapes/1", this
+ * library's size classes, valid shapes; other entries are skipped).  shapes
+ * (host, 56 int32) receives, at ((dtype * 2 + inv_var) * 7 + class) * 2, the
+ * warps per CTA and the warps per stamp (0, 0 for the library default), or
+ * -1, -1 for a dtype and inverse-variance setting the file has no entry for.
+ * Returns the number of entries read (0 or more), or -FSE_EINVAL for a NULL
+ * argument or a file that cannot be opened.  Host call. */
+int fse_tuning_read(const char *path, const char *device, int32_t *shapes);
+
 /* The launch shape the ragged path uses for each of the seven size classes
  * (tuned or default), for a dtype and with (1) or without (0) inverse
  * variance: warps per CTA and warps per stamp (host arrays of 7; the second

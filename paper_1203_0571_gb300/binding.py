@@ -34,7 +34,7 @@ ST = dict(MOM_CONVERGED=1 << 0, FIT_CONVERGED=1 << 1, MOM_MAXITER=1 << 2, FIT_MA
 EXPORTS = ["fse_create", "fse_destroy", "fse_last_error", "fse_opts_default", "fse_centroid",
            "fse_ellipticity", "fse_sersic_fit", "fse_fit_batch", "fse_fit_batch_plain",
            "fse_fit_batch_host", "fse_fit_batch_ragged", "fse_autotune", "fse_tuning_save",
-           "fse_tuning_load", "fse_tuned_warps", "fse_star_fit", "fse_moment_vjp", "fse_moment_jvp",
+           "fse_tuning_load", "fse_tuning_read", "fse_tuned_warps", "fse_star_fit", "fse_moment_vjp", "fse_moment_jvp",
            "fse_cutout", "fse_sersic_b", "fse_sersic_chi2_grad", "fse_partition", "fse_sync_check",
            "fse_fit_batch_static"]
 CUTOUT_DTYPE = np.dtype([("row0", "<i4"), ("col0", "<i4"), ("h", "<i4"), ("w", "<i4"), ("r50", "<f4"),
@@ -128,6 +128,8 @@ def load(build: bool = True, path: str | None = None) -> ctypes.CDLL:
     for f in ("fse_tuning_save", "fse_tuning_load"):
         getattr(L, f).argtypes = [_vp, ctypes.c_char_p]
         getattr(L, f).restype = ctypes.c_int
+    L.fse_tuning_read.argtypes = [ctypes.c_char_p, ctypes.c_char_p, _vp]
+    L.fse_tuning_read.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -151,6 +153,18 @@ def partition(index, parts: int) -> np.ndarray:
     if rc != FSE_OK:
         raise FseError(rc, f"fse_partition(count={n}, parts={parts})")
     return starts
+
+
+def tuning_read(path: str, device: str):
+    """fse_tuning_read: the launch shapes a saved cache file holds for a device
+    name, without a context or a GPU.  Returns (entries read, shapes) with
+    shapes an int32 array [dtype, inv_var, class, (warps per CTA, warps per
+    stamp)], -1 where the file has no entry for that dtype and setting."""
+    shapes = np.zeros((2, 2, 7, 2), dtype=np.int32)
+    n = load().fse_tuning_read(os.fsencode(path), device.encode(), _vp(shapes.ctypes.data))
+    if n < 0:
+        raise FseError(-n, f"fse_tuning_read({path!r})")
+    return n, shapes
 
 
 def default_opts(**kw) -> Opts:

@@ -893,12 +893,11 @@ int fse_tuning_save(const fse_ctx* ctx, const char* path) {
     return FSE_OK;
 }
 
-int fse_tuning_load(fse_ctx* ctx, const char* path) {
-    if (!ctx || !path) return FSE_EINVAL;
-    char name[256];
-    if (!device_name(ctx->device, name, sizeof name)) return set_error(ctx, FSE_ECUDA, "device properties");
+int fse_tuning_read(const char* path, const char* device, int32_t* shapes) {
+    if (!path || !device || !shapes) return -FSE_EINVAL;
     FILE* f = fopen(path, "r");
-    if (!f) return set_error(ctx, FSE_EINVAL, "cannot read %s", path);
+    if (!f) return -FSE_EINVAL;
+    for (int i = 0; i < 2 * 2 * kK * 2; ++i) shapes[i] = -1;   // no entry
     char line[4096];
     bool format_ok = false;
     int applied = 0;
@@ -907,7 +906,7 @@ int fse_tuning_load(fse_ctx* ctx, const char* path) {
         if (json_str(line, "format", fmt, sizeof fmt)) format_ok = strcmp(fmt, kTuneFormat) == 0;
         char dev[256], dts[16];
         if (!format_ok || strncmp(line, "{\"device\": ", 11) != 0 || !json_str(line, "device", dev, sizeof dev) ||
-            strcmp(dev, name) != 0 || !json_str(line, "dtype", dts, sizeof dts))
+            strcmp(dev, device) != 0 || !json_str(line, "dtype", dts, sizeof dts))
             continue;
         long ivv[1], pix[kK], w[kK], nw[kK];
         if (json_ints(line, "inv_var", ivv, 1) != 1) {
@@ -934,13 +933,34 @@ int fse_tuning_load(fse_ctx* ctx, const char* path) {
         }
         if (!ok) continue;
         for (int k = 0; k < kK; ++k) {
-            ctx->tuned[dt][iv][k] = static_cast<int>(w[k]);
-            ctx->tuned_nw[dt][iv][k] = w[k] ? static_cast<int>(nw[k]) : 0;
+            int32_t* e = shapes + ((dt * 2 + iv) * kK + k) * 2;
+            e[0] = static_cast<int32_t>(w[k]);
+            e[1] = w[k] ? static_cast<int32_t>(nw[k]) : 0;
         }
         ++applied;
     }
     fclose(f);
-    if (!applied) return set_error(ctx, FSE_EINVAL, "%s holds no launch shapes for %s", path, name);
+    return applied;
+}
+
+int fse_tuning_load(fse_ctx* ctx, const char* path) {
+    if (!ctx || !path) return FSE_EINVAL;
+    char name[256];
+    if (!device_name(ctx->device, name, sizeof name)) return set_error(ctx, FSE_ECUDA, "device properties");
+    int32_t shapes[2 * 2 * kK * 2];
+    const int applied = fse_tuning_read(path, name, shapes);
+    if (applied < 0) return set_error(ctx, FSE_EINVAL, "cannot read %s", path);
+    if (applied == 0) return set_error(ctx, FSE_EINVAL, "%s holds no launch shapes for %s", path, name);
+    // settings absent from the file keep the context's shapes
+    for (int dt = 0; dt < 2; ++dt)
+        for (int iv = 0; iv < 2; ++iv) {
+            const int32_t* e = shapes + (dt * 2 + iv) * kK * 2;
+            if (e[0] < 0) continue;
+            for (int k = 0; k < kK; ++k) {
+                ctx->tuned[dt][iv][k] = e[2 * k];
+                ctx->tuned_nw[dt][iv][k] = e[2 * k + 1];
+            }
+        }
     ++ctx->tune_version;
     return FSE_OK;
 }
