@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(256) chi2_grad_kernel(GradArgs a) {
         // in flight.  Per lane the pixels are still taken in the order
         // q = lane, lane + 32, ..., so the sums do not change.
         constexpr int KB = 8;
-        PixelWalk pw(lane, ix.w);
+        FWalk pw(lane, ix.w);
         for (int q0 = lane; q0 < npix; q0 += 32 * KB) {
             float fv[KB], wv[KB];
 #pragma unroll
@@ -113,13 +113,14 @@ __global__ void __launch_bounds__(256) chi2_grad_kernel(GradArgs a) {
                     fv[j] = in ? __ldcs(pf + q) : 0.f;
                 wv[j] = IVAR ? (in ? __ldcs(iv + q) : 0.f) : 1.f;
             }
+            float cp = 0.f;   // this lane's chi^2 over the KB pixels, then one double-float add
 #pragma unroll
             for (int j = 0; j < KB; ++j) {
                 const int q = q0 + 32 * j;
                 if (q >= npix) continue;
                 const float f = fv[j];
-                const float t1 = static_cast<float>(pw.col) - x0;
-                const float t2 = static_cast<float>(pw.row) - y0;
+                const float t1 = pw.c - x0;
+                const float t2 = pw.r - y0;
                 pw.next();
                 const float tpa = fmaf(t1, cph, t2 * sph);
                 const float tpe = fmaf(t2, cph, -t1 * sph);
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(256) chi2_grad_kernel(GradArgs a) {
                 // which outputs were requested
                 const float res = fmaf(I0, E, -f);
                 const float wr = wgt * res;
-                df_add(ch[0], cl[0], __fmul_rn(wr, res));
+                cp += __fmul_rn(wr, res);
                 if (GRAD) {
                     const float c = 2.f * wr;
                     if (DPIX) __stcs(dp + q, __fmul_rn(-c, gof));
@@ -154,6 +155,7 @@ __global__ void __launch_bounds__(256) chi2_grad_kernel(GradArgs a) {
                     S[6] = fmaf(qv, tpa * tpe, S[6]);
                 }
             }
+            df_add(ch[0], cl[0], cp);
         }
         warp_allsum_df(ch, cl);
         if (GRAD) warp_allsum(S);

@@ -88,6 +88,28 @@ struct PixelWalk {
     }
 };
 
+// Pixel coordinates of p = t, t + 32, ... of a w-wide stamp as floats.  They
+// are integers, so every step is exact, and so is t = coordinate - centre.
+struct FWalk {
+    float c, r, dc, dr, wf;
+    __device__ FWalk(int t, int w) {
+        const int row = t / w;
+        c = static_cast<float>(t - row * w);
+        r = static_cast<float>(row);
+        dr = static_cast<float>(32 / w);
+        dc = static_cast<float>(32 - (32 / w) * w);
+        wf = static_cast<float>(w);
+    }
+    __device__ __forceinline__ void next() {
+        c += dc;
+        r += dr;
+        if (c >= wf) {
+            c -= wf;
+            r += 1.f;
+        }
+    }
+};
+
 // b(n), b'(n) in fp32 from a table of (b, b') at n = kBnLo + k kBnStep:
 // cubic Hermite interpolation for b; b' as the linear interpolation of the
 // node values of b' (error O(h^2 b''') ~ 1e-9).  Differentiating the

@@ -50,28 +50,6 @@ struct Geom {
     float A, B, G4, cw;      // R^2 = A t1^2 + B t2^2 - G4 t1 t2; W = 2^(cw R^2)
 };
 
-// Pixel coordinates of p = t, t + 32, ... of a w-wide stamp as floats.  They
-// are integers, so every step is exact, and so is t = coordinate - centre.
-struct FWalk {
-    float c, r, dc, dr, wf;
-    __device__ FWalk(int t, int w) {
-        const int row = t / w;
-        c = static_cast<float>(t - row * w);
-        r = static_cast<float>(row);
-        dr = static_cast<float>(32 / w);
-        dc = static_cast<float>(32 - (32 / w) * w);
-        wf = static_cast<float>(w);
-    }
-    __device__ __forceinline__ void next() {
-        c += dc;
-        r += dr;
-        if (c >= wf) {
-            c -= wf;
-            r += 1.f;
-        }
-    }
-};
-
 // Polynomial factors of degree <= 2 (coefficients of 1, t1, t2, t1^2, t1 t2,
 // t2^2) for J_kl = sum I W [a_l m_k + dm_k/dtheta_l]: m_k, a_l (the derivative
 // of log W: -R^2_l / 2 s^2, or R^2 / s^3 for sigma_w) and dm_k/dtheta_l.

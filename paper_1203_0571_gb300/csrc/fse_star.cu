@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(256) star_kernel(StarArgs a) {
             const float inv1g2 = om * om;
             const float sc = (DT == FSE_BF16 && a.scale) ? a.scale[si] : 1.f;
             bool fin = true;
-            PixelWalk pw(lane, ix.w);
+            FWalk pw(lane, ix.w);
             for (int p0 = lane; p0 < npix; p0 += 256) {
                 // eight loads in flight per lane before any is used
                 float v[8];
@@ -109,8 +109,8 @@ __global__ void __launch_bounds__(256) star_kernel(StarArgs a) {
                 for (int u = 0; u < 8; ++u) {
                     const int p = p0 + 32 * u;
                     if (p < npix) {
-                        const float t1 = static_cast<float>(pw.col) - mom.x0;
-                        const float t2 = static_cast<float>(pw.row) - mom.y0;
+                        const float t1 = pw.c - mom.x0;
+                        const float t2 = pw.r - mom.y0;
                         pw.next();
                         const float R2 = fmaf(A, t1 * t1, fmaf(B, t2 * t2, -G4 * (t1 * t2)));
                         sp[p] = make_float2(v[u], fmaxf(R2, 0.f) * inv1g2);
