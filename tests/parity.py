@@ -25,6 +25,12 @@ Every stamp of a comparison is accounted for, in exactly one class:
                  GPU's point is a fixed point (its moment step there below
                  1e-5, sigma_w held) and the oracle's own fit from the GPU's
                  moments agrees with the GPU's fit.  Otherwise a failure.
+  other_fixed_point
+                 the same without the clamp: both converged, at different
+                 centres or ellipticities, each a fixed point of Secs. 2-3 (at
+                 low SNR the iteration has several).  Confirmed as above, and
+                 allowed up to assert_gate's max_other_fixed_point (0 unless a
+                 test states otherwise).
   disagree       the two sides disagree on whether the moments, or the fit,
                  converged.  Each such stamp carries its reason:
                    oracle_*   the GPU converged and the oracle did not.  It is
@@ -172,12 +178,15 @@ def _gpu_short_reason(gs, fit_level):
 
 def compare(gpu, orc, keys=("x0", "y0", "e1", "e2", "re", "n", "flux", "chi2"), fit=True,
             O=None, batch=None, ids=None, ivar=None, supersample=1, ellip=True, sigw_mode=1,
-            orc_opts=None):
+            orc_opts=None, same_pixels=True):
     """Per-stamp errors, the class of every stamp and the gate verdict.  Returns a report.
 
     O, batch and ids (stamp j of gpu/orc is stamp ids[j] of batch) let the
     oracle check the exclusions; without them every exclusion that needs a
-    check counts as unconfirmed."""
+    check counts as unconfirmed.  same_pixels=False (the two sides measured
+    different pixels, e.g. bf16 storage against fp32) keeps every jointly
+    converged stamp in the gate: its differences are the measurement, not
+    another fixed point."""
     gs, os_ = gpu["status"].astype(np.int64), orc["status"].astype(np.int64)
     n = len(gs)
     mom_g, mom_o = (gs & MOM_CONVERGED) != 0, (os_ & MOM_CONVERGED) != 0
@@ -226,14 +235,13 @@ def compare(gpu, orc, keys=("x0", "y0", "e1", "e2", "re", "n", "flux", "chi2"), 
     # both converged at the sub-pixel weight clamp, on different fixed points
     mkeys = [k for k in ("x0", "y0", "e1", "e2") if k in keys]
     for j in np.nonzero(conv)[0]:
-        if klass[j] not in ("gated", "other_minimum") or not mkeys:
+        if klass[j] not in ("gated", "other_minimum") or not mkeys or not same_pixels:
             continue
         if all(err[k][j] <= TOL[k] for k in mkeys):
             continue
-        if not (_clamped_low(gpu[j]) and _clamped_low(orc[j])):
-            continue
-        klass[j] = "clamped_fixed_point"
-        reason[j] = "clamped_fixed_point"
+        kind = "clamped_fixed_point" if _clamped_low(gpu[j]) and _clamped_low(orc[j]) else "other_fixed_point"
+        klass[j] = kind
+        reason[j] = kind
         confirmed[j] = False
         if not checkable:
             continue
@@ -292,7 +300,8 @@ def compare(gpu, orc, keys=("x0", "y0", "e1", "e2", "re", "n", "flux", "chi2"), 
     within = gate & ok
     gpu_short = np.array([r.startswith("gpu_") for r in reason], bool)
     subpixel = np.array([r.startswith("subpixel_") for r in reason], bool)
-    unconfirmed = (np.isin(klass, ["other_minimum", "disagree", "clamped_fixed_point"]) & ~confirmed & ~gpu_short
+    unconfirmed = (np.isin(klass, ["other_minimum", "disagree", "clamped_fixed_point", "other_fixed_point"])
+                   & ~confirmed & ~gpu_short
                    & ~subpixel)
     counts = {}
     for j in range(n):
@@ -307,6 +316,7 @@ def compare(gpu, orc, keys=("x0", "y0", "e1", "e2", "re", "n", "flux", "chi2"), 
         "excluded_condition": int((klass == "cond").sum()),
         "excluded_other_minimum": int(((klass == "other_minimum") & confirmed).sum()),
         "excluded_clamped_fixed_point": int(((klass == "clamped_fixed_point") & confirmed).sum()),
+        "excluded_other_fixed_point": int(((klass == "other_fixed_point") & confirmed).sum()),
         "disagree_confirmed": int(((klass == "disagree") & confirmed).sum()),
         "gpu_short": int(gpu_short.sum()),
         "subpixel": int(subpixel.sum()),
@@ -318,7 +328,8 @@ def compare(gpu, orc, keys=("x0", "y0", "e1", "e2", "re", "n", "flux", "chi2"), 
         "p99_err": {k: float(np.percentile(err[k][gate], 99)) if gate.any() else 0.0 for k in keys},
         "failing": [int(j) for j in np.nonzero(gate & ~ok)[0][:50]],
     }
-    listed = np.nonzero((gate & ~ok) | np.isin(klass, ["other_minimum", "disagree", "cond", "clamped_fixed_point"]))[0]
+    listed = np.nonzero((gate & ~ok) | np.isin(klass, ["other_minimum", "disagree", "cond", "clamped_fixed_point",
+                                                       "other_fixed_point"]))[0]
     rep["detail"] = [{"j": int(j), "id": int(ids[j]) if ids is not None else int(j),
                       "class": str(klass[j]), "reason": reason[j], "confirmed": bool(confirmed[j]),
                       **extra[j],
@@ -334,21 +345,25 @@ def summary(rep: dict) -> dict:
     return {k: v for k, v in rep.items() if not k.startswith("_") and k != "detail"}
 
 
-def assert_gate(rep: dict, max_gpu_short: int = 0, min_gated: float = 0.5, max_subpixel: int = 0):
+def assert_gate(rep: dict, max_gpu_short: int = 0, min_gated: float = 0.5, max_subpixel: int = 0,
+                max_other_fixed_point: int = 0):
     """Every gated stamp within tolerance; every exclusion confirmed by the
     oracle; at most max_gpu_short stamps that the oracle converged and the GPU
-    did not, and at most max_subpixel disagreements at the sub-pixel weight
-    clamp (each listed in the report with its reason); and, as a guard
-    against a gate that excludes everything, at least min_gated of the stamps
-    gated."""
+    did not, at most max_subpixel disagreements at the sub-pixel weight clamp
+    and at most max_other_fixed_point other fixed points (each listed in the
+    report with its reason); and, as a guard against a gate that excludes
+    everything, at least min_gated of the stamps gated."""
     s = summary(rep)
-    bad = [d for d in rep["detail"] if d["class"] in ("other_minimum", "disagree", "clamped_fixed_point")
+    bad = [d for d in rep["detail"] if d["class"] in ("other_minimum", "disagree", "clamped_fixed_point",
+                                                      "other_fixed_point")
            and not d["confirmed"] and not d["reason"].startswith(("gpu_", "subpixel_"))]
     assert rep["unconfirmed"] == 0, (s, bad[:5])
     short = [d for d in rep["detail"] if d["reason"].startswith("gpu_")]
     assert rep["gpu_short"] <= max_gpu_short, (s, short[:10])
     sub = [d for d in rep["detail"] if d["reason"].startswith("subpixel_")]
     assert rep["subpixel"] <= max_subpixel, (s, sub[:10])
+    other = [d for d in rep["detail"] if d["class"] == "other_fixed_point"]
+    assert rep["excluded_other_fixed_point"] <= max_other_fixed_point, (s, other[:10])
     assert rep["within_tolerance"] == rep["gated"], (rep["failing"], rep["max_err"], s)
     assert rep["gated"] >= min_gated * rep["n"], s
 

@@ -56,9 +56,12 @@ def errors(g, o, O, batch, same_pixels=True):
     # on different pixels (storage error) chi^2 values are not comparable, and
     # neither is the "lower chi^2 means another basin" exclusion built on them
     keys = KEYS if same_pixels else tuple(k for k in KEYS if k != "chi2")
-    rep = PR.compare(g, o, keys=keys, O=O, batch=batch, ids=np.arange(batch.count))
+    rep = PR.compare(g, o, keys=keys, O=O, batch=batch, ids=np.arange(batch.count), same_pixels=same_pixels)
     gate = rep["_gate"]
-    row = {"gated": int(gate.sum()), "total": int(gate.size)}
+    row = {"gated": int(gate.sum()), "total": int(gate.size), "reasons": dict(rep["reasons"]),
+           "excluded": {k: rep[k] for k in ("excluded_condition", "excluded_other_minimum",
+                                             "excluded_clamped_fixed_point", "excluded_other_fixed_point",
+                                             "gpu_short", "subpixel", "unconfirmed")}}
     for k in keys:
         e = rep["_err"][k][gate]
         row[k] = {"median": float(np.median(e)) if e.size else 0.0,
@@ -118,6 +121,10 @@ def markdown(rep) -> str:
             lines.append(f"| {lab} — {stat} | {r['gated']}/{r['total']} | " + " | ".join(cells) + " |")
     s = rep["oracle_sigma_median"]
     lines += ["", f"Median 1-sigma statistical error (oracle J^T J): r_e {s['re']:.1e} relative, n {s['n']:.1e} relative."]
+    for name in ("fp32", "bf16_compute"):
+        ex = rep[name]["reasons"]
+        lines.append(f"Outside the gate ({name}), by reason: " +
+                     (", ".join(f"{k} {v}" for k, v in sorted(ex.items())) or "none") + ".")
     return "\n".join(lines)
 
 
