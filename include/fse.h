@@ -356,7 +356,13 @@ int fse_star_fit(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
  * FSE_ST_NONFINITE, FSE_ST_BAD_SIZE (h*w above FSE_MAX_PIX: nothing written),
  * FSE_ST_FIT_SINGULAR (J singular); such stamps get zero derivatives.
  * bf16 pixels are decoded with scale[s]; the derivatives are with respect to
- * the decoded intensities.  Device pointers; asynchronous on `stream`. */
+ * the decoded intensities.  Device pointers; asynchronous on `stream`.  The
+ * VJP runs two launches: one per stamp for the sums, J and the solve, which
+ * writes 96 bytes of coefficients per stamp to a grow-only scratch buffer of
+ * the context (allocated, with a device synchronisation, when a call has more
+ * stamps than any before: not under stream capture); then one that writes
+ * dL/dI from them.  VJP calls on one context that overlap on the GPU share the
+ * scratch. */
 int fse_moment_vjp(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
                    const fse_stamp *idx, int64_t count, const fse_result *moments, int mode,
                    const float *v, float *dpix, uint32_t *status, void *stream);

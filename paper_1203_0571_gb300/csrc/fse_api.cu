@@ -60,6 +60,9 @@ struct fse_ctx {
     int32_t* d_perm = nullptr;
     size_t perm_cap = 0;
     unsigned int* d_cls = nullptr;
+    // grow-only per-stamp coefficients of fse_moment_vjp
+    fse::VjpCoef* d_vjp = nullptr;
+    size_t vjp_cap = 0;
     // warps per CTA chosen by fse_autotune, by dtype, inverse variance and size
     // class (0 = library default)
     int tuned[2][2][fse::kClasses] = {};
@@ -462,6 +465,7 @@ void fse_destroy(fse_ctx* ctx) {
         cudaFree(ctx->d_ivar);
         cudaFree(ctx->d_perm);
         cudaFree(ctx->d_cls);
+        cudaFree(ctx->d_vjp);
         if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
         if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
         if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -1069,6 +1073,12 @@ static int moment_grad(fse_ctx* ctx, bool jvp, const void* pix, int dtype, const
     a.tangent = tangent;
     a.dtheta = dtheta;
     a.status = status;
+    if (!jvp) {
+        // the analysis kernel's per-stamp coefficients for the write kernel
+        const int rc = grow(ctx, &ctx->d_vjp, &ctx->vjp_cap, static_cast<size_t>(count));
+        if (rc) return rc;
+        a.coef = ctx->d_vjp;
+    }
     a.queue = ctx->d_queue + (ctx->next_queue++ % kQueues);
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), st);

@@ -107,6 +107,18 @@ struct StarArgs {
 
 // Arguments of the implicit-gradient kernel of the moment fixed point
 // (fse_moment_vjp / fse_moment_jvp).
+// Per-stamp coefficients of the VJP's pixel gradient, dL/dI_p =
+// -W(p) (c0 + c1 t1 + c2 t2 + c3 t1^2 + c4 t1 t2 + c5 t2^2) + the growth
+// curve's ring term, written by the analysis kernel for the write kernel.
+struct VjpCoef {
+    float x0, y0, A, B, G4, cw;   // the weight at the fixed point
+    float c[6];
+    float kc_in, kc_ring, kc_out; // kappa d sigma_w / d I_p inside, on and outside the crossing ring
+    float pc, pr, km2, k2;        // brightest pixel; (k-1)^2 (or -1) and k^2 of the crossing ring
+    int ring, ok;
+    float pad[3];                 // 96 bytes
+};
+
 struct MomentGradArgs {
     const void* pix;
     int dtype;
@@ -121,6 +133,7 @@ struct MomentGradArgs {
     float* dtheta;               // JVP: count x 5
     uint32_t* status;            // count, or NULL
     unsigned int* queue;         // work counter (zeroed before launch)
+    VjpCoef* coef;               // VJP: count per-stamp coefficients (scratch)
 };
 
 // Arguments of the cut-out launches (fse_cutout, Sec. 4.1).

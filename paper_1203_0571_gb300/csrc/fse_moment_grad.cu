@@ -527,47 +527,84 @@ __global__ void __launch_bounds__(256, 2) moment_grad_kernel(MomentGradArgs a) {
                 if (lane == i && status == 0) val = xs[i];
             if (lane < 5) a.dtheta[si * 5 + lane] = val;
         } else {
-            // dL/dI_p = -W(p) sum_k lambda_k m_k(p) + kappa d sigma_w / d I_p
-            float c[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            float kc_in = 0.f, kc_ring = 0.f, kc_out = 0.f;
+            // dL/dI_p = -W(p) sum_k lambda_k m_k(p) + kappa d sigma_w / d I_p:
+            // the per-stamp coefficients, for the write kernel
+            VjpCoef cf;
+            cf.x0 = q.x0;
+            cf.y0 = q.y0;
+            cf.A = q.A;
+            cf.B = q.B;
+            cf.G4 = q.G4;
+            cf.cw = q.cw;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) cf.c[i] = 0.f;
+            cf.kc_in = cf.kc_ring = cf.kc_out = 0.f;
+            cf.pc = static_cast<float>(rg.pc);
+            cf.pr = static_cast<float>(rg.pr);
+            cf.km2 = rg.k >= 1 ? static_cast<float>((rg.k - 1) * (rg.k - 1)) : -1.f;
+            cf.k2 = static_cast<float>(rg.k * rg.k);
+            cf.ring = rg.on && status == 0;
+            cf.ok = status == 0;
             if (status == 0) {
                 const float gg = q.g1 * q.g1 + q.g2 * q.g2;
                 const float ew1 = 2.f * q.g1 / (1.f + gg), ew2 = 2.f * q.g2 / (1.f + gg);
-                c[0] = -xs[4] * q.s * q.s;
-                c[1] = xs[0];
-                c[2] = xs[1];
-                c[3] = xs[2] * (1.f - ew1) - xs[3] * ew2 + xs[4] * q.A;
-                c[4] = 2.f * xs[3] - xs[4] * q.G4;
-                c[5] = -xs[2] * (1.f + ew1) - xs[3] * ew2 + xs[4] * q.B;
+                cf.c[0] = -xs[4] * q.s * q.s;
+                cf.c[1] = xs[0];
+                cf.c[2] = xs[1];
+                cf.c[3] = xs[2] * (1.f - ew1) - xs[3] * ew2 + xs[4] * q.A;
+                cf.c[4] = 2.f * xs[3] - xs[4] * q.G4;
+                cf.c[5] = -xs[2] * (1.f + ew1) - xs[3] * ew2 + xs[4] * q.B;
                 if (rg.on) {
                     float kappa = a.v[si * 5 + 4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) kappa = fmaf(-xs[i], Jcol4[i], kappa);
-                    kc_in = kappa * rg.c_in;
-                    kc_ring = kappa * rg.c_ring;
-                    kc_out = kappa * rg.c_out;
+                    cf.kc_in = kappa * rg.c_in;
+                    cf.kc_ring = kappa * rg.c_ring;
+                    cf.kc_out = kappa * rg.c_out;
                 }
             }
-            FWalk pw(lane, ix.w);
-            const float pcf = static_cast<float>(rg.pc), prf = static_cast<float>(rg.pr);
-            const float km2 = rg.k >= 1 ? static_cast<float>((rg.k - 1) * (rg.k - 1)) : -1.f;
-            const float k2 = static_cast<float>(rg.k * rg.k);
-            for (int p = lane; p < npix; p += 32) {
-                const float t1 = pw.c - q.x0, t2 = pw.r - q.y0;
-                const float R2 = fmaf(q.A, t1 * t1, fmaf(q.B, t2 * t2, -q.G4 * (t1 * t2)));
-                const float W = ex2(R2 * q.cw);
-                const float Q = fmaf(t1, fmaf(c[3], t1, fmaf(c[4], t2, c[1])), fmaf(t2, fmaf(c[5], t2, c[2]), c[0]));
-                float g = -W * Q;
-                if (rg.on) {
-                    const float dj = pw.c - pcf, di = pw.r - prf;
-                    const float d2 = fmaf(di, di, dj * dj);
-                    g += d2 <= km2 ? kc_in : (d2 <= k2 ? kc_ring : kc_out);
-                }
-                pw.next();
-                __stcs(a.dpix + ix.offset + p, status == 0 ? g : 0.f);
-            }
+            if (lane == 0) a.coef[si] = cf;
         }
         if (lane == 0 && a.status) a.status[si] = status;
+    }
+}
+
+// The VJP's pixel gradient from the per-stamp coefficients: it depends on
+// the pixels only through the coefficients, so this pass reads none and
+// streams the writes.  One warp per stamp, stamps in grid-stride order;
+// stamps of invalid size are left unwritten, like the analysis kernel
+// leaves them; a stamp without a solution gets zeros.
+__global__ void __launch_bounds__(256) moment_vjp_write_kernel(MomentGradArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t si = gw; si < a.count; si += nw) {
+        const fse_stamp ix = a.idx[si];
+        const long long npl = static_cast<long long>(ix.h) * ix.w;
+        if (ix.h < 1 || ix.w < 1 || npl > FSE_MAX_PIX) continue;
+        const int npix = static_cast<int>(npl);
+        const VjpCoef cf = a.coef[si];
+        float* out = a.dpix + ix.offset;
+        if (!cf.ok) {
+            for (int p = lane; p < npix; p += 32) __stcs(out + p, 0.f);
+            continue;
+        }
+        FWalk pw(lane, ix.w);
+        for (int p = lane; p < npix; p += 32) {
+            const float t1 = pw.c - cf.x0, t2 = pw.r - cf.y0;
+            const float R2 = fmaf(cf.A, t1 * t1, fmaf(cf.B, t2 * t2, -cf.G4 * (t1 * t2)));
+            const float W = ex2(R2 * cf.cw);
+            const float Q = fmaf(t1, fmaf(cf.c[3], t1, fmaf(cf.c[4], t2, cf.c[1])),
+                                 fmaf(t2, fmaf(cf.c[5], t2, cf.c[2]), cf.c[0]));
+            float g = -W * Q;
+            if (cf.ring) {
+                const float dj = pw.c - cf.pc, di = pw.r - cf.pr;
+                const float d2 = fmaf(di, di, dj * dj);
+                g += d2 <= cf.km2 ? cf.kc_in : (d2 <= cf.k2 ? cf.kc_ring : cf.kc_out);
+            }
+            pw.next();
+            __stcs(out + p, g);
+        }
     }
 }
 
@@ -587,6 +624,12 @@ cudaError_t launch_t(const MomentGradArgs& a, cudaStream_t stream) {
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     kern<<<static_cast<unsigned>(grid), 256, 0, stream>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || JVP) return e;
+    long long wgrid = (a.count + 7) / 8;          // eight stamps (warps) per CTA
+    const long long wcap = static_cast<long long>(sms) * 8;
+    if (wgrid > wcap) wgrid = wcap;
+    moment_vjp_write_kernel<<<static_cast<unsigned>(wgrid), 256, 0, stream>>>(a);
     return cudaGetLastError();
 }
 
