@@ -27,6 +27,7 @@ namespace {
 constexpr float kPiF = 3.14159265358979f;
 constexpr float kSqrt2Ln2F = 1.17741002f;
 constexpr float kLn2F = 0.693147181f;
+constexpr float kWeightCutF = 7.4446500f;   // sqrt(80 ln 2): W = exp(-r^2/2 s_w^2) = 2^-40 at r = this s_w
 
 __host__ __device__ inline size_t star_warp_bytes(int max_pix) {
     return static_cast<size_t>(max_pix) * sizeof(float2);
@@ -130,9 +131,26 @@ __global__ void __launch_bounds__(256) star_kernel(StarArgs a) {
             int it;
             for (it = 1; it <= a.max_iter; ++it) {
                 float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
-                const float c = PROF == FSE_STAR_GAUSS ? -kLog2e / (2.f * sw * sw) : 1.f / (sw * sw);
-                int p = lane;
-                for (; p + 224 < npix; p += 256) {
+                const float isw2 = 1.f / (sw * sw);
+                const float c = PROF == FSE_STAR_GAUSS ? -0.5f * kLog2e * isw2 : isw2;
+                // The Gaussian weight: only the rows whose pixels can have
+                // W >= 2^-40 (r^2 <= 80 ln 2 s_w^2, i.e. R(g)^2 <= that times
+                // (1-|g|)^2, an ellipse within |t2| <= rho sqrt(A) / (1-|g|^2)),
+                // with a row of margin; the rows left out add less than
+                // 2^-40 |I| r^k each.  The Moffat weight falls as r^-6 and
+                // takes every pixel.
+                int p = lane, pend = npix;
+                if (PROF == FSE_STAR_GAUSS) {
+                    const float rho = kWeightCutF * sw * (1.f - gabs);
+                    const float hy = fminf(rho * sqrtf(1.f + gg - 2.f * g1) / (1.f - gg) + 1.f, 4096.f);
+                    const int r0 = max(0, static_cast<int>(floorf(mom.y0 - hy)));
+                    const int r1 = min(ix.h - 1, static_cast<int>(ceilf(mom.y0 + hy)));
+                    if (r1 >= r0 && hy > 0.f) {
+                        p = r0 * ix.w + lane;
+                        pend = (r1 + 1) * ix.w;
+                    }
+                }
+                for (; p + 224 < pend; p += 256) {
                     // eight pixels in two interleaved fp32 chains
                     float a0 = 0.f, a1 = 0.f, a2 = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f;
 #pragma unroll
@@ -146,7 +164,7 @@ __global__ void __launch_bounds__(256) star_kernel(StarArgs a) {
                 }
                 {
                     float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-                    for (; p < npix; p += 32) star_pixel<PROF>(sp[p], c, a0, a1, a2);
+                    for (; p < pend; p += 32) star_pixel<PROF>(sp[p], c, a0, a1, a2);
                     df_add(hi[0], lo[0], a0);
                     df_add(hi[1], lo[1], a1);
                     if (PROF == FSE_STAR_MOFFAT) df_add(hi[2], lo[2], a2);
@@ -164,8 +182,9 @@ __global__ void __launch_bounds__(256) star_kernel(StarArgs a) {
                     res.status |= FSE_ST_MOM_FAILED;
                     break;
                 }
+                const float ir0 = 1.f / r0;
                 if (PROF == FSE_STAR_GAUSS) {
-                    size = sqrtf(r2 / r0);
+                    size = sqrtf(r2 * ir0);
                 } else {
                     const float ratio = r4 * r0 / (2.f * r2 * r2);
                     if (!(ratio > 1.f)) {
@@ -173,13 +192,13 @@ __global__ void __launch_bounds__(256) star_kernel(StarArgs a) {
                         break;
                     }
                     beta = 1.f / (ratio - 1.f);
-                    size = sqrtf(r2 / r0 * (beta + 1.f));
+                    size = sqrtf(r2 * ir0 * (beta + 1.f));
                 }
                 if (!isfinite(size) || !(size > 0.f)) {
                     res.status |= FSE_ST_MOM_FAILED;
                     break;
                 }
-                const float step = fabsf(size / sw - 1.f);
+                const float step = fabsf(__fdividef(size, sw) - 1.f);
                 sw = size;
                 if (step <= a.tol) {
                     res.status |= FSE_ST_MOM_CONVERGED;
