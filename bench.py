@@ -45,12 +45,13 @@ OPS_FIT_SETUP = 8 + 26  # 0.5 log2 R^2 per pixel + the four-candidate start pass
 OPS_FIT = 18           # one profile pass (10 sums, 2 ex2)
 OPS_REFINE = 61        # one fit refinement pass (two ~1-ulp exp2, double-float gradient and chi^2
                        # sums, fp32 J^T J and curvature sums)
-# The per-pass figures of the survey's roofline: a moment pass 1 ex2 + ~30 fp32
-# operations, a fit pass 3 MUFU + ~30; every pixel pass the kernels run counts
-# once at these rates (the start-up and the refinement passes included, the
-# four-candidate fit start as one fit pass).
-SURVEY_MOMENT = 31
-SURVEY_FIT = 33
+# The nominal per-pass figures (the "frac_survey" accounting): a moment pass
+# 1 ex2 + ~30 fp32 operations, a fit pass 3 MUFU + ~30; every pixel pass the
+# kernels run counts once at these rates over the whole stamp (the start-up
+# and the refinement passes included, the four-candidate fit start as one fit
+# pass).
+NOMINAL_MOMENT = 31
+NOMINAL_FIT = 33
 SMS = 152
 LANES_PER_SM = 128
 
@@ -120,13 +121,13 @@ def algorithmic_ops(res, h: int = 48, w: int = 48) -> float:
     return float(ops.sum())
 
 
-def survey_ops(res) -> float:
-    """The survey's count: every pass at 31 (moment kind) or 33 (fit kind) per
+def nominal_ops(res) -> float:
+    """The nominal count: every pass at 31 (moment kind) or 33 (fit kind) per
     pixel of the whole stamp (the method's nominal work; the kernels visit
     fewer pixels in the moment passes)."""
     c = pass_counts(res)
-    per_px = (SURVEY_MOMENT * (c["init"] + c["mom4"] + c["mom"] + c["mom_refine"]) +
-              SURVEY_FIT * (c["fit_start"] + c["fit"] + c["fit_refine"]))
+    per_px = (NOMINAL_MOMENT * (c["init"] + c["mom4"] + c["mom"] + c["mom_refine"]) +
+              NOMINAL_FIT * (c["fit_start"] + c["fit"] + c["fit_refine"]))
     return float((res["npix"].astype(np.float64) * per_px).sum())
 
 
@@ -429,7 +430,7 @@ def main():
     ms = max_over_ranks(total_ms / args.steps, f"cuda:{local}")
     res = B.results(out)
     ops = algorithmic_ops(res)
-    sops = survey_ops(res)
+    sops = nominal_ops(res)
     kernel_ms = statistics.mean(step_ms)
     peak_gops = SMS * LANES_PER_SM * 2070.0 * 1e6 / 1e9     # at the maximum SM clock
     achieved = ops / (kernel_ms / 1e3) / 1e9
