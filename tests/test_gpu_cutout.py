@@ -113,6 +113,35 @@ def test_cutout_ragged_and_corners(ctx, O):
         assert inf["status"][7] == ST["INIT_FALLBACK"]
 
 
+def test_cutout_long_images(ctx, O):
+    """Images with a side above 32768 pixels take the 64-bit ring arithmetic,
+    narrower ones the 32-bit form; both against the oracle, with the bump near
+    the middle and near an end."""
+    rng = np.random.default_rng(9)
+    shapes = [(1, 40000), (40000, 1), (3, 33000), (33000, 2), (2, 20000), (20000, 3)]
+    imgs, offs, hs, ws = [], [], [], []
+    pos = 0
+    for k, (h, w) in enumerate(shapes):
+        yy, xx = np.mgrid[0:h, 0:w].astype(np.float64)
+        along = xx if w >= h else yy
+        c = (0.37 * max(h, w)) if k % 2 == 0 else (max(h, w) - 4.2)
+        sig = rng.uniform(1.5, 4.0)
+        I = 100.0 * np.exp(-(along - c) ** 2 / (2 * sig * sig)) + rng.normal(0, 0.5, (h, w))
+        imgs.append(I.astype(np.float32).ravel())
+        offs.append(pos)
+        hs.append(h)
+        ws.append(w)
+        pos += h * w
+    batch = synth.StampBatch(pix=torch.as_tensor(np.concatenate(imgs)), offset=torch.as_tensor(offs),
+                             h=torch.as_tensor(hs, dtype=torch.int32), w=torch.as_tensor(ws, dtype=torch.int32),
+                             truth={}).to("cuda")
+    idx = B.make_index(batch.offset, batch.h, batch.w)
+    pix, cidx, info = ctx.cutout(batch.pix, idx)
+    torch.cuda.synchronize()
+    inf = check_against_oracle(O, batch, pix, cidx, info)
+    assert np.all(inf["status"] == 0), inf["status"]
+
+
 def test_cutout_bf16(ctx, O):
     """bf16 images with a per-image scale: the growth curve on the decoded
     values; the cut-out copies the stored bf16 values."""
