@@ -60,9 +60,12 @@ struct fse_ctx {
     int32_t* d_perm = nullptr;
     size_t perm_cap = 0;
     unsigned int* d_cls = nullptr;
-    // grow-only per-stamp coefficients of fse_moment_vjp
+    // grow-only per-stamp coefficients of fse_moment_vjp, and growth-curve
+    // records of fse_moment_vjp / _jvp
     fse::VjpCoef* d_vjp = nullptr;
     size_t vjp_cap = 0;
+    fse::R50Grad* d_r50 = nullptr;
+    size_t r50_cap = 0;
     // warps per CTA chosen by fse_autotune, by dtype, inverse variance and size
     // class (0 = library default)
     int tuned[2][2][fse::kClasses] = {};
@@ -466,6 +469,7 @@ void fse_destroy(fse_ctx* ctx) {
         cudaFree(ctx->d_perm);
         cudaFree(ctx->d_cls);
         cudaFree(ctx->d_vjp);
+        cudaFree(ctx->d_r50);
         if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
         if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
         if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -1078,6 +1082,12 @@ static int moment_grad(fse_ctx* ctx, bool jvp, const void* pix, int dtype, const
         const int rc = grow(ctx, &ctx->d_vjp, &ctx->vjp_cap, static_cast<size_t>(count));
         if (rc) return rc;
         a.coef = ctx->d_vjp;
+    }
+    if (mode & FSE_MOM_SIGW_R50) {
+        // the ring launch's growth-curve records for the analysis kernel
+        const int rc = grow(ctx, &ctx->d_r50, &ctx->r50_cap, static_cast<size_t>(count));
+        if (rc) return rc;
+        a.r50g = ctx->d_r50;
     }
     a.queue = ctx->d_queue + (ctx->next_queue++ % kQueues);
     const cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -107,6 +107,19 @@ struct StarArgs {
 
 // Arguments of the implicit-gradient kernel of the moment fixed point
 // (fse_moment_vjp / fse_moment_jvp).
+// The growth curve of the start-up (Sec. 4.1) around the brightest pixel, for
+// d sigma_w / d I: the crossing ring k (the first whose enclosed sum reaches
+// half the total) and the constants of d sigma_w / d I_p in the three regions
+// d <= k-1, k-1 < d <= k and d > k; for the JVP the tangent's sums over the
+// two discs.  Written per stamp by the ring launch of the moment gradient.
+struct R50Grad {
+    int on;                  // sigma_w depends on the pixels
+    int pr, pc, k;
+    float c_in, c_ring, c_out;
+    float u_in, u_disc;      // JVP: tangent summed over d <= k-1 and d <= k
+    float pad[3];            // 48 bytes
+};
+
 // Per-stamp coefficients of the VJP's pixel gradient, dL/dI_p =
 // -W(p) (c0 + c1 t1 + c2 t2 + c3 t1^2 + c4 t1 t2 + c5 t2^2) + the growth
 // curve's ring term, written by the analysis kernel for the write kernel.
@@ -134,6 +147,7 @@ struct MomentGradArgs {
     uint32_t* status;            // count, or NULL
     unsigned int* queue;         // work counter (zeroed before launch)
     VjpCoef* coef;               // VJP: count per-stamp coefficients (scratch)
+    R50Grad* r50g;               // FSE_MOM_SIGW_R50: count growth-curve records (scratch)
 };
 
 // Arguments of the cut-out launches (fse_cutout, Sec. 4.1).

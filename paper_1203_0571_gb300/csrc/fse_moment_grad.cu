@@ -195,18 +195,12 @@ __device__ bool solve5(float X[25], float r[5], float x[5]) {
 // k-1 < d <= k and d > k.  The disc sums are double-float, so k is the
 // start-up's own except where an enclosed sum lies within ~1e-13 of half the
 // total.  For the JVP the tangent's sums over the two discs come with them.
-struct R50Grad {
-    bool on;                 // sigma_w depends on the pixels
-    int pr, pc, k;
-    float c_in, c_ring, c_out;
-    float u_in, u_disc;      // JVP: tangent summed over d <= k-1 and d <= k
-};
 
 template <int DT, bool JVP>
 __device__ R50Grad r50_ring(const MomentGradArgs& a, const fse_stamp& ix, int npix, float sc, float r50_hint,
                             int peak, float tot_h, float tot_l, int lane) {
     R50Grad o;
-    o.on = false;
+    o.on = 0;
     o.pr = peak / ix.w;
     o.pc = peak - o.pr * ix.w;
     o.k = 0;
@@ -257,7 +251,7 @@ __device__ R50Grad r50_ring(const MomentGradArgs& a, const fse_stamp& ix, int np
             --k;
         } else {
             o.k = k;
-            o.on = true;
+            o.on = 1;
             o.u_in = h[2] + l[2];
             o.u_disc = h[3] + l[3];
             if (k == 0) {
@@ -367,8 +361,6 @@ __global__ void __launch_bounds__(256, 2) moment_grad_kernel(MomentGradArgs a) {
         for (int i = 0; i < 15; ++i) Mh[i] = Ml[i] = 0.f;
 #pragma unroll
         for (int i = 0; i < 7; ++i) Uh[i] = Ul[i] = 0.f;
-        float vmax = -INFINITY, th_ = 0.f, tl_ = 0.f;
-        int imax = 0x7fffffff;
         if (status == 0) {
             FWalk pw(lane, ix.w);
             int p0 = lane;
@@ -387,10 +379,6 @@ __global__ void __launch_bounds__(256, 2) moment_grad_kernel(MomentGradArgs a) {
                 }
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    if (sig_r50) {
-                        if (v[u] > vmax) { vmax = v[u]; imax = p0 + 32 * u; }
-                        ptot += v[u];
-                    }
                     moment_terms<JVP>(q, pw.c - q.x0, pw.r - q.y0, v[u], JVP ? uu[u] : 0.f, P, PU);
                     pw.next();
                 }
@@ -400,7 +388,6 @@ __global__ void __launch_bounds__(256, 2) moment_grad_kernel(MomentGradArgs a) {
 #pragma unroll
                     for (int i = 0; i < 7; ++i) df_add(Uh[i], Ul[i], PU[i]);
                 }
-                if (sig_r50) df_add(th_, tl_, ptot);
             }
             {
                 float P[15], PU[7], ptot = 0.f;
@@ -411,10 +398,6 @@ __global__ void __launch_bounds__(256, 2) moment_grad_kernel(MomentGradArgs a) {
                 for (int p = p0; p < npix; p += 32) {
                     const float v = load_pix<DT>(a, ix.offset + p, sc);
                     const float uu = JVP ? __ldg(a.tangent + ix.offset + p) : 0.f;
-                    if (sig_r50) {
-                        if (v > vmax) { vmax = v; imax = p; }
-                        ptot += v;
-                    }
                     moment_terms<JVP>(q, pw.c - q.x0, pw.r - q.y0, v, uu, P, PU);
                     pw.next();
                 }
@@ -424,11 +407,10 @@ __global__ void __launch_bounds__(256, 2) moment_grad_kernel(MomentGradArgs a) {
 #pragma unroll
                     for (int i = 0; i < 7; ++i) df_add(Uh[i], Ul[i], PU[i]);
                 }
-                if (sig_r50) df_add(th_, tl_, ptot);
             }
             // a NaN or Inf pixel (or tangent) makes I W (u W) non-finite
             // whatever its weight, and with it the warp's total
-            float chk = (Mh[0] + Ml[0]) + (JVP ? Uh[6] + Uh[0] : 0.f) + (sig_r50 ? th_ : 0.f);
+            float chk = (Mh[0] + Ml[0]) + (JVP ? Uh[6] + Uh[0] : 0.f);
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) chk += __shfl_xor_sync(kFull, chk, off);
             finite = isfinite(chk);
@@ -443,22 +425,12 @@ __global__ void __launch_bounds__(256, 2) moment_grad_kernel(MomentGradArgs a) {
                 for (int i = 0; i < 7; ++i) Su[i] = Uh[i] + Ul[i];
             }
         }
-        // pass 2 (growth-curve sigma_w): the crossing ring around the brightest pixel
+        // the growth curve's crossing ring and constants, from the ring launch
         R50Grad rg;
-        rg.on = false;
+        rg.on = 0;
         rg.pr = rg.pc = rg.k = 0;
         rg.c_in = rg.c_ring = rg.c_out = rg.u_in = rg.u_disc = 0.f;
-        if (status == 0 && sig_r50) {
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const float ov = __shfl_xor_sync(kFull, vmax, off);
-                const int oi = __shfl_xor_sync(kFull, imax, off);
-                if (ov > vmax || (ov == vmax && oi < imax)) { vmax = ov; imax = oi; }
-            }
-            float t2h[1] = {th_}, t2l[1] = {tl_};
-            warp_allsum_df(t2h, t2l);
-            rg = r50_ring<DT, JVP>(a, ix, npix, sc, mom.r50, imax, t2h[0], t2l[0], lane);
-        }
+        if (status == 0 && sig_r50) rg = a.r50g[si];
         // J: lane 5k + l assembles J_kl; then every lane holds all 25
         float X[25], xs[5], rhs[5];
         bool solved = false;
@@ -569,6 +541,72 @@ __global__ void __launch_bounds__(256, 2) moment_grad_kernel(MomentGradArgs a) {
     }
 }
 
+// The growth curve of the start-up for the sigma_w derivative, in a launch of
+// its own (the analysis kernel's body is long enough that its warps wait on
+// instruction fetch): per stamp, one pass for the brightest pixel (ties to the
+// lowest index) and the double-float total, then r50_ring's disc sums; the
+// record goes to a.r50g for the analysis kernel.  One warp per stamp, stamps
+// in grid-stride order; a stamp whose sigma_w does not come from the growth
+// curve, or that the analysis kernel skips, gets on = 0.
+template <int DT, bool JVP>
+__global__ void __launch_bounds__(256) moment_r50_kernel(MomentGradArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t si = gw; si < a.count; si += nw) {
+        const fse_stamp ix = a.idx[si];
+        const fse_result mom = a.moments[si];
+        R50Grad rg;
+        rg.on = 0;
+        rg.pr = rg.pc = rg.k = 0;
+        rg.c_in = rg.c_ring = rg.c_out = rg.u_in = rg.u_disc = 0.f;
+        const long long npl = static_cast<long long>(ix.h) * ix.w;
+        const bool sig_held = (a.mode & FSE_MOM_SIGW_FIXED) || (mom.status & FSE_ST_SIGW_CLAMPED);
+        const bool use = ix.h >= 1 && ix.w >= 1 && npl <= FSE_MAX_PIX && (mom.status & FSE_ST_MOM_CONVERGED) &&
+                         !sig_held && (a.mode & FSE_MOM_SIGW_R50);
+        if (use) {
+            const int npix = static_cast<int>(npl);
+            const float sc = (DT == FSE_BF16 && a.scale) ? a.scale[si] : 1.f;
+            float vmax = -INFINITY;
+            int imax = 0x7fffffff;
+            float th[1] = {0.f}, tl[1] = {0.f};
+            int p0 = lane;
+            for (; p0 + 224 < npix; p0 += 256) {
+                float v[8], pt = 0.f;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = load_pix<DT>(a, ix.offset + p0 + 32 * u, sc);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (v[u] > vmax) { vmax = v[u]; imax = p0 + 32 * u; }
+                    pt += v[u];
+                }
+                df_add(th[0], tl[0], pt);
+            }
+            {
+                float pt = 0.f;
+                for (int p = p0; p < npix; p += 32) {
+                    const float v = load_pix<DT>(a, ix.offset + p, sc);
+                    if (v > vmax) { vmax = v; imax = p; }
+                    pt += v;
+                }
+                df_add(th[0], tl[0], pt);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const float ov = __shfl_xor_sync(kFull, vmax, off);
+                const int oi = __shfl_xor_sync(kFull, imax, off);
+                if (ov > vmax || (ov == vmax && oi < imax)) { vmax = ov; imax = oi; }
+            }
+            warp_allsum_df(th, tl);
+            // a non-finite pixel leaves the total non-finite: no dependence
+            // (the analysis kernel flags the stamp)
+            if (isfinite(th[0]) && imax < npix)
+                rg = r50_ring<DT, JVP>(a, ix, npix, sc, mom.r50, imax, th[0], tl[0], lane);
+        }
+        if (lane == 0) a.r50g[si] = rg;
+    }
+}
+
 // The VJP's pixel gradient from the per-stamp coefficients: it depends on
 // the pixels only through the coefficients, so this pass reads none and
 // streams the writes.  One warp per stamp, stamps in grid-stride order;
@@ -616,6 +654,14 @@ cudaError_t launch_t(const MomentGradArgs& a, cudaStream_t stream) {
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    if (a.mode & FSE_MOM_SIGW_R50) {
+        long long rgrid = (a.count + 7) / 8;          // eight stamps (warps) per CTA
+        const long long rcap = static_cast<long long>(sms) * 8;
+        if (rgrid > rcap) rgrid = rcap;
+        moment_r50_kernel<DT, JVP><<<static_cast<unsigned>(rgrid), 256, 0, stream>>>(a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
