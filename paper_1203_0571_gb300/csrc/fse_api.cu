@@ -1083,7 +1083,7 @@ static int moment_grad(fse_ctx* ctx, bool jvp, const void* pix, int dtype, const
         if (rc) return rc;
         a.coef = ctx->d_vjp;
     }
-    if (mode & FSE_MOM_SIGW_R50) {
+    if (!jvp && (mode & FSE_MOM_SIGW_R50)) {
         // the ring launch's growth-curve records for the analysis kernel
         const int rc = grow(ctx, &ctx->d_r50, &ctx->r50_cap, static_cast<size_t>(count));
         if (rc) return rc;

@@ -361,6 +361,12 @@ __global__ void __launch_bounds__(256, 2) moment_grad_kernel(MomentGradArgs a) {
         for (int i = 0; i < 15; ++i) Mh[i] = Ml[i] = 0.f;
 #pragma unroll
         for (int i = 0; i < 7; ++i) Uh[i] = Ul[i] = 0.f;
+        // JVP: the brightest pixel and the total ride along the moments pass
+        // (its one launch reads the stamp once); the VJP has them from the
+        // ring launch
+        const bool inl = JVP && sig_r50;
+        float vmax = -INFINITY, th_ = 0.f, tl_ = 0.f;
+        int imax = 0x7fffffff;
         if (status == 0) {
             FWalk pw(lane, ix.w);
             int p0 = lane;
@@ -379,6 +385,10 @@ __global__ void __launch_bounds__(256, 2) moment_grad_kernel(MomentGradArgs a) {
                 }
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
+                    if (JVP && inl) {
+                        if (v[u] > vmax) { vmax = v[u]; imax = p0 + 32 * u; }
+                        ptot += v[u];
+                    }
                     moment_terms<JVP>(q, pw.c - q.x0, pw.r - q.y0, v[u], JVP ? uu[u] : 0.f, P, PU);
                     pw.next();
                 }
@@ -387,6 +397,7 @@ __global__ void __launch_bounds__(256, 2) moment_grad_kernel(MomentGradArgs a) {
                 if (JVP) {
 #pragma unroll
                     for (int i = 0; i < 7; ++i) df_add(Uh[i], Ul[i], PU[i]);
+                    if (inl) df_add(th_, tl_, ptot);
                 }
             }
             {
@@ -398,6 +409,10 @@ __global__ void __launch_bounds__(256, 2) moment_grad_kernel(MomentGradArgs a) {
                 for (int p = p0; p < npix; p += 32) {
                     const float v = load_pix<DT>(a, ix.offset + p, sc);
                     const float uu = JVP ? __ldg(a.tangent + ix.offset + p) : 0.f;
+                    if (JVP && inl) {
+                        if (v > vmax) { vmax = v; imax = p; }
+                        ptot += v;
+                    }
                     moment_terms<JVP>(q, pw.c - q.x0, pw.r - q.y0, v, uu, P, PU);
                     pw.next();
                 }
@@ -406,11 +421,12 @@ __global__ void __launch_bounds__(256, 2) moment_grad_kernel(MomentGradArgs a) {
                 if (JVP) {
 #pragma unroll
                     for (int i = 0; i < 7; ++i) df_add(Uh[i], Ul[i], PU[i]);
+                    if (inl) df_add(th_, tl_, ptot);
                 }
             }
             // a NaN or Inf pixel (or tangent) makes I W (u W) non-finite
             // whatever its weight, and with it the warp's total
-            float chk = (Mh[0] + Ml[0]) + (JVP ? Uh[6] + Uh[0] : 0.f);
+            float chk = (Mh[0] + Ml[0]) + (JVP ? Uh[6] + Uh[0] : 0.f) + (inl ? th_ : 0.f);
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) chk += __shfl_xor_sync(kFull, chk, off);
             finite = isfinite(chk);
@@ -430,7 +446,21 @@ __global__ void __launch_bounds__(256, 2) moment_grad_kernel(MomentGradArgs a) {
         rg.on = 0;
         rg.pr = rg.pc = rg.k = 0;
         rg.c_in = rg.c_ring = rg.c_out = rg.u_in = rg.u_disc = 0.f;
-        if (status == 0 && sig_r50) rg = a.r50g[si];
+        if (status == 0 && sig_r50) {
+            if constexpr (JVP) {
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    const float ov = __shfl_xor_sync(kFull, vmax, off);
+                    const int oi = __shfl_xor_sync(kFull, imax, off);
+                    if (ov > vmax || (ov == vmax && oi < imax)) { vmax = ov; imax = oi; }
+                }
+                float t2h[1] = {th_}, t2l[1] = {tl_};
+                warp_allsum_df(t2h, t2l);
+                rg = r50_ring<DT, JVP>(a, ix, npix, sc, mom.r50, imax, t2h[0], t2l[0], lane);
+            } else {
+                rg = a.r50g[si];
+            }
+        }
         // J: lane 5k + l assembles J_kl; then every lane holds all 25
         float X[25], xs[5], rhs[5];
         bool solved = false;
@@ -541,11 +571,12 @@ __global__ void __launch_bounds__(256, 2) moment_grad_kernel(MomentGradArgs a) {
     }
 }
 
-// The growth curve of the start-up for the sigma_w derivative, in a launch of
-// its own (the analysis kernel's body is long enough that its warps wait on
-// instruction fetch): per stamp, one pass for the brightest pixel (ties to the
-// lowest index) and the double-float total, then r50_ring's disc sums; the
-// record goes to a.r50g for the analysis kernel.  One warp per stamp, stamps
+// The growth curve of the start-up for the VJP's sigma_w derivative, in a
+// launch of its own (the analysis kernel's body is long enough that its warps
+// wait on instruction fetch; the JVP keeps it in its one kernel, whose passes
+// then read the stamp from DRAM once): per stamp, one pass for the brightest
+// pixel (ties to the lowest index) and the double-float total, then
+// r50_ring's disc sums; the record goes to a.r50g for the analysis kernel.  One warp per stamp, stamps
 // in grid-stride order; a stamp whose sigma_w does not come from the growth
 // curve, or that the analysis kernel skips, gets on = 0.
 template <int DT, bool JVP>
@@ -654,13 +685,15 @@ cudaError_t launch_t(const MomentGradArgs& a, cudaStream_t stream) {
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    if (a.mode & FSE_MOM_SIGW_R50) {
-        long long rgrid = (a.count + 7) / 8;          // eight stamps (warps) per CTA
-        const long long rcap = static_cast<long long>(sms) * 8;
-        if (rgrid > rcap) rgrid = rcap;
-        moment_r50_kernel<DT, JVP><<<static_cast<unsigned>(rgrid), 256, 0, stream>>>(a);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+    if constexpr (!JVP) {
+        if (a.mode & FSE_MOM_SIGW_R50) {
+            long long rgrid = (a.count + 7) / 8;          // eight stamps (warps) per CTA
+            const long long rcap = static_cast<long long>(sms) * 8;
+            if (rgrid > rcap) rgrid = rcap;
+            moment_r50_kernel<DT, false><<<static_cast<unsigned>(rgrid), 256, 0, stream>>>(a);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
     }
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
     if (e != cudaSuccess) return e;
