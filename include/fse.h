@@ -357,12 +357,13 @@ int fse_star_fit(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
  * FSE_ST_FIT_SINGULAR (J singular); such stamps get zero derivatives.
  * bf16 pixels are decoded with scale[s]; the derivatives are with respect to
  * the decoded intensities.  Device pointers; asynchronous on `stream`.  The
- * VJP runs two launches: one per stamp for the sums, J and the solve, which
- * writes 96 bytes of coefficients per stamp to a grow-only scratch buffer of
- * the context (allocated, with a device synchronisation, when a call has more
- * stamps than any before: not under stream capture); then one that writes
- * dL/dI from them.  VJP calls on one context that overlap on the GPU share the
- * scratch. */
+ * VJP runs up to three launches: with FSE_MOM_SIGW_R50 one for the growth
+ * curve (a 48-byte record per stamp), one per stamp for the sums, J and the
+ * solve (96 bytes of coefficients per stamp), then one that writes dL/dI from
+ * them.  The records and coefficients live in grow-only scratch buffers of the
+ * context, allocated, with a device synchronisation, when a call has more
+ * stamps than any before (so not under stream capture); VJP calls on one
+ * context that overlap on the GPU share them. */
 int fse_moment_vjp(fse_ctx *ctx, const void *pix, int dtype, const float *scale,
                    const fse_stamp *idx, int64_t count, const fse_result *moments, int mode,
                    const float *v, float *dpix, uint32_t *status, void *stream);
