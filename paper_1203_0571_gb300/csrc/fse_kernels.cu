@@ -1244,12 +1244,21 @@ __device__ __forceinline__ SubGeom sub_geom(const MomState& st, int S) {
     return q;
 }
 
+// 0.5 log2 R^2 of a pixel or sub-grid point; at R = 0 (the centre itself) a
+// value whose exp2 is 0.  The hardware lg2 is used: its absolute error (about
+// 2^-22 on the logarithm of the mantissa) is that of the fp32 value it is kept
+// in for the radii of a stamp, and it enters the model only through
+// u = exp2((0.5 log2 R^2 - c0) / n), as an absolute error of the exponent.
+__device__ __forceinline__ float half_log2_r2(float R2) {
+    return R2 > 0.f ? 0.5f * __log2f(R2) : -1000.f;
+}
+
 // a = log2(r / r_e) of one sub-grid point (r = R / (1 - |g|); c0 = log2 r_e + log2(1 - |g|)).
 __device__ __forceinline__ float sub_a(const SubGeom& q, float t1, float t2, int a, int c, float c0) {
     const float u1 = t1 + (static_cast<float>(a) + 0.5f) * q.invS - 0.5f;
     const float u2 = t2 + (static_cast<float>(c) + 0.5f) * q.invS - 0.5f;
     const float R2 = fmaf(q.A, u1 * u1, fmaf(q.B, u2 * u2, -q.G4 * (u1 * u2)));
-    return (R2 > 0.f ? 0.5f * log2f(R2) : -1000.f) - c0;
+    return half_log2_r2(R2) - c0;
 }
 
 // Offsets of a pixel from the fixed centre.
@@ -1744,7 +1753,7 @@ __device__ FitOut sersic_fit(const float* s, float* L, const float* sq, int h, i
             const float t1 = static_cast<float>(pw.col - st.xi) - st.xf;
             const float t2 = static_cast<float>(pw.row - st.yi) - st.yf;
             const float R2 = fmaf(A, t1 * t1, fmaf(B, t2 * t2, -G4 * (t1 * t2)));
-            L[p] = R2 > 0.f ? 0.5f * log2f(R2) : -1000.f;
+            L[p] = half_log2_r2(R2);
             pw.next();
         }
         g.sync();
