@@ -241,7 +241,9 @@ int fse_fit_batch_plain(fse_ctx *ctx, const void *pix, int dtype, const float *s
  * runs each chunk's chain on `stream` or a second context stream as soon as
  * its copy is done, copies the results back and returns when out[] is
  * complete.  npix_total bounds every idx[s].offset + h*w; a stamp outside it
- * returns FSE_EINVAL before anything is copied.  Results equal those of
+ * returns FSE_EINVAL before any kernel runs, with out[] untouched (each chunk
+ * is checked just before its copy, so the chunks before it may already have
+ * been copied into the context's buffers).  Results equal those of
  * fse_fit_batch byte for byte.  One host-buffer call at a time per context
  * (the device buffers and events are the context's). */
 int fse_fit_batch_host(fse_ctx *ctx, const void *pix, int64_t npix_total, int dtype,

@@ -565,24 +565,6 @@ int fse_fit_batch_host(fse_ctx* ctx, const void* pix, int64_t npix_total, int dt
         }
         lo[kHostChunks] = count;
     }
-    // one pass over the index: every stamp inside the buffer, the tile size,
-    // and the pixel span [p_lo, p_hi) of each chunk
-    int64_t maxp = 1;
-    int64_t p_lo[kHostChunks], p_hi[kHostChunks];
-    for (int c = 0; c < nchunk; ++c) {
-        p_lo[c] = INT64_MAX;
-        p_hi[c] = 0;
-        for (int64_t st = lo[c]; st < lo[c + 1]; ++st) {
-            const int64_t a = static_cast<int64_t>(idx[st].h) * idx[st].w;
-            if (idx[st].h < 1 || idx[st].w < 1 || a > FSE_MAX_PIX) continue;
-            if (idx[st].offset < 0 || idx[st].offset + a > npix_total)
-                return set_error(ctx, FSE_EINVAL, "stamp %lld lies outside the pixel buffer", (long long)st);
-            maxp = std::max(maxp, a);
-            p_lo[c] = std::min(p_lo[c], idx[st].offset);
-            p_hi[c] = std::max(p_hi[c], idx[st].offset + a);
-        }
-    }
-    if (o.max_pix == 0) o.max_pix = static_cast<int32_t>(maxp);
     if ((rc = grow(ctx, reinterpret_cast<char**>(&ctx->d_pix), &ctx->pix_cap, npix_total * esz)) ||
         (rc = grow(ctx, &ctx->d_idx, &ctx->idx_cap, count)) ||
         (rc = grow(ctx, &ctx->d_out, &ctx->out_cap, count)) ||
@@ -592,34 +574,55 @@ int fse_fit_batch_host(fse_ctx* ctx, const void* pix, int64_t npix_total, int dt
     // Three streams: the copy stream moves every chunk's inputs to the device
     // back to back and records chunk_ev[c] after chunk c; chunk c's kernels and
     // its result copy run on compute stream c % 2 once chunk_ev[c] is done, so
-    // one chunk's launch tail overlaps the next chunk's kernels.  Copies and
-    // kernels are issued chunk by chunk: from pageable memory a copy returns
-    // only when done, and the kernels issued before it run meanwhile.
+    // one chunk's launch tail overlaps the next chunk's kernels.
     const cudaStream_t s0 = static_cast<cudaStream_t>(stream);
     const cudaStream_t streams[2] = {s0, ctx->aux_stream};
+    const cudaStream_t cs = ctx->copy_stream;
     cudaEvent_t ev_start = ctx->chunk_ev[kHostChunks], ev_end = ctx->chunk_ev[kHostChunks + 1];
     cudaError_t e = cudaEventRecord(ev_start, s0);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ev_start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_start, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux_stream, ev_start, 0);
+    // First, chunk by chunk: every stamp inside the pixel buffer, the largest
+    // stamp, the chunk's pixel span [p_lo, p_hi), then the chunk's copies, so
+    // that the first chunks move while the later ones are checked.  From
+    // pageable memory a copy returns only when done.
+    int64_t maxp = 1;
     for (int c = 0; c < nchunk && e == cudaSuccess; ++c) {
+        int64_t p_lo = INT64_MAX, p_hi = 0;
+        for (int64_t st = lo[c]; st < lo[c + 1]; ++st) {
+            const int64_t a = static_cast<int64_t>(idx[st].h) * idx[st].w;
+            if (idx[st].h < 1 || idx[st].w < 1 || a > FSE_MAX_PIX) continue;
+            if (idx[st].offset < 0 || idx[st].offset + a > npix_total) {
+                cudaStreamSynchronize(cs);   // the copies already issued read the caller's buffers
+                return set_error(ctx, FSE_EINVAL, "stamp %lld lies outside the pixel buffer", (long long)st);
+            }
+            maxp = std::max(maxp, a);
+            p_lo = std::min(p_lo, idx[st].offset);
+            p_hi = std::max(p_hi, idx[st].offset + a);
+        }
         const int64_t s_lo = lo[c], n_c = lo[c + 1] - lo[c];
-        const cudaStream_t cs = ctx->copy_stream;
         if (n_c > 0) {
             e = cudaMemcpyAsync(ctx->d_idx + s_lo, idx + s_lo, n_c * sizeof(fse_stamp),
                                 cudaMemcpyHostToDevice, cs);
-            if (e == cudaSuccess && p_hi[c] > p_lo[c])
-                e = cudaMemcpyAsync(static_cast<char*>(ctx->d_pix) + p_lo[c] * esz,
-                                    static_cast<const char*>(pix) + p_lo[c] * esz,
-                                    (p_hi[c] - p_lo[c]) * esz, cudaMemcpyHostToDevice, cs);
+            if (e == cudaSuccess && p_hi > p_lo)
+                e = cudaMemcpyAsync(static_cast<char*>(ctx->d_pix) + p_lo * esz,
+                                    static_cast<const char*>(pix) + p_lo * esz,
+                                    (p_hi - p_lo) * esz, cudaMemcpyHostToDevice, cs);
             if (e == cudaSuccess && scale)
                 e = cudaMemcpyAsync(ctx->d_scale + s_lo, scale + s_lo, n_c * sizeof(float),
                                     cudaMemcpyHostToDevice, cs);
-            if (e == cudaSuccess && inv_var && p_hi[c] > p_lo[c])
-                e = cudaMemcpyAsync(ctx->d_ivar + p_lo[c], inv_var + p_lo[c],
-                                    (p_hi[c] - p_lo[c]) * sizeof(float), cudaMemcpyHostToDevice, cs);
+            if (e == cudaSuccess && inv_var && p_hi > p_lo)
+                e = cudaMemcpyAsync(ctx->d_ivar + p_lo, inv_var + p_lo,
+                                    (p_hi - p_lo) * sizeof(float), cudaMemcpyHostToDevice, cs);
         }
         if (e == cudaSuccess) e = cudaEventRecord(ctx->chunk_ev[c], cs);
-        if (e != cudaSuccess || n_c == 0) continue;
+    }
+    // Then each chunk's chain once its copy is done, all with the launch shape
+    // of the batch's largest stamp (as fse_fit_batch, so the results are the same).
+    if (o.max_pix == 0) o.max_pix = static_cast<int32_t>(maxp);
+    for (int c = 0; c < nchunk && e == cudaSuccess; ++c) {
+        const int64_t s_lo = lo[c], n_c = lo[c + 1] - lo[c];
+        if (n_c == 0) continue;
         const cudaStream_t st = streams[c & 1];
         e = cudaStreamWaitEvent(st, ctx->chunk_ev[c], 0);
         if (e != cudaSuccess) break;
@@ -638,7 +641,7 @@ int fse_fit_batch_host(fse_ctx* ctx, const void* pix, int64_t npix_total, int dt
         launch_shape(o, a.opts.max_pix, fse::kStageAll, &a.warps_per_cta, &a.warps_per_stamp);
         rc = run(ctx, a, st);
         if (rc) {
-            cudaStreamSynchronize(ctx->copy_stream);
+            cudaStreamSynchronize(cs);
             cudaStreamSynchronize(ctx->aux_stream);
             cudaStreamSynchronize(s0);
             cudaGetLastError();

@@ -236,6 +236,26 @@ def test_host_buffers_equal_device(ctx):
     assert host.tobytes() == dev.tobytes()
 
 
+def test_host_buffers_stamp_outside_the_buffer(ctx):
+    """A stamp past the end of the pixel buffer in the last of the nine chunks:
+    the call returns FSE_EINVAL with out[] untouched, after the chunks before
+    it were checked and copied; the context then runs the batch unchanged."""
+    batch = synth.make_workload(1, count=9000)
+    host_pix = batch.pix.pin_memory()
+    bad = B.make_index(batch.offset, batch.h, batch.w, device="cpu").clone()
+    bad[8990, 0] = batch.pix.numel() - 100          # offset + 48 * 48 > npix_total
+    out = torch.full((batch.count, 64), 0xA5, dtype=torch.uint8).pin_memory()
+    with pytest.raises(B.FseError) as err:
+        ctx.fit_batch_host(host_pix, bad.pin_memory(), out=out)
+    assert err.value.code == B.FSE_EINVAL and "8990" in str(err.value)
+    assert bool((out == 0xA5).all())
+    good = B.make_index(batch.offset, batch.h, batch.w, device="cpu").pin_memory()
+    ctx.fit_batch_host(host_pix, good, out=out)
+    b = batch.to("cuda")
+    dev = B.results(ctx.fit_batch(b.pix, B.make_index(b.offset, b.h, b.w), opts=opts_for(batch)))
+    assert out.numpy().view(B.RESULT_DTYPE).reshape(-1).tobytes() == dev.tobytes()
+
+
 def test_host_buffers_ragged_bf16_inverse_variance(ctx):
     """The chunked host-buffer pipeline on 9,001 stamps of 32-64 px (bf16 with a
     per-stamp scale, a per-pixel inverse variance, two stamps of a refused
